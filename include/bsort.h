@@ -1,0 +1,165 @@
+/*
+ * bsort.h — C ABI of the GB300 length-bucketed word sort.
+ *
+ * The operation (arXiv 1407.6603, Section II "Pre-processing", three phases;
+ * Section III "Approach one", steps 1-4):
+ *   1. strip the special characters from a text: every byte that is not an
+ *      ASCII letter [A-Za-z] is deleted, and whitespace (0x20, 0x09..0x0D)
+ *      separates words; words left empty are dropped;
+ *   2. put the words in buckets by their number of characters, shorter
+ *      buckets first (the bucket sizes are the per-length counts);
+ *   3. sort each bucket by the ASCII codes of its letters (unsigned byte
+ *      order, case kept, duplicates kept).
+ * The result is unique: two equal-length words compare equal only when they
+ * are the same bytes, so every correct sort returns the same stream.
+ *
+ * Every step runs in CUDA kernels on one GPU (sm_103a).  There is no CPU
+ * fallback: a context cannot be created without a CUDA device.
+ *
+ * Conventions for every function below:
+ *   - No call aborts or throws.  Each returns a bsort_status; the message of
+ *     the last failure on a context is available from bsort_last_error().
+ *   - A failed call leaves its output struct(s) zeroed.
+ *   - A context is not thread-safe: one host thread at a time.
+ *   - Output buffers belong to the context.  They stay valid until the next
+ *     bsort_text / bsort_text_device / bsort_batch call on the same context,
+ *     bsort_result_release() or bsort_destroy(), whichever comes first.
+ */
+#ifndef BSORT_H
+#define BSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bsort_ctx bsort_ctx; /* opaque */
+
+typedef enum {
+  BSORT_OK = 0,
+  BSORT_E_INVAL = 1,         /* a NULL pointer where one is required, or a bad config value */
+  BSORT_E_NOMEM = 2,         /* device or pinned host memory could not be allocated */
+  BSORT_E_CUDA = 3,          /* a CUDA runtime call or a kernel launch failed */
+  BSORT_E_TOO_LARGE = 4,     /* a document of 2^32 bytes or more (offsets are 32-bit) */
+  BSORT_E_WORD_TOO_LONG = 5, /* a word longer than the context's l_cap letters */
+  BSORT_E_TIMEOUT = 6,       /* a bounded device-side wait gave up (the context stays usable) */
+  BSORT_E_BUSY = 7           /* the context is in use by another call */
+} bsort_status;
+
+/* Context configuration.  Fill with bsort_config_default() and change fields. */
+typedef struct {
+  uint32_t l_cap;        /* longest word accepted, 1..255 letters (default 255).  A longer word
+                            makes the call fail with BSORT_E_WORD_TOO_LONG. */
+  int32_t want_offsets;  /* 1 (default): produce per-word offsets; 0: counts and stream only */
+  int32_t device;        /* CUDA device ordinal; -1 (default) = the current device */
+  int32_t profile;       /* 1: time every kernel launch with CUDA events (see bsort_profile_read);
+                            0 (default): no events are recorded */
+  uint64_t wait_limit;   /* iteration limit of every device-side spin wait (0 = default, about
+                            a second); when one runs out the call returns BSORT_E_TIMEOUT */
+} bsort_config;
+
+/*
+ * One document's result.
+ *   counts[L], 0 <= L <= max_len: number of words of L letters; counts[0] == 0.
+ *   stream: the sorted words back to back, no separators: bucket 1 first,
+ *           each bucket in ascending unsigned byte order.
+ *   offsets[j], 0 <= j <= n_words: word j is stream[offsets[j] .. offsets[j+1]);
+ *           offsets[0] == 0 and offsets[n_words] == stream_bytes.  NULL when the
+ *           context was created with want_offsets == 0.
+ * A document with no words has max_len 0, counts = {0}, offsets = {0} and an
+ * empty stream.
+ */
+typedef struct {
+  uint32_t max_len;         /* longest word, 0 if there is none */
+  uint32_t status;          /* bsort_status of this document (batch calls) */
+  uint64_t n_words;         /* number of words */
+  uint64_t stream_bytes;    /* total letters = sum over L of L * counts[L] */
+  const uint64_t* counts;   /* [max_len + 1] */
+  const uint32_t* offsets;  /* [n_words + 1] or NULL */
+  const uint8_t* stream;    /* [stream_bytes] */
+} bsort_result;
+
+/* Default configuration: l_cap 255, offsets on, current device, default wait limit. */
+void bsort_config_default(bsort_config* cfg);
+
+/*
+ * Creates a context on the configured device (cfg may be NULL for the
+ * defaults).  The context owns a CUDA stream, a device arena and pinned host
+ * buffers, all grown on demand.  Errors: BSORT_E_INVAL (out == NULL or a bad
+ * config value), BSORT_E_CUDA (no usable device), BSORT_E_NOMEM.
+ */
+bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg);
+
+/* Frees everything the context owns.  NULL is accepted. */
+void bsort_destroy(bsort_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none); valid until the next call on ctx. */
+const char* bsort_last_error(const bsort_ctx* ctx);
+
+/*
+ * Sorts one document held in host memory (bytes may be NULL when len == 0).
+ * Synchronous: on return, *out holds HOST pointers into buffers owned by the
+ * context.  Errors: BSORT_E_INVAL, BSORT_E_TOO_LARGE (len >= 2^32),
+ * BSORT_E_WORD_TOO_LONG, BSORT_E_NOMEM, BSORT_E_CUDA, BSORT_E_TIMEOUT.
+ */
+bsort_status bsort_text(bsort_ctx* ctx, const uint8_t* bytes, size_t len, bsort_result* out);
+
+/*
+ * Sorts one document already in device memory.  d_bytes is a device pointer
+ * (any alignment) to len bytes; it must stay unchanged until the work
+ * enqueued on `stream` has finished.  `stream` is a cudaStream_t (NULL = the
+ * legacy default stream).
+ * The call enqueues the whole path on `stream` and waits only for the length
+ * histogram, which fixes the bucket layout; it returns with the scalar fields
+ * of *out filled and with DEVICE pointers in counts, offsets and stream, whose
+ * contents are complete once `stream` reaches the point of return (for
+ * example after cudaStreamSynchronize(stream)).
+ * Errors: as bsort_text.
+ */
+bsort_status bsort_text_device(bsort_ctx* ctx, const uint8_t* d_bytes, size_t len, void* stream,
+                               bsort_result* out);
+
+/*
+ * Sorts n independent documents held in host memory in one pass of the path:
+ * every kernel launch covers all documents.  docs[i] points to lens[i] bytes.
+ * outs[i] receives document i's result (HOST pointers), with outs[i].status
+ * set per document; the call returns BSORT_OK when every document succeeded,
+ * otherwise the first failing document's status.  Each document's result is
+ * identical to what bsort_text returns for it alone.
+ */
+bsort_status bsort_batch(bsort_ctx* ctx, const uint8_t* const* docs, const size_t* lens, size_t n,
+                         bsort_result* outs);
+
+/*
+ * Kernel tracing.  Every launch is counted; with config.profile == 1 each one
+ * is also bracketed by two CUDA events on the stream it runs on, and tagged
+ * with the algorithmic bytes it must move (the reads and writes the method
+ * needs: input, stripped letters, word starts, keys, output).
+ */
+typedef struct {
+  const char* name;   /* kernel family: "tok_summary", "tok_scan", "tok_write", "hist", "scatter",
+                         "tile_sort", "merge_pass", "emit" (static string) */
+  uint64_t launches;  /* launches since the last read */
+  double ms;          /* summed device time of those launches (0 when profiling is off) */
+  double bytes;       /* summed algorithmic bytes of those launches */
+} bsort_kernel_stat;
+
+/* Writes up to `max` per-family statistics accumulated since the last read
+ * into out[], waits for the recorded events, resets the accumulators and
+ * returns the number of families written (or -1 on error). */
+int bsort_profile_read(bsort_ctx* ctx, bsort_kernel_stat* out, int max);
+
+/* Kernel launches made by this context since it was created. */
+uint64_t bsort_launch_count(const bsort_ctx* ctx);
+
+/* Marks a result's buffers as no longer needed and zeroes *res.  The memory
+ * itself stays with the context for reuse. */
+void bsort_result_release(bsort_ctx* ctx, bsort_result* res);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSORT_H */

@@ -1,0 +1,303 @@
+"""Python binding of libbsort, the GB300 length-bucketed word sort.
+
+The method (arXiv 1407.6603, Section II, three pre-processing phases): strip
+every non-letter from a text, bucket its words by length with shorter buckets
+first, and sort each bucket into ASCII order.  All of it runs in the CUDA
+kernels of ``libbsort.so``; this module only marshals arguments through the C
+ABI of ``include/bsort.h`` and has the same entry point names.  There is no
+CPU fallback: ``load()`` raises when the library has not been built.
+
+PyTorch is used here only for device memory and streams (``text_device``
+takes a CUDA tensor and the current torch stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbsort.so")
+
+BSORT_OK = 0
+BSORT_E_INVAL = 1
+BSORT_E_NOMEM = 2
+BSORT_E_CUDA = 3
+BSORT_E_TOO_LARGE = 4
+BSORT_E_WORD_TOO_LONG = 5
+BSORT_E_TIMEOUT = 6
+BSORT_E_BUSY = 7
+STATUS_NAMES = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_TOO_LARGE", 5: "E_WORD_TOO_LONG",
+                6: "E_TIMEOUT", 7: "E_BUSY"}
+
+
+class bsort_config(ctypes.Structure):
+    _fields_ = [("l_cap", ctypes.c_uint32), ("want_offsets", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("wait_limit", ctypes.c_uint64)]
+
+
+class bsort_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+class bsort_result(ctypes.Structure):
+    _fields_ = [("max_len", ctypes.c_uint32), ("status", ctypes.c_uint32), ("n_words", ctypes.c_uint64),
+                ("stream_bytes", ctypes.c_uint64), ("counts", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("stream", ctypes.c_void_p)]
+
+
+class BsortError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"bsort {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    from . import builder as _b
+
+    return _b.build(force=force)
+
+
+def load(path: str | None = None):
+    """Load libbsort.so.  Raises if it is missing: there is no fallback path."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libbsort.so not found at {p}: run build() (nvcc, sm_103a) first")
+    lib = ctypes.CDLL(p)
+    ctx_p = ctypes.c_void_p
+    lib.bsort_config_default.restype = None
+    lib.bsort_config_default.argtypes = [ctypes.POINTER(bsort_config)]
+    lib.bsort_create.restype = ctypes.c_int
+    lib.bsort_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(bsort_config)]
+    lib.bsort_destroy.restype = None
+    lib.bsort_destroy.argtypes = [ctx_p]
+    lib.bsort_last_error.restype = ctypes.c_char_p
+    lib.bsort_last_error.argtypes = [ctx_p]
+    lib.bsort_text.restype = ctypes.c_int
+    lib.bsort_text.argtypes = [ctx_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(bsort_result)]
+    lib.bsort_text_device.restype = ctypes.c_int
+    lib.bsort_text_device.argtypes = [ctx_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                      ctypes.POINTER(bsort_result)]
+    lib.bsort_batch.restype = ctypes.c_int
+    lib.bsort_batch.argtypes = [ctx_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t),
+                                ctypes.c_size_t, ctypes.POINTER(bsort_result)]
+    lib.bsort_result_release.restype = None
+    lib.bsort_result_release.argtypes = [ctx_p, ctypes.POINTER(bsort_result)]
+    lib.bsort_profile_read.restype = ctypes.c_int
+    lib.bsort_profile_read.argtypes = [ctx_p, ctypes.POINTER(bsort_kernel_stat), ctypes.c_int]
+    lib.bsort_launch_count.restype = ctypes.c_uint64
+    lib.bsort_launch_count.argtypes = [ctx_p]
+    if path is None:
+        _lib = lib
+    return lib
+
+
+# ---- thin wrappers with the C names ----
+
+def bsort_config_default() -> bsort_config:
+    cfg = bsort_config()
+    load().bsort_config_default(ctypes.byref(cfg))
+    return cfg
+
+
+def bsort_create(cfg: bsort_config | None = None) -> ctypes.c_void_p:
+    lib = load()
+    h = ctypes.c_void_p()
+    st = lib.bsort_create(ctypes.byref(h), ctypes.byref(cfg) if cfg is not None else None)
+    if st != BSORT_OK:
+        raise BsortError(st, "bsort_create failed")
+    return h
+
+
+def bsort_destroy(h) -> None:
+    load().bsort_destroy(h)
+
+
+def bsort_last_error(h) -> str:
+    return load().bsort_last_error(h).decode(errors="replace")
+
+
+def _as_u8(data) -> np.ndarray:
+    if isinstance(data, (bytes, bytearray, memoryview)):
+        return np.frombuffer(bytes(data), dtype=np.uint8)
+    return np.ascontiguousarray(data, dtype=np.uint8).reshape(-1)
+
+
+def bsort_text(h, data) -> bsort_result:
+    a = _as_u8(data)
+    res = bsort_result()
+    st = load().bsort_text(h, a.ctypes.data if a.size else None, a.size, ctypes.byref(res))
+    if st != BSORT_OK:
+        raise BsortError(st, bsort_last_error(h))
+    return res
+
+
+def bsort_text_device(h, ptr: int, nbytes: int, stream: int) -> bsort_result:
+    res = bsort_result()
+    st = load().bsort_text_device(h, ptr if nbytes else None, nbytes, stream or None, ctypes.byref(res))
+    if st != BSORT_OK:
+        raise BsortError(st, bsort_last_error(h))
+    return res
+
+
+def bsort_batch(h, docs: list) -> tuple[int, list[bsort_result]]:
+    arrs = [_as_u8(d) for d in docs]
+    n = len(arrs)
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data if a.size else None for a in arrs])
+    lens = (ctypes.c_size_t * max(n, 1))(*[a.size for a in arrs])
+    outs = (bsort_result * max(n, 1))()
+    st = load().bsort_batch(h, ptrs, lens, n, outs)
+    return st, [outs[i] for i in range(n)]
+
+
+def bsort_result_release(h, res: bsort_result) -> None:
+    load().bsort_result_release(h, ctypes.byref(res))
+
+
+def bsort_profile_read(h) -> dict:
+    """Per kernel family: {name: (launches, ms, algorithmic bytes)} since the last read."""
+    arr = (bsort_kernel_stat * 16)()
+    k = load().bsort_profile_read(h, arr, 16)
+    if k < 0:
+        raise BsortError(BSORT_E_CUDA, "bsort_profile_read failed")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms), float(arr[i].bytes)) for i in range(k)}
+
+
+def bsort_launch_count(h) -> int:
+    return int(load().bsort_launch_count(h))
+
+
+# ---- convenience layer ----
+
+@dataclass
+class Result:
+    max_len: int
+    n_words: int
+    stream_bytes: int
+    counts: np.ndarray
+    offsets: np.ndarray | None
+    stream: np.ndarray
+    status: int = 0
+
+    def words(self) -> list[bytes]:
+        s = self.stream.tobytes()
+        off = self.offsets.tolist()
+        return [s[off[i]:off[i + 1]] for i in range(len(off) - 1)]
+
+
+def _host_result(r: bsort_result, want_offsets: bool) -> Result:
+    n = int(r.n_words)
+    ml = int(r.max_len)
+
+    def arr(ptr, ctype, count, dtype):
+        if count == 0:
+            return np.zeros(0, dtype=dtype)
+        return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctype)), shape=(count,)).copy()
+
+    return Result(
+        max_len=ml, n_words=n, stream_bytes=int(r.stream_bytes),
+        counts=arr(r.counts, ctypes.c_uint64, ml + 1, np.uint64),
+        offsets=arr(r.offsets, ctypes.c_uint32, n + 1, np.uint32) if want_offsets else None,
+        stream=arr(r.stream, ctypes.c_uint8, int(r.stream_bytes), np.uint8),
+        status=int(r.status),
+    )
+
+
+class _DevView:
+    """A device buffer owned by the context, seen through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, count: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr or 0, False),
+                                         "version": 3, "strides": None, "stream": None}
+
+
+class Context:
+    """Owns a bsort context (CUDA stream, device arena, pinned host buffers)."""
+
+    def __init__(self, l_cap: int = 255, want_offsets: bool = True, device: int = -1, wait_limit: int = 0,
+                 profile: bool = False):
+        cfg = bsort_config_default()
+        cfg.l_cap = l_cap
+        cfg.want_offsets = 1 if want_offsets else 0
+        cfg.device = device
+        cfg.profile = 1 if profile else 0
+        cfg.wait_limit = wait_limit
+        self.want_offsets = want_offsets
+        self._h = bsort_create(cfg)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            bsort_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def text(self, data) -> Result:
+        """Host bytes in, host result out (synchronous)."""
+        return _host_result(bsort_text(self._h, data), self.want_offsets)
+
+    def text_device_raw(self, tensor, stream=None) -> bsort_result:
+        """Device tensor in (uint8, contiguous); device pointers out, valid once
+        ``stream`` (default: torch's current stream) reaches this point."""
+        import torch
+
+        assert tensor.is_cuda and tensor.dtype == torch.uint8 and tensor.is_contiguous()
+        s = stream if stream is not None else torch.cuda.current_stream(tensor.device)
+        return bsort_text_device(self._h, tensor.data_ptr(), tensor.numel(), s.cuda_stream)
+
+    def text_device(self, tensor, stream=None, clone: bool = True) -> dict:
+        """As text_device_raw, returning torch tensors (copies unless clone=False)."""
+        import torch
+
+        r = self.text_device_raw(tensor, stream)
+        n, ml = int(r.n_words), int(r.max_len)
+        dev = tensor.device
+
+        def view(ptr, count, typestr, dtype):
+            if count == 0:
+                return torch.zeros(0, dtype=dtype, device=dev)
+            t = torch.as_tensor(_DevView(ptr, count, typestr), device=dev)
+            return t.clone() if clone else t
+
+        with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream(dev)):
+            out = {
+                "max_len": ml, "n_words": n, "stream_bytes": int(r.stream_bytes),
+                # signed views: torch handles int64/int32 everywhere (values < 2^31 here)
+                "counts": view(r.counts, ml + 1, "<i8", torch.int64),
+                "offsets": view(r.offsets, n + 1, "<i4", torch.int32) if self.want_offsets else None,
+                "stream": view(r.stream, int(r.stream_bytes), "|u1", torch.uint8),
+            }
+        return out
+
+    def batch(self, docs: list) -> tuple[int, list[Result]]:
+        st, rs = bsort_batch(self._h, docs)
+        return st, [_host_result(r, self.want_offsets) for r in rs]
+
+    def last_error(self) -> str:
+        return bsort_last_error(self._h)
+
+    def profile_read(self) -> dict:
+        return bsort_profile_read(self._h)
+
+    def launch_count(self) -> int:
+        return bsort_launch_count(self._h)

@@ -1,0 +1,741 @@
+// Host runtime and C ABI of libbsort (declared in include/bsort.h).
+//
+// One call runs the whole path for one or more documents on one CUDA stream:
+//   K1a/K1b/K1c  strip + tokenize            (paper Section II, phase 1)
+//   K2           per-document length counts  (phase 2: sub-array sizes)
+//   -- the host reads the counts back and lays out one bucket per
+//      (document, length): key offsets, tiles, merge passes --
+//   K3           scatter words into buckets as packed keys (phase 2)
+//   K4, K5       sort every bucket: odd-even transposition tiles, then
+//                merge-path passes (phase 3)
+//   K6           write counts, offsets and the sorted stream
+// The only host/device synchronisation inside a call is the read of the
+// length counts; everything after it is enqueued without waiting.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bsort.h"
+#include "bsort_dev.cuh"
+
+using namespace bsort;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+struct HostBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+// Key widths of the classes and the lengths each one holds.
+constexpr uint32_t kClassLmin[kNumClasses] = {1, 9, 17, 33, 65, 129};
+constexpr uint32_t kClassLmax[kNumClasses] = {8, 16, 32, 64, 128, 255};
+
+uint32_t merge_passes(uint64_t n, uint64_t tile) {
+  uint32_t p = 0;
+  while ((tile << p) < n) ++p;
+  return p;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Layout of the device "meta" region, read back in one copy after K2.
+struct MetaLayout {
+  size_t meta = 0, wbase = 0, lbase = 0, item0 = 0, hist = 0, total = 0;
+  void set(uint32_t ndocs) {
+    meta = 0;
+    wbase = meta + align_up(sizeof(Meta), 128);
+    lbase = wbase + align_up((ndocs + 1) * 4ull, 128);
+    item0 = lbase + align_up((ndocs + 1) * 4ull, 128);
+    hist = item0 + align_up((ndocs + 1) * 4ull, 128);
+    total = hist + (size_t)ndocs * kHist * 4;
+  }
+};
+
+struct ClassPlan {
+  uint32_t sbeg = 0, send = 0, tiles = 0, passes = 0;
+  uint64_t key_bytes = 0;  // keys of the class, in bytes
+};
+
+enum Kind { kTokSummary, kTokScan, kTokWrite, kHistK, kScatter, kTileSort, kMerge, kEmit, kKinds };
+const char* const kKindName[kKinds] = {"tok_summary", "tok_scan", "tok_write", "hist",
+                                       "scatter",     "tile_sort", "merge_pass", "emit"};
+
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+}  // namespace
+
+struct bsort_ctx {
+  bsort_config cfg{};
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t own_stream = nullptr;
+  std::string err;
+  bool busy = false;
+
+  DevBuf sticky;  // a Meta kept across calls: err_timeout of bounded device waits
+  HostBuf h_sticky;
+  DevBuf in, docs, sums, carry, meta, starts, letters, lookup, segs, cursor, keysA, keysB, counts, offsets, stream;
+  HostBuf h_in, h_docs, h_meta, h_plan, h_counts, h_offsets, h_stream;
+
+  // results of the last run (host view)
+  MetaLayout ml;
+  uint32_t ndocs = 0;
+  std::vector<Segment> segv;
+  std::vector<uint32_t> lookupv;
+  std::vector<uint32_t> doc_status;
+
+  // tracing
+  uint64_t launches = 0;
+  uint64_t kind_launches[kKinds] = {};
+  double kind_bytes[kKinds] = {};
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<ProfRec> recs;
+};
+
+namespace {
+
+bsort_status fail(bsort_ctx* c, bsort_status s, const std::string& msg) {
+  c->err = msg;
+  return s;
+}
+
+bsort_status cuda_fail(bsort_ctx* c, cudaError_t e, const char* what) {
+  c->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return (e == cudaErrorMemoryAllocation) ? BSORT_E_NOMEM : BSORT_E_CUDA;
+}
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+bsort_status grow(bsort_ctx* c, DevBuf& b, size_t bytes, const char* what) {
+  if (bytes <= b.cap && b.p) return BSORT_OK;
+  size_t want = std::max<size_t>(bytes, 256);
+  want = std::max(want, b.cap + b.cap / 4);  // amortise repeated growth
+  if (b.p) {
+    cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    c->err = std::string("device allocation of ") + std::to_string(want) + " bytes for " + what + " failed";
+    return BSORT_E_NOMEM;
+  }
+  b.cap = want;
+  return BSORT_OK;
+}
+
+bsort_status grow_host(bsort_ctx* c, HostBuf& b, size_t bytes, const char* what) {
+  if (bytes <= b.cap && b.p) return BSORT_OK;
+  size_t want = std::max<size_t>(bytes, 256);
+  want = std::max(want, b.cap + b.cap / 4);
+  if (b.p) {
+    cudaFreeHost(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  cudaError_t e = cudaMallocHost(&b.p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    c->err = std::string("pinned host allocation of ") + std::to_string(want) + " bytes for " + what + " failed";
+    return BSORT_E_NOMEM;
+  }
+  b.cap = want;
+  return BSORT_OK;
+}
+
+#define GROW(buf, bytes, what)                                \
+  do {                                                        \
+    bsort_status s_ = grow(c, (buf), (bytes), (what));        \
+    if (s_ != BSORT_OK) return s_;                            \
+  } while (0)
+#define GROW_HOST(buf, bytes, what)                           \
+  do {                                                        \
+    bsort_status s_ = grow_host(c, (buf), (bytes), (what));   \
+    if (s_ != BSORT_OK) return s_;                            \
+  } while (0)
+
+template <typename T>
+T* dptr(const DevBuf& b, size_t byte_off = 0) {
+  return reinterpret_cast<T*>(static_cast<char*>(b.p) + byte_off);
+}
+template <typename T>
+T* hptr(const HostBuf& b, size_t byte_off = 0) {
+  return reinterpret_cast<T*>(static_cast<char*>(b.p) + byte_off);
+}
+
+// Tracing: count every launch; with profiling on, bracket it with events.
+cudaEvent_t next_event(bsort_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
+}
+
+struct Trace {
+  bsort_ctx* c;
+  cudaStream_t st;
+  int kind;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  Trace(bsort_ctx* c_, cudaStream_t st_, int kind_, double bytes_) : c(c_), st(st_), kind(kind_), bytes(bytes_) {
+    if (c->cfg.profile) {
+      a = next_event(c);
+      if (a) cudaEventRecord(a, st);
+    }
+  }
+  cudaError_t done(cudaError_t e) {
+    if (e != cudaSuccess) return e;
+    c->launches += 1;
+    c->kind_launches[kind] += 1;
+    c->kind_bytes[kind] += bytes;
+    if (a) {
+      cudaEvent_t b = next_event(c);
+      if (b) {
+        cudaEventRecord(b, st);
+        c->recs.push_back(ProfRec{kind, a, b, bytes});
+      }
+    }
+    return e;
+  }
+};
+
+#define LAUNCH(kind, bytes, call, what)                 \
+  do {                                                  \
+    Trace tr_(c, st, (kind), (double)(bytes));          \
+    CK(tr_.done(call), what);                           \
+  } while (0)
+
+// Runs the whole path over `ndocs` documents that sit at d_in + offs[i]
+// (lens[i] bytes each) in device memory.  Leaves the outputs in c->counts,
+// c->offsets, c->stream and the host copy of the meta region in c->h_meta.
+bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, const uint64_t* lens,
+                      uint32_t ndocs, cudaStream_t st) {
+  c->ndocs = ndocs;
+  c->doc_status.assign(ndocs, BSORT_OK);
+  // ---- documents and chunks ----
+  GROW_HOST(c->h_docs, sizeof(DocDesc) * ndocs, "document table");
+  DocDesc* hd = hptr<DocDesc>(c->h_docs);
+  uint64_t chunks = 0, total_len = 0, words_bound = 0, items_bound = 0;
+  for (uint32_t i = 0; i < ndocs; ++i) {
+    if (lens[i] >= (1ull << 32))
+      return fail(c, BSORT_E_TOO_LARGE, "document of 2^32 bytes or more (offsets are 32-bit)");
+    const uint64_t mis = (reinterpret_cast<uintptr_t>(d_in) + offs[i]) & 15u;
+    const uint64_t nch = lens[i] ? (mis + lens[i] + kChunk - 1) / kChunk : 0;
+    hd[i] = DocDesc{offs[i], lens[i], (uint32_t)chunks, (uint32_t)nch};
+    chunks += nch;
+    total_len += lens[i];
+    const uint64_t wb = lens[i] / 2 + 1;
+    words_bound += wb;
+    items_bound += (wb + kWordBlock - 1) / kWordBlock;
+  }
+  if (total_len >= (1ull << 32))
+    return fail(c, BSORT_E_TOO_LARGE, "2^32 bytes or more in one pass (positions are 32-bit)");
+  c->ml.set(ndocs);
+  const MetaLayout& ml = c->ml;
+  GROW(c->docs, sizeof(DocDesc) * ndocs, "document table");
+  GROW(c->sums, sizeof(TokSum) * (chunks + 1), "chunk summaries");
+  GROW(c->carry, sizeof(TokSum) * (chunks + 1), "chunk prefixes");
+  GROW(c->meta, ml.total, "meta");
+  GROW(c->starts, 4 * (words_bound + 1), "word starts");
+  GROW(c->letters, total_len + 16, "stripped letters");
+  GROW_HOST(c->h_meta, ml.total, "meta");
+  Meta* d_meta = dptr<Meta>(c->meta, ml.meta);
+  Meta* d_sticky = dptr<Meta>(c->sticky);
+  uint32_t* d_wbase = dptr<uint32_t>(c->meta, ml.wbase);
+  uint32_t* d_lbase = dptr<uint32_t>(c->meta, ml.lbase);
+  uint32_t* d_item0 = dptr<uint32_t>(c->meta, ml.item0);
+  uint32_t* d_hist = dptr<uint32_t>(c->meta, ml.hist);
+
+  CK(cudaMemcpyAsync(c->docs.p, hd, sizeof(DocDesc) * ndocs, cudaMemcpyHostToDevice, st), "copy document table");
+  CK(cudaMemsetAsync(c->meta.p, 0, ml.total, st), "clear meta");
+  const DocDesc* d_docs = dptr<DocDesc>(c->docs);
+  // Algorithmic bytes of K1/K2 are known only after the counts come back;
+  // they are added to the tags below once n and S are read.
+  if (chunks) {
+    LAUNCH(kTokSummary, 0, launch_tok_summary(d_in, d_docs, ndocs, (uint32_t)chunks, dptr<TokSum>(c->sums), st),
+           "K1a tok_summary");
+  }
+  LAUNCH(kTokScan, 0,
+         launch_tok_scan(dptr<TokSum>(c->sums), (uint32_t)chunks, d_docs, ndocs, dptr<TokSum>(c->carry), d_wbase,
+                         d_lbase, d_item0, dptr<uint32_t>(c->starts), d_meta, st),
+         "K1b tok_scan");
+  if (chunks) {
+    LAUNCH(kTokWrite, 0,
+           launch_tok_write(d_in, d_docs, ndocs, (uint32_t)chunks, dptr<TokSum>(c->carry), dptr<uint8_t>(c->letters),
+                            dptr<uint32_t>(c->starts), st),
+           "K1c tok_write");
+  }
+  const uint32_t hist_grid = (uint32_t)std::min<uint64_t>(items_bound, (uint64_t)c->sm_count * 8);
+  LAUNCH(kHistK, 0,
+         launch_hist(dptr<uint32_t>(c->starts), d_wbase, d_item0, ndocs, std::max(hist_grid, 1u), c->cfg.l_cap,
+                     d_hist, d_meta, st),
+         "K2 hist");
+  CK(cudaMemcpyAsync(c->h_meta.p, c->meta.p, ml.total, cudaMemcpyDeviceToHost, st), "read counts");
+  CK(cudaMemcpyAsync(c->h_sticky.p, c->sticky.p, sizeof(Meta), cudaMemcpyDeviceToHost, st), "read status");
+  CK(cudaStreamSynchronize(st), "wait for counts");
+
+  const Meta* hm = hptr<Meta>(c->h_meta, ml.meta);
+  const Meta* hs = hptr<Meta>(c->h_sticky);
+  const uint32_t* h_wbase = hptr<uint32_t>(c->h_meta, ml.wbase);
+  const uint32_t* h_lbase = hptr<uint32_t>(c->h_meta, ml.lbase);
+  const uint32_t* h_hist = hptr<uint32_t>(c->h_meta, ml.hist);
+  if (hs->err_timeout) {
+    CK(cudaMemsetAsync(d_sticky, 0, sizeof(Meta), st), "clear timeout flag");
+    return fail(c, BSORT_E_TIMEOUT, "a bounded device wait ran out in an earlier call on this context");
+  }
+  const uint32_t n_total = hm->n_total, s_total = hm->s_total, items = hm->items_total;
+  {
+    // algorithmic bytes of the launches above: K1a reads the input; K1b the
+    // chunk summaries; K1c reads the input and writes S and the word starts;
+    // K2 reads the word starts
+    const double N = (double)total_len, S = s_total, n4 = 4.0 * n_total;
+    const double per[4] = {N, 2.0 * sizeof(TokSum) * chunks, N + S + n4, n4};
+    const int kinds[4] = {kTokSummary, kTokScan, kTokWrite, kHistK};
+    for (int i = 0; i < 4; ++i) {
+      if (i != 1 && i != 3 && chunks == 0) continue;
+      c->kind_bytes[kinds[i]] += per[i];
+      for (auto it = c->recs.rbegin(); it != c->recs.rend(); ++it)
+        if (it->kind == kinds[i]) {
+          it->bytes += per[i];
+          break;
+        }
+    }
+  }
+
+  // ---- bucket layout: one segment per (document, length), ordered by class ----
+  c->lookupv.assign((size_t)ndocs * kHist, kNoSegment);
+  c->segv.clear();
+  for (uint32_t d = 0; d < ndocs; ++d)
+    if (h_hist[(size_t)d * kHist] != 0) c->doc_status[d] = BSORT_E_WORD_TOO_LONG;
+  ClassPlan cp[kNumClasses];
+  uint64_t key_words = 0;
+  uint32_t etile = 0;
+  for (int cl = 0; cl < kNumClasses; ++cl) {
+    const int W = width_of_class(cl);
+    const uint32_t T = (uint32_t)tile_of_width(W);
+    cp[cl].sbeg = (uint32_t)c->segv.size();
+    uint32_t tile = 0, passes = 0;
+    for (uint32_t d = 0; d < ndocs; ++d) {
+      if (c->doc_status[d] != BSORT_OK) continue;
+      const uint32_t* h = h_hist + (size_t)d * kHist;
+      uint32_t word_before = h_wbase[d] + d, byte_before = h_lbase[d];
+      for (uint32_t L = 1; L < kClassLmin[cl]; ++L) {
+        word_before += h[L];
+        byte_before += L * h[L];
+      }
+      for (uint32_t L = kClassLmin[cl]; L <= kClassLmax[cl]; ++L) {
+        const uint32_t n = h[L];
+        if (n) {
+          Segment s{};
+          s.key_off = key_words;
+          s.n = n;
+          s.L = L;
+          s.doc = d;
+          s.tile0 = tile;
+          s.etile0 = etile;
+          s.out_word = word_before;
+          s.stream_off = byte_before;
+          s.doc_stream0 = h_lbase[d];
+          const uint32_t p = merge_passes(n, T);
+          s.final_buf = p & 1u;
+          passes = std::max(passes, p);
+          const uint32_t nt = (n + T - 1) / T;
+          tile += nt;
+          etile += nt;
+          key_words += align_up((size_t)n * W, 16);
+          c->lookupv[(size_t)d * kHist + L] = (uint32_t)c->segv.size();
+          c->segv.push_back(s);
+        }
+        word_before += n;
+        byte_before += L * n;
+      }
+    }
+    cp[cl].send = (uint32_t)c->segv.size();
+    cp[cl].tiles = tile;
+    cp[cl].passes = passes;
+    for (uint32_t i = cp[cl].sbeg; i < cp[cl].send; ++i) cp[cl].key_bytes += 8ull * W * c->segv[i].n;
+  }
+  const uint32_t nseg = (uint32_t)c->segv.size();
+
+  // ---- upload the layout, size the key and output buffers ----
+  const size_t seg_bytes = sizeof(Segment) * std::max<size_t>(nseg, 1);
+  const size_t lookup_bytes = 4ull * ndocs * kHist;
+  GROW_HOST(c->h_plan, seg_bytes + lookup_bytes, "layout");
+  std::memcpy(c->h_plan.p, c->segv.data(), sizeof(Segment) * nseg);
+  std::memcpy(hptr<char>(c->h_plan, seg_bytes), c->lookupv.data(), lookup_bytes);
+  GROW(c->segs, seg_bytes, "segments");
+  GROW(c->lookup, lookup_bytes, "segment lookup");
+  GROW(c->cursor, 4ull * std::max<uint32_t>(nseg, 1), "segment cursors");
+  GROW(c->keysA, 8 * std::max<uint64_t>(key_words, 16), "keys");
+  GROW(c->keysB, 8 * std::max<uint64_t>(key_words, 16), "keys");
+  GROW(c->counts, 8ull * ndocs * kHist, "counts");
+  GROW(c->offsets, 4ull * ((uint64_t)n_total + ndocs), "offsets");
+  GROW(c->stream, (size_t)s_total + 16, "stream");
+  CK(cudaMemcpyAsync(c->segs.p, c->h_plan.p, sizeof(Segment) * nseg, cudaMemcpyHostToDevice, st), "copy segments");
+  CK(cudaMemcpyAsync(c->lookup.p, hptr<char>(c->h_plan, seg_bytes), lookup_bytes, cudaMemcpyHostToDevice, st),
+     "copy segment lookup");
+  CK(cudaMemsetAsync(c->cursor.p, 0, 4ull * std::max<uint32_t>(nseg, 1), st), "clear cursors");
+
+  const Segment* d_segs = dptr<Segment>(c->segs);
+  uint64_t* kA = dptr<uint64_t>(c->keysA);
+  uint64_t* kB = dptr<uint64_t>(c->keysB);
+  uint64_t key_bytes_all = 0;
+  for (int cl = 0; cl < kNumClasses; ++cl) key_bytes_all += cp[cl].key_bytes;
+  if (items) {
+    LAUNCH(kScatter, (double)s_total + 4.0 * n_total + key_bytes_all,
+           launch_scatter(dptr<uint32_t>(c->starts), dptr<uint8_t>(c->letters), d_wbase, d_item0, ndocs, items,
+                          dptr<uint32_t>(c->lookup), d_segs, dptr<uint32_t>(c->cursor), kA, st),
+           "K3 scatter");
+  }
+  const uint32_t grid_cap = (uint32_t)c->sm_count * 16;
+  for (int cl = 0; cl < kNumClasses; ++cl) {
+    if (cp[cl].tiles == 0) continue;
+    const int W = width_of_class(cl);
+    const uint32_t grid = std::min(cp[cl].tiles, grid_cap);
+    LAUNCH(kTileSort, 2.0 * cp[cl].key_bytes,
+           launch_tile_sort(W, d_segs, cp[cl].sbeg, cp[cl].send, cp[cl].tiles, grid, kA, d_sticky,
+                            c->cfg.wait_limit, st),
+           "K4 tile_sort");
+    for (uint32_t p = 0; p < cp[cl].passes; ++p) {
+      // only buckets longer than one run of this pass move
+      const uint64_t run = (uint64_t)tile_of_width(W) << p;
+      double moved = 0;
+      for (uint32_t i = cp[cl].sbeg; i < cp[cl].send; ++i)
+        if (c->segv[i].n > run) moved += 16.0 * W * c->segv[i].n;
+      LAUNCH(kMerge, moved,
+             launch_merge_pass(W, d_segs, cp[cl].sbeg, cp[cl].send, cp[cl].tiles, grid, p, (p & 1) ? kB : kA,
+                               (p & 1) ? kA : kB, st),
+             "K5 merge_pass");
+    }
+  }
+  const uint32_t emit_grid =
+      std::max<uint32_t>(1u, std::min<uint32_t>(std::max(etile, (ndocs * kHist + kSortThreads - 1) / kSortThreads),
+                                                grid_cap));
+  const double emit_bytes = (double)key_bytes_all + s_total +
+                            (c->cfg.want_offsets ? 4.0 * ((double)n_total + ndocs) : 0.0) + 8.0 * kHist * ndocs;
+  LAUNCH(kEmit, emit_bytes,
+         launch_emit(d_segs, nseg, etile, emit_grid, kA, kB, d_hist, d_wbase, d_lbase, ndocs, c->cfg.want_offsets,
+                     dptr<uint8_t>(c->stream), dptr<uint32_t>(c->offsets), dptr<uint64_t>(c->counts), st),
+         "K6 emit");
+  return BSORT_OK;
+}
+
+// Fills the scalar fields of document d's result from the host meta copy.
+void fill_scalars(const bsort_ctx* c, uint32_t d, bsort_result* r) {
+  const uint32_t* h_wbase = hptr<uint32_t>(c->h_meta, c->ml.wbase);
+  const uint32_t* h_lbase = hptr<uint32_t>(c->h_meta, c->ml.lbase);
+  const uint32_t* h = hptr<uint32_t>(c->h_meta, c->ml.hist) + (size_t)d * kHist;
+  uint32_t max_len = 0;
+  for (uint32_t L = 1; L < (uint32_t)kHist; ++L)
+    if (h[L]) max_len = L;
+  r->max_len = max_len;
+  r->n_words = h_wbase[d + 1] - h_wbase[d];
+  r->stream_bytes = h_lbase[d + 1] - h_lbase[d];
+  r->status = c->doc_status[d];
+}
+
+// Copies the outputs of the last run to pinned host memory (offsets and
+// stream land at the given bases of the host buffers) and builds the counts.
+bsort_status read_back(bsort_ctx* c, cudaStream_t st, size_t off_base, size_t stream_base, size_t counts_base) {
+  const uint32_t* h_wbase = hptr<uint32_t>(c->h_meta, c->ml.wbase);
+  const uint32_t* h_lbase = hptr<uint32_t>(c->h_meta, c->ml.lbase);
+  const uint32_t ndocs = c->ndocs;
+  const uint64_t n_off = (uint64_t)h_wbase[ndocs] + ndocs;
+  const uint64_t n_bytes = h_lbase[ndocs];
+  if (c->cfg.want_offsets && n_off)
+    CK(cudaMemcpyAsync(hptr<uint32_t>(c->h_offsets) + off_base, c->offsets.p, 4 * n_off, cudaMemcpyDeviceToHost, st),
+       "read offsets");
+  if (n_bytes)
+    CK(cudaMemcpyAsync(hptr<uint8_t>(c->h_stream) + stream_base, c->stream.p, n_bytes, cudaMemcpyDeviceToHost, st),
+       "read stream");
+  Meta* hs = hptr<Meta>(c->h_sticky);
+  CK(cudaMemcpyAsync(hs, c->sticky.p, sizeof(Meta), cudaMemcpyDeviceToHost, st), "read status");
+  uint64_t* hc = hptr<uint64_t>(c->h_counts) + counts_base;
+  const uint32_t* hh = hptr<uint32_t>(c->h_meta, c->ml.hist);
+  for (size_t i = 0; i < (size_t)ndocs * kHist; ++i) hc[i] = (i % kHist) ? hh[i] : 0;
+  CK(cudaStreamSynchronize(st), "wait for results");
+  if (hs->err_timeout) {
+    CK(cudaMemsetAsync(c->sticky.p, 0, sizeof(Meta), st), "clear timeout flag");
+    CK(cudaStreamSynchronize(st), "clear timeout flag");
+    return fail(c, BSORT_E_TIMEOUT, "a bounded device wait ran out");
+  }
+  return BSORT_OK;
+}
+
+struct Busy {
+  bsort_ctx* c;
+  explicit Busy(bsort_ctx* x) : c(x) { c->busy = true; }
+  ~Busy() { c->busy = false; }
+};
+
+bsort_status enter(bsort_ctx* c) {
+  if (c->busy) return fail(c, BSORT_E_BUSY, "context in use by another call");
+  c->err.clear();
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  return BSORT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void bsort_config_default(bsort_config* cfg) {
+  if (!cfg) return;
+  cfg->l_cap = kMaxLen;
+  cfg->want_offsets = 1;
+  cfg->device = -1;
+  cfg->profile = 0;
+  cfg->wait_limit = 0;
+}
+
+bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
+  if (!out) return BSORT_E_INVAL;
+  *out = nullptr;
+  bsort_config conf;
+  bsort_config_default(&conf);
+  if (cfg) conf = *cfg;
+  if (conf.l_cap == 0) conf.l_cap = kMaxLen;
+  if (conf.l_cap > (uint32_t)kMaxLen) return BSORT_E_INVAL;
+  if (conf.wait_limit == 0) conf.wait_limit = kDefaultWaitLimit;
+  conf.want_offsets = conf.want_offsets ? 1 : 0;
+  conf.profile = conf.profile ? 1 : 0;
+  int dev = conf.device;
+  if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return BSORT_E_CUDA;
+  }
+  if (cudaSetDevice(dev) != cudaSuccess) {
+    cudaGetLastError();
+    return BSORT_E_CUDA;
+  }
+  bsort_ctx* c = new (std::nothrow) bsort_ctx();
+  if (!c) return BSORT_E_NOMEM;
+  c->cfg = conf;
+  c->device = dev;
+  if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return BSORT_E_CUDA;
+  }
+  // the sticky status word starts cleared
+  if (grow(c, c->sticky, sizeof(Meta), "status") != BSORT_OK ||
+      grow_host(c, c->h_sticky, sizeof(Meta), "status") != BSORT_OK ||
+      cudaMemset(c->sticky.p, 0, sizeof(Meta)) != cudaSuccess) {
+    cudaGetLastError();
+    bsort_destroy(c);
+    return BSORT_E_NOMEM;
+  }
+  *out = c;
+  return BSORT_OK;
+}
+
+void bsort_destroy(bsort_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+  for (DevBuf* b : {&c->sticky, &c->in, &c->docs, &c->sums, &c->carry, &c->meta, &c->starts, &c->letters, &c->lookup, &c->segs,
+                    &c->cursor, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream})
+    if (b->p) cudaFree(b->p);
+  for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets, &c->h_stream})
+    if (b->p) cudaFreeHost(b->p);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+}
+
+const char* bsort_last_error(const bsort_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+bsort_status bsort_text(bsort_ctx* c, const uint8_t* bytes, size_t len, bsort_result* out) {
+  if (!c || !out || (!bytes && len)) return c ? fail(c, BSORT_E_INVAL, "null argument") : BSORT_E_INVAL;
+  std::memset(out, 0, sizeof(*out));
+  bsort_status s = enter(c);
+  if (s != BSORT_OK) return s;
+  Busy busy(c);
+  if ((uint64_t)len >= (1ull << 32)) return fail(c, BSORT_E_TOO_LARGE, "document of 2^32 bytes or more");
+  cudaStream_t st = c->own_stream;
+  GROW_HOST(c->h_in, len + 16, "input staging");
+  GROW(c->in, len + 16, "input");
+  if (len) {
+    std::memcpy(c->h_in.p, bytes, len);
+    CK(cudaMemcpyAsync(c->in.p, c->h_in.p, len, cudaMemcpyHostToDevice, st), "copy input");
+  }
+  const uint64_t off = 0, l = len;
+  s = run_path(c, dptr<uint8_t>(c->in), &off, &l, 1, st);
+  if (s != BSORT_OK) return s;
+  if (c->doc_status[0] != BSORT_OK) return fail(c, (bsort_status)c->doc_status[0], "a word is longer than l_cap");
+  const uint32_t* h_wbase = hptr<uint32_t>(c->h_meta, c->ml.wbase);
+  const uint32_t* h_lbase = hptr<uint32_t>(c->h_meta, c->ml.lbase);
+  GROW_HOST(c->h_offsets, 4ull * (h_wbase[1] + 1), "offsets");
+  GROW_HOST(c->h_stream, (size_t)h_lbase[1] + 16, "stream");
+  GROW_HOST(c->h_counts, 8ull * kHist, "counts");
+  s = read_back(c, st, 0, 0, 0);
+  if (s != BSORT_OK) return s;
+  fill_scalars(c, 0, out);
+  out->counts = hptr<uint64_t>(c->h_counts);
+  out->offsets = c->cfg.want_offsets ? hptr<uint32_t>(c->h_offsets) : nullptr;
+  out->stream = hptr<uint8_t>(c->h_stream);
+  return BSORT_OK;
+}
+
+bsort_status bsort_text_device(bsort_ctx* c, const uint8_t* d_bytes, size_t len, void* stream, bsort_result* out) {
+  if (!c || !out || (!d_bytes && len)) return c ? fail(c, BSORT_E_INVAL, "null argument") : BSORT_E_INVAL;
+  std::memset(out, 0, sizeof(*out));
+  bsort_status s = enter(c);
+  if (s != BSORT_OK) return s;
+  Busy busy(c);
+  if ((uint64_t)len >= (1ull << 32)) return fail(c, BSORT_E_TOO_LARGE, "document of 2^32 bytes or more");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint64_t off = 0, l = len;
+  // an empty document still needs a valid (never dereferenced) base pointer
+  const uint8_t* base = len ? d_bytes : dptr<uint8_t>(c->meta);
+  s = run_path(c, base, &off, &l, 1, st);
+  if (s != BSORT_OK) return s;
+  if (c->doc_status[0] != BSORT_OK) return fail(c, (bsort_status)c->doc_status[0], "a word is longer than l_cap");
+  fill_scalars(c, 0, out);
+  out->counts = dptr<uint64_t>(c->counts);
+  out->offsets = c->cfg.want_offsets ? dptr<uint32_t>(c->offsets) : nullptr;
+  out->stream = dptr<uint8_t>(c->stream);
+  return BSORT_OK;
+}
+
+bsort_status bsort_batch(bsort_ctx* c, const uint8_t* const* docs, const size_t* lens, size_t n, bsort_result* outs) {
+  if (!c || (n && (!docs || !lens || !outs))) return c ? fail(c, BSORT_E_INVAL, "null argument") : BSORT_E_INVAL;
+  for (size_t i = 0; i < n; ++i) std::memset(&outs[i], 0, sizeof(bsort_result));
+  if (n == 0) return BSORT_OK;
+  for (size_t i = 0; i < n; ++i)
+    if (!docs[i] && lens[i]) return fail(c, BSORT_E_INVAL, "null document with non-zero length");
+  if (n >= (1ull << 24)) return fail(c, BSORT_E_TOO_LARGE, "too many documents in one call");
+  bsort_status s = enter(c);
+  if (s != BSORT_OK) return s;
+  Busy busy(c);
+  cudaStream_t st = c->own_stream;
+  // Host output buffers for the whole call; documents run in groups of at
+  // most 1 GiB of input so that 32-bit positions suffice inside a group.
+  uint64_t total = 0, off_total = 0;
+  for (size_t i = 0; i < n; ++i) {
+    if ((uint64_t)lens[i] >= (1ull << 30)) return fail(c, BSORT_E_TOO_LARGE, "document of 1 GiB or more in a batch");
+    total += lens[i];
+    off_total += lens[i] / 2 + 2;
+  }
+  GROW_HOST(c->h_offsets, 4 * off_total, "offsets");
+  GROW_HOST(c->h_stream, total + 16, "stream");
+  GROW_HOST(c->h_counts, 8ull * kHist * n, "counts");
+  const uint64_t kGroupBytes = 1ull << 30;
+  std::vector<uint64_t> offs, ls;
+  std::vector<uint32_t> first_err;
+  size_t g0 = 0, off_base = 0, stream_base = 0;
+  bsort_status first = BSORT_OK;
+  while (g0 < n) {
+    size_t g1 = g0;
+    uint64_t bytes = 0;
+    while (g1 < n && (g1 == g0 || bytes + align_up(lens[g1], 16) <= kGroupBytes)) bytes += align_up(lens[g1++], 16);
+    const uint32_t nd = (uint32_t)(g1 - g0);
+    GROW_HOST(c->h_in, bytes + 16, "input staging");
+    GROW(c->in, bytes + 16, "input");
+    offs.resize(nd);
+    ls.resize(nd);
+    uint64_t pos = 0;
+    for (uint32_t i = 0; i < nd; ++i) {
+      offs[i] = pos;
+      ls[i] = lens[g0 + i];
+      if (ls[i]) std::memcpy(hptr<uint8_t>(c->h_in, pos), docs[g0 + i], ls[i]);
+      pos += align_up(ls[i], 16);
+    }
+    if (bytes) CK(cudaMemcpyAsync(c->in.p, c->h_in.p, bytes, cudaMemcpyHostToDevice, st), "copy input");
+    s = run_path(c, dptr<uint8_t>(c->in), offs.data(), ls.data(), nd, st);
+    if (s != BSORT_OK) return s;
+    s = read_back(c, st, off_base, stream_base, (size_t)g0 * kHist);
+    if (s != BSORT_OK) return s;
+    const uint32_t* h_wbase = hptr<uint32_t>(c->h_meta, c->ml.wbase);
+    const uint32_t* h_lbase = hptr<uint32_t>(c->h_meta, c->ml.lbase);
+    for (uint32_t i = 0; i < nd; ++i) {
+      bsort_result* r = &outs[g0 + i];
+      fill_scalars(c, i, r);
+      if (r->status != BSORT_OK) {
+        if (first == BSORT_OK) {
+          first = (bsort_status)r->status;
+          c->err = "document " + std::to_string(g0 + i) + ": a word is longer than l_cap";
+        }
+        const uint32_t st_keep = r->status;
+        std::memset(r, 0, sizeof(*r));
+        r->status = st_keep;
+        continue;
+      }
+      r->counts = hptr<uint64_t>(c->h_counts) + (size_t)(g0 + i) * kHist;
+      r->offsets = c->cfg.want_offsets ? hptr<uint32_t>(c->h_offsets) + off_base + h_wbase[i] + i : nullptr;
+      r->stream = hptr<uint8_t>(c->h_stream) + stream_base + h_lbase[i];
+    }
+    off_base += (size_t)h_wbase[nd] + nd;
+    stream_base += h_lbase[nd];
+    g0 = g1;
+  }
+  return first;
+}
+
+int bsort_profile_read(bsort_ctx* c, bsort_kernel_stat* out, int max) {
+  if (!c || (!out && max > 0) || max < 0) return -1;
+  if (cudaSetDevice(c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  double ms[kKinds] = {};
+  for (const ProfRec& r : c->recs) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    ms[r.kind] += t;
+  }
+  int k = 0;
+  for (int i = 0; i < kKinds && k < max; ++i) {
+    out[k].name = kKindName[i];
+    out[k].launches = c->kind_launches[i];
+    out[k].ms = ms[i];
+    out[k].bytes = c->kind_bytes[i];
+    ++k;
+  }
+  for (int i = 0; i < kKinds; ++i) {
+    c->kind_launches[i] = 0;
+    c->kind_bytes[i] = 0;
+  }
+  c->recs.clear();
+  c->ev_used = 0;
+  return k;
+}
+
+uint64_t bsort_launch_count(const bsort_ctx* c) { return c ? c->launches : 0; }
+
+void bsort_result_release(bsort_ctx* c, bsort_result* res) {
+  (void)c;
+  if (res) std::memset(res, 0, sizeof(*res));
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// Internal declarations shared by the CUDA translation units of libbsort.
+//
+// Data flow of one call (every kernel covers all documents of the call):
+//   K1a tok_summary   per 16 KiB chunk: letters, word starts, boundary state
+//   K1b tok_scan      one CTA: exclusive scan of the chunk summaries, per-
+//                     document bases of letters / words / word-blocks
+//   K1c tok_write     per chunk: the stripped letter stream S and the start
+//                     offset of every word in S
+//   K2  hist          per 1024-word block: length histogram per document
+//   -- host reads the histograms and lays out one segment per (doc, length)
+//   K3  scatter       per 1024-word block: each word packed into a big-endian
+//                     key of W u64 words, written to its segment
+//   K4  tile_sort     per tile: odd-even transposition sort
+//   K5  merge_pass    per tile and pass: merge-path merge of run pairs
+//   K6  emit          per tile: keys back to bytes, offsets, counts
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bsort {
+
+constexpr int kHist = 256;                  // histogram bins: lengths 0..255
+constexpr int kMaxLen = 255;                // longest word the key layout holds
+constexpr int kTokThreads = 256;            // K1 CTA size
+constexpr int kTokSeg = 64;                 // bytes per K1 thread
+constexpr int kChunk = kTokThreads * kTokSeg;  // bytes per K1 chunk (16 KiB)
+constexpr int kWordBlock = 1024;            // words per K2/K3 work item
+constexpr int kWordThreads = 256;
+constexpr int kSortThreads = 256;           // K4/K5/K6 CTA size
+constexpr int kNumClasses = 6;              // key widths W = 1, 2, 4, 8, 16, 32 u64 words
+constexpr uint32_t kNoSegment = 0xFFFFFFFFu;
+constexpr uint64_t kDefaultWaitLimit = 1ull << 26;
+
+// Key width class of a word of L letters: W = next power of two >= ceil(L/8).
+__host__ __device__ inline int width_of_len(uint32_t L) {
+  const uint32_t k = (L + 7) >> 3;
+  int w = 1;
+  while ((uint32_t)w < k) w <<= 1;
+  return w;
+}
+__host__ __device__ inline int class_of_width(int W) {
+  return W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : W == 16 ? 4 : 5;
+}
+__host__ __device__ inline int width_of_class(int c) { return 1 << c; }
+// Keys per thread of the sort kernels: a tile holds 2048 u64 words (16 KiB)
+// for W <= 8, and 256 keys for the wider classes.
+__host__ __device__ inline int kpt_of_width(int W) { return W >= 8 ? 1 : 8 / W; }
+__host__ __device__ inline int tile_of_width(int W) { return kSortThreads * kpt_of_width(W); }
+
+struct DocDesc {
+  uint64_t byte_off;  // first byte of the document, counted from the input base pointer
+  uint64_t len;       // bytes
+  uint32_t chunk0;    // first K1 chunk of the document
+  uint32_t nchunks;   // K1 chunks (0 for an empty document)
+};
+
+// Scan element of K1: what a span of bytes contributes to the word count.
+//   letters : letters in the span
+//   words   : word starts decided inside the span
+//   flags   : bit0 EV  the span has a letter or a whitespace byte
+//             bit1 WS  the span's last such byte is whitespace
+//             bit2 U   the span's first such byte is a letter, whose being a
+//                      word start depends on what precedes the span
+struct TokSum {
+  uint32_t letters;
+  uint32_t words;
+  uint32_t flags;
+};
+constexpr uint32_t kEv = 1u, kWs = 2u, kU = 4u;
+
+__host__ __device__ inline TokSum tok_combine(const TokSum& a, const TokSum& b) {
+  TokSum r;
+  r.letters = a.letters + b.letters;
+  const bool resolve = (b.flags & kU) && (a.flags & kEv) && (a.flags & kWs);
+  r.words = a.words + b.words + (resolve ? 1u : 0u);
+  const uint32_t ev = (a.flags | b.flags) & kEv;
+  const uint32_t ws = (b.flags & kEv) ? (b.flags & kWs) : (a.flags & kWs);
+  const uint32_t u = (a.flags & kEv) ? (a.flags & kU) : (b.flags & kU);
+  r.flags = ev | ws | u;
+  return r;
+}
+
+// Device-written summary that the host reads after K2.
+struct Meta {
+  uint32_t n_total;       // words over all documents
+  uint32_t s_total;       // letters over all documents
+  uint32_t items_total;   // K2/K3 work items
+  uint32_t err_long;      // words longer than l_cap
+  uint32_t err_timeout;   // bounded waits that ran out (sticky until read)
+  uint32_t pad[3];
+};
+
+// One (document, length) bucket.  The table is ordered by key class, then
+// document, then length; each class's tiles are numbered from 0 (tile0) and
+// all tiles are numbered across classes too (etile0).
+struct Segment {
+  uint64_t key_off;     // first key, in u64 words, in both key buffers
+  uint32_t n;           // words in the bucket
+  uint32_t L;           // their length
+  uint32_t doc;
+  uint32_t tile0;       // first tile within the class
+  uint32_t etile0;      // first tile across all classes
+  uint32_t out_word;    // index in offsets[] of the bucket's first word
+  uint32_t stream_off;  // byte offset in the output stream of the bucket's first word
+  uint32_t doc_stream0; // first stream byte of the document (offsets are per document)
+  uint32_t final_buf;   // 0: sorted keys end in buffer A, 1: in buffer B
+  uint32_t pad;
+};
+
+// -------- launchers (each returns the launch's cudaError_t) --------
+
+cudaError_t launch_tok_summary(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
+                               TokSum* sums, cudaStream_t st);
+cudaError_t launch_tok_scan(const TokSum* sums, uint32_t nchunks, const DocDesc* docs, uint32_t ndocs,
+                            TokSum* carry, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0,
+                            uint32_t* starts, Meta* meta, cudaStream_t st);
+cudaError_t launch_tok_write(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
+                             const TokSum* carry, uint8_t* letters, uint32_t* starts, cudaStream_t st);
+cudaError_t launch_hist(const uint32_t* starts, const uint32_t* doc_wbase, const uint32_t* doc_item0,
+                        uint32_t ndocs, uint32_t grid, uint32_t l_cap, uint32_t* hist, Meta* meta,
+                        cudaStream_t st);
+cudaError_t launch_scatter(const uint32_t* starts, const uint8_t* letters, const uint32_t* doc_wbase,
+                           const uint32_t* doc_item0, uint32_t ndocs, uint32_t items, const uint32_t* seg_lookup,
+                           const Segment* segs, uint32_t* cursor, uint64_t* keys, cudaStream_t st);
+cudaError_t launch_tile_sort(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
+                             uint32_t grid, uint64_t* keys, Meta* meta, uint64_t wait_limit, cudaStream_t st);
+cudaError_t launch_merge_pass(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
+                              uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st);
+cudaError_t launch_emit(const Segment* segs, uint32_t nseg, uint32_t tiles, uint32_t grid, const uint64_t* keysA,
+                        const uint64_t* keysB, const uint32_t* hist, const uint32_t* doc_wbase,
+                        const uint32_t* doc_lbase, uint32_t ndocs, int want_offsets, uint8_t* stream,
+                        uint32_t* offsets, uint64_t* counts, cudaStream_t st);
+
+}  // namespace bsort

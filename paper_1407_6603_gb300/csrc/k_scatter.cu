@@ -1,0 +1,169 @@
+// K3 (scatter + pack) and K6 (emit).
+//
+// K3 is phase 2 of the paper's method (Section II; Section III step 3): each
+// word goes to the sub-array of its length.  The paper's chosen layout is a
+// 3-D char array, one plane per length (Section III "Approach Second"); here
+// each (document, length) bucket is a contiguous array of packed keys, W u64
+// words per key, big-endian so that integer order is ASCII order.  A CTA
+// takes 1024 words of one document, ranks them per length in shared memory
+// and reserves each length's slots with one atomic per length, so the slots
+// of a bucket come out in no fixed order (the sort that follows makes the
+// result unique anyway).
+//
+// K6 writes the result: the buckets in ascending length, each word unpacked
+// back to its L letters, the per-word offsets and the per-length counts.
+#include "bsort_dev.cuh"
+
+namespace bsort {
+namespace {
+
+__device__ __forceinline__ uint32_t doc_of_item(const uint32_t* doc_item0, uint32_t ndocs, uint32_t it) {
+  uint32_t lo = 0, hi = ndocs - 1;  // last document with doc_item0 <= it
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (doc_item0[mid] <= it)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int kWordsPerThread = kWordBlock / kWordThreads;
+
+__global__ void __launch_bounds__(kWordThreads) k_scatter(const uint32_t* __restrict__ starts,
+                                                          const uint8_t* __restrict__ letters,
+                                                          const uint32_t* __restrict__ doc_wbase,
+                                                          const uint32_t* __restrict__ doc_item0, uint32_t ndocs,
+                                                          uint32_t items, const uint32_t* __restrict__ seg_lookup,
+                                                          const Segment* __restrict__ segs,
+                                                          uint32_t* __restrict__ cursor, uint64_t* __restrict__ keys) {
+  __shared__ uint32_t cnt[kHist];
+  __shared__ uint32_t base[kHist];
+  __shared__ uint32_t s_doc;
+  const int t = threadIdx.x;
+  for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
+    for (int i = t; i < kHist; i += kWordThreads) cnt[i] = 0;
+    if (t == 0) s_doc = doc_of_item(doc_item0, ndocs, it);
+    __syncthreads();
+    const uint32_t d = s_doc;
+    const uint32_t* lookup = seg_lookup + (size_t)d * kHist;
+    const uint32_t w0 = doc_wbase[d] + (it - doc_item0[d]) * kWordBlock;
+    const uint32_t w1 = min(w0 + kWordBlock, doc_wbase[d + 1]);
+    uint32_t s0[kWordsPerThread], len[kWordsPerThread], rank[kWordsPerThread];
+#pragma unroll
+    for (int k = 0; k < kWordsPerThread; ++k) {
+      const uint32_t wi = w0 + t + k * kWordThreads;
+      len[k] = 0;
+      if (wi < w1) {
+        s0[k] = starts[wi];
+        const uint32_t L = starts[wi + 1] - s0[k];
+        if (L <= (uint32_t)kMaxLen && lookup[L] != kNoSegment) {
+          len[k] = L;
+          rank[k] = atomicAdd(&cnt[L], 1u);
+        }
+      }
+    }
+    __syncthreads();
+    for (int L = t; L < kHist; L += kWordThreads)
+      if (cnt[L]) base[L] = atomicAdd(&cursor[lookup[L]], cnt[L]);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kWordsPerThread; ++k) {
+      const uint32_t L = len[k];
+      if (L == 0) continue;
+      const Segment& sg = segs[lookup[L]];
+      const int W = width_of_len(L);
+      uint64_t* out = keys + sg.key_off + (size_t)(base[L] + rank[k]) * W;
+      const uint8_t* src = letters + s0[k];
+      for (int q = 0; q < W; ++q) {
+        uint64_t v = 0;
+        const uint32_t b0 = (uint32_t)q * 8;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const uint32_t i = b0 + b;
+          const uint64_t byte = i < L ? (uint64_t)src[i] : 0ull;
+          v |= byte << (56 - 8 * b);
+        }
+        out[q] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ uint32_t find_segment_e(const Segment* segs, uint32_t nseg, uint32_t it) {
+  uint32_t lo = 0, hi = nseg - 1;  // last segment with etile0 <= it
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (segs[mid].etile0 <= it)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_emit(const Segment* __restrict__ segs, uint32_t nseg,
+                                                       uint32_t tiles, const uint64_t* __restrict__ keysA,
+                                                       const uint64_t* __restrict__ keysB,
+                                                       const uint32_t* __restrict__ hist,
+                                                       const uint32_t* __restrict__ doc_wbase,
+                                                       const uint32_t* __restrict__ doc_lbase, uint32_t ndocs,
+                                                       int want_offsets, uint8_t* __restrict__ stream,
+                                                       uint32_t* __restrict__ offsets, uint64_t* __restrict__ counts) {
+  // per-document counts (bin 0 is always 0 in a result) and the closing offset
+  const uint32_t gsz = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ndocs * kHist; i += gsz) {
+    const uint32_t d = i / kHist, L = i % kHist;
+    counts[i] = L ? hist[i] : 0ull;
+    if (L == 0 && want_offsets) offsets[doc_wbase[d + 1] + d] = doc_lbase[d + 1] - doc_lbase[d];
+  }
+  __shared__ uint32_t s_seg;
+  for (uint32_t it = blockIdx.x; it < tiles; it += gridDim.x) {
+    if (threadIdx.x == 0) s_seg = find_segment_e(segs, nseg, it);
+    __syncthreads();
+    const Segment sg = segs[s_seg];
+    __syncthreads();
+    const uint32_t L = sg.L;
+    const int W = width_of_len(L);
+    const uint32_t T = (uint32_t)tile_of_width(W);
+    const uint32_t j0 = (it - sg.etile0) * T;
+    const uint32_t cnt = min(T, sg.n - j0);
+    const uint64_t* src = (sg.final_buf ? keysB : keysA) + sg.key_off;
+    for (uint32_t j = threadIdx.x; j < cnt; j += kSortThreads) {
+      const uint32_t k = j0 + j;
+      const uint64_t* kp = src + (size_t)k * W;
+      uint8_t* dst = stream + sg.stream_off + (size_t)k * L;
+      uint64_t v = 0;
+      for (uint32_t b = 0; b < L; ++b) {
+        if ((b & 7) == 0) v = kp[b >> 3];
+        dst[b] = (uint8_t)(v >> (56 - 8 * (b & 7)));
+      }
+      if (want_offsets) offsets[sg.out_word + k] = sg.stream_off - sg.doc_stream0 + k * L;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_scatter(const uint32_t* starts, const uint8_t* letters, const uint32_t* doc_wbase,
+                           const uint32_t* doc_item0, uint32_t ndocs, uint32_t items, const uint32_t* seg_lookup,
+                           const Segment* segs, uint32_t* cursor, uint64_t* keys, cudaStream_t st) {
+  if (items == 0) return cudaSuccess;
+  k_scatter<<<items, kWordThreads, 0, st>>>(starts, letters, doc_wbase, doc_item0, ndocs, items, seg_lookup, segs,
+                                            cursor, keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const Segment* segs, uint32_t nseg, uint32_t tiles, uint32_t grid, const uint64_t* keysA,
+                        const uint64_t* keysB, const uint32_t* hist, const uint32_t* doc_wbase,
+                        const uint32_t* doc_lbase, uint32_t ndocs, int want_offsets, uint8_t* stream,
+                        uint32_t* offsets, uint64_t* counts, cudaStream_t st) {
+  if (grid == 0) return cudaSuccess;
+  k_emit<<<grid, kSortThreads, 0, st>>>(nseg ? segs : nullptr, nseg, nseg ? tiles : 0u, keysA, keysB, hist,
+                                        doc_wbase, doc_lbase, ndocs, want_offsets, stream, offsets, counts);
+  return cudaGetLastError();
+}
+
+}  // namespace bsort

@@ -1,0 +1,226 @@
+"""Parity of the CUDA path with the CPU oracle, byte for byte.
+
+Every result of the path is an exact permutation of bytes with a unique
+answer, so the tolerance is zero: counts, offsets and the sorted stream must
+equal the oracle's exactly.  Inputs are seeded: the paper-sized synthetic
+documents, and adversarial cases for each kernel (chunk and tile boundaries,
+ragged tails, every word length 1..255, key widths 1..32 u64 words, giant
+single buckets, all-equal keys, unaligned device pointers, empty inputs).
+"""
+import random
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def assert_same(got, exp, label=""):
+    assert got.n_words == exp["n_words"], label
+    assert got.max_len == exp["max_len"], label
+    assert got.stream_bytes == exp["stream_bytes"], label
+    assert np.array_equal(got.counts, exp["counts"]), label
+    assert np.array_equal(got.offsets, exp["offsets"]), label
+    assert np.array_equal(got.stream, exp["stream"]), label
+
+
+def assert_same_dev(dev, exp, label=""):
+    assert dev["n_words"] == exp["n_words"] and dev["max_len"] == exp["max_len"], label
+    assert np.array_equal(dev["counts"].cpu().numpy().astype(np.uint64), exp["counts"]), label
+    assert np.array_equal(dev["offsets"].cpu().numpy().astype(np.uint32), exp["offsets"]), label
+    assert np.array_equal(dev["stream"].cpu().numpy(), exp["stream"]), label
+
+
+@pytest.fixture(scope="module")
+def ctx(bsort_gpu):
+    c = bsort_gpu.Context()
+    yield c
+    c.close()
+
+
+HAND = [
+    b"Hello, world! The cat-sat\non a mat; The end.",
+    b"", b"!!! ... ---", b" \t\n\x0b\x0c\r ", b"a\tb\r\nc", b"\xc3\xa9t\xc3\xa9", b"don't can't",
+    b"abc123 456", b"a\x00b", b"Zebra apple", b"b a b a", b"zz y xxx", b"q", b"x" * 255,
+]
+
+
+@pytest.mark.parametrize("i", range(len(HAND)))
+def test_hand_cases(ctx, oracle_mod, i):
+    data = HAND[i]
+    assert_same(ctx.text(data), oracle_mod.bubble(data), repr(data))
+
+
+def test_hand_example_values(ctx):
+    r = ctx.text(b"Hello, world! The cat-sat\non a mat; The end.")
+    assert r.counts.tolist() == [0, 1, 1, 4, 0, 2, 1]
+    assert r.stream.tobytes() == b"aonTheTheendmatHelloworldcatsat"
+    assert r.offsets.tolist() == [0, 1, 3, 6, 9, 12, 15, 20, 25, 31]
+
+
+@pytest.mark.parametrize("name", ["plain_190k", "plain_1m38"])
+def test_paper_sized_documents(ctx, oracle_mod, synth_mod, name):
+    import torch
+
+    data = synth_mod.plain(name)
+    exp = oracle_mod.stable(data, nthreads=8)
+    assert_same(ctx.text(data), exp, name)
+    assert_same_dev(ctx.text_device(torch.from_numpy(data).cuda()), exp, name)
+    torch.cuda.synchronize()
+    if name == "plain_190k":
+        assert_same(ctx.text(data), oracle_mod.bubble(data, nthreads=8), name + " vs bubble")
+
+
+def test_repeat_calls_identical(ctx, synth_mod):
+    data = synth_mod.plain("plain_190k")
+    a = ctx.text(data)
+    b = ctx.text(data)
+    assert np.array_equal(a.stream, b.stream) and np.array_equal(a.offsets, b.offsets)
+
+
+def _fuzz_bytes(rng: random.Random, n: int) -> bytes:
+    pool = (b"abcdefghijklmnopqrstuvwxyzABCDEFGHIJKLMNOPQRSTUVWXYZ" * 4 + b" \t\n\x0b\x0c\r" * 3
+            + b".,;:?!\"'-0123456789" + bytes(range(128, 256, 5)) + b"\x00\x7f")
+    return bytes(rng.choice(pool) for _ in range(n))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_fuzz_random_bytes(ctx, oracle_mod, seed):
+    rng = random.Random(seed)
+    data = _fuzz_bytes(rng, rng.choice([1, 15, 16, 17, 1000, 16383, 16384, 16385, 50_000, 200_000]))
+    assert_same(ctx.text(data), oracle_mod.stable(data), f"seed {seed}")
+
+
+def test_every_length_and_key_width(ctx, oracle_mod):
+    # words of every length 1..255: all six key widths (1, 2, 4, 8, 16, 32 u64)
+    # and the 8/9, 16/17, 32/33, 64/65, 128/129 boundaries
+    rng = random.Random(3)
+    words = []
+    for L in range(1, 256):
+        for _ in range(rng.randint(1, 40)):
+            words.append(bytes(rng.choice(b"abcXYZ") for _ in range(L)))
+    rng.shuffle(words)
+    data = b" ".join(words)
+    assert_same(ctx.text(data), oracle_mod.stable(data, nthreads=8))
+
+
+def test_long_words_share_prefixes(ctx, oracle_mod):
+    # multi-word keys that agree on the first words and differ late
+    rng = random.Random(4)
+    words = []
+    for L in (9, 16, 17, 24, 31, 32, 33, 40, 64, 65, 100, 128, 129, 200, 255):
+        stem = bytes(rng.choice(b"ab") for _ in range(L - 1))
+        for _ in range(300):
+            words.append(stem + bytes([rng.choice(b"abAB")]))
+            words.append(bytes(rng.choice(b"ab") for _ in range(L)))
+    rng.shuffle(words)
+    data = b"\n".join(words)
+    assert_same(ctx.text(data), oracle_mod.stable(data, nthreads=8))
+
+
+def test_giant_single_bucket(ctx, oracle_mod):
+    # 600k five-letter words: one bucket spanning ~300 tiles and 9 merge passes
+    rng = np.random.default_rng(5)
+    letters = rng.integers(97, 123, size=(600_000, 5), dtype=np.uint8)
+    data = np.concatenate([letters, np.full((600_000, 1), 32, np.uint8)], axis=1).reshape(-1)
+    assert_same(ctx.text(data), oracle_mod.stable(data, nthreads=8))
+
+
+def test_all_equal_keys_and_reverse_order(ctx, oracle_mod):
+    data = b" ".join([b"same"] * 100_000 + [b"%04d" % 0 + b"z"] + [bytes([122 - i % 26]) * 3 for i in range(50_000)])
+    assert_same(ctx.text(data), oracle_mod.stable(data))
+
+
+def test_words_straddling_chunks(ctx, oracle_mod):
+    # punctuation runs inside words that cross 16 KiB chunk boundaries
+    parts = [b"a" + b"-" * 40_000 + b"b", b"  ", b"xy" + b"." * 16_383 + b"z", b" ", b"q" * 200 + b"'" * 5 + b"r" * 55]
+    data = b"\n".join([b"".join(parts)] * 3)
+    exp = oracle_mod.stable(data)
+    assert exp["max_len"] == 255
+    assert_same(ctx.text(data), exp)
+    assert oracle_mod.tokenize(data)[0] == b"ab"
+
+
+@pytest.mark.parametrize("offset", [0, 1, 3, 7, 8, 13, 15])
+def test_unaligned_device_input(ctx, oracle_mod, synth_mod, offset):
+    import torch
+
+    data = synth_mod.text(synth_mod.TAG_FUZZ, 100 + offset, 70_001 + offset, 900, 3.7, 20)
+    buf = torch.zeros(data.size + 64, dtype=torch.uint8, device="cuda")
+    buf[offset:offset + data.size] = torch.from_numpy(data).cuda()
+    buf[:offset] = ord("z")  # bytes before and after the document must not leak in
+    buf[offset + data.size:] = ord("z")
+    dev = ctx.text_device(buf[offset:offset + data.size])
+    torch.cuda.synchronize()
+    assert_same_dev(dev, oracle_mod.stable(data), f"offset {offset}")
+
+
+def test_empty_device_input(ctx):
+    import torch
+
+    dev = ctx.text_device(torch.zeros(0, dtype=torch.uint8, device="cuda"))
+    torch.cuda.synchronize()
+    assert dev["n_words"] == 0 and dev["max_len"] == 0
+    assert dev["counts"].cpu().tolist() == [0] and dev["offsets"].cpu().tolist() == [0]
+
+
+def test_word_too_long(bsort_gpu):
+    with bsort_gpu.Context(l_cap=10) as c:
+        assert c.text(b"abcdefghij ok").n_words == 2
+        with pytest.raises(bsort_gpu.BsortError) as e:
+            c.text(b"ok abcdefghijk ok")
+        assert e.value.status == bsort_gpu.BSORT_E_WORD_TOO_LONG
+        # the context stays usable
+        assert c.text(b"b a").stream.tobytes() == b"ab"
+    with bsort_gpu.Context() as c:
+        with pytest.raises(bsort_gpu.BsortError) as e:
+            c.text(b"x" * 256)
+        assert e.value.status == bsort_gpu.BSORT_E_WORD_TOO_LONG
+
+
+def test_no_offsets_mode(bsort_gpu, oracle_mod, synth_mod):
+    data = synth_mod.plain("plain_190k")
+    with bsort_gpu.Context(want_offsets=False) as c:
+        r = c.text(data)
+    exp = oracle_mod.stable(data)
+    assert r.offsets is None
+    assert np.array_equal(r.stream, exp["stream"]) and np.array_equal(r.counts, exp["counts"])
+
+
+def test_batch_equals_single(ctx, oracle_mod, synth_mod):
+    rng = random.Random(9)
+    docs = [synth_mod.batch_doc(*s) for s in synth_mod.batch_shapes(40)]
+    docs[3] = np.zeros(0, np.uint8)
+    docs[7] = np.frombuffer(b"  ..  ", np.uint8)
+    docs[11] = np.frombuffer(_fuzz_bytes(rng, 5000), np.uint8)
+    docs[12] = np.frombuffer(b"word", np.uint8)
+    st, rs = ctx.batch(docs)
+    assert st == 0, ctx.last_error()
+    for i, d in enumerate(docs):
+        exp = oracle_mod.stable(d, nthreads=8)
+        assert_same(rs[i], exp, f"doc {i}")
+        assert_same(ctx.text(d), exp, f"doc {i} alone")
+
+
+def test_batch_reports_failing_document(bsort_gpu, oracle_mod):
+    docs = [b"fine words here", b"x" * 30, b"also fine"]
+    with bsort_gpu.Context(l_cap=20) as c:
+        st, rs = c.batch(docs)
+    assert st == bsort_gpu.BSORT_E_WORD_TOO_LONG
+    assert [r.status for r in rs] == [0, bsort_gpu.BSORT_E_WORD_TOO_LONG, 0]
+    assert_same(rs[0], oracle_mod.stable(docs[0]))
+    assert_same(rs[2], oracle_mod.stable(docs[2]))
+
+
+@pytest.mark.slow
+def test_plain_256m_full(ctx, oracle_mod, synth_mod):
+    """The 256 MiB workload through the device entry point, as the benchmark
+    runs it, against the oracle's stable_sort path on every byte."""
+    import torch
+
+    data = synth_mod.plain("plain_256m")
+    dev = ctx.text_device(torch.from_numpy(data).cuda())
+    torch.cuda.synchronize()
+    exp = oracle_mod.stable(data, nthreads=oracle_mod.max_threads())
+    assert_same_dev(dev, exp, "plain_256m")
+    assert exp["max_len"] > 16  # multi-word keys are exercised
