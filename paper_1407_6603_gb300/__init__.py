@@ -199,7 +199,7 @@ def _host_result(r: bsort_result, want_offsets: bool) -> Result:
     ml = int(r.max_len)
 
     def arr(ptr, ctype, count, dtype):
-        if count == 0:
+        if count == 0 or not ptr:  # empty, or a failed document (zeroed result)
             return np.zeros(0, dtype=dtype)
         return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctype)), shape=(count,)).copy()
 
