@@ -57,6 +57,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", default="plain_1m38", choices=["plain_190k", "plain_1m38", "plain_256m"])
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--prefix-bytes", type=int, default=None,
+                   help="use only the first B bytes of the workload (profiling captures on smaller cases)")
     return p.parse_args(argv)
 
 
@@ -264,6 +266,8 @@ def run_ours(args) -> None:
     dev = torch.device("cuda", local_rank)
     bs.load()
     data = synth.plain(args.workload)
+    if args.prefix_bytes:
+        data = data[: args.prefix_bytes]
     nbytes = int(data.size)
     d_in = torch.from_numpy(data).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -344,7 +348,8 @@ def run_ours(args) -> None:
         "warmup": max(args.warmup, 3), "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded text generator shaped like the paper's Hamlet files)",
-        "config": {"workload": args.workload, "bytes": nbytes, "words": n_words, "stream_bytes": s_bytes,
+        "config": {"workload": args.workload + (f" (first {nbytes} B)" if args.prefix_bytes else ""),
+                   "bytes": nbytes, "words": n_words, "stream_bytes": s_bytes,
                    "entry": "bsort_text_device (input resident in HBM)", "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps by writing a 256 MiB buffer"},
         "words_per_s": agg["words_per_s"],
