@@ -154,6 +154,44 @@ int bsort_profile_read(bsort_ctx* ctx, bsort_kernel_stat* out, int max);
 /* Kernel launches made by this context since it was created. */
 uint64_t bsort_launch_count(const bsort_ctx* ctx);
 
+/*
+ * Strip + tokenize without allocating (the paper has no counterpart: this is
+ * an entry point for callers that cannot call cudaMalloc, such as code running
+ * while a CUDA graph is being captured, plugins whose host framework owns all
+ * device memory, or processes that must not grow their device footprint).
+ *
+ * Runs phase 1 of the method (strip the special characters, split the words)
+ * on one document in device memory, as one kernel, and writes:
+ *   d_letters[0 .. L)  the document's letters in input order (capacity >= len bytes),
+ *   d_starts[0 .. n]   d_starts[w] = offset in d_letters of word w's first letter,
+ *                      d_starts[n] = L (capacity >= len/2 + 2 entries),
+ *   d_totals[0..2]     n (words), L (letters), and a status: 0, or BSORT_E_TIMEOUT
+ *                      when a bounded device wait ran out (outputs then invalid).
+ * Every pointer is a device pointer; d_bytes may have any alignment.  The work
+ * is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream) and
+ * the outputs are complete when the stream reaches that point; the call does
+ * not wait for it.
+ *
+ * Allocation: none.  The call makes no cudaMalloc, cudaFree or other
+ * allocating call.  Its scratch, one 32-byte record per 16 KiB of input, lives
+ * in a 131,328-byte array inside the library that every GPU which loads the
+ * library holds until the process exits.  Hence the limit: len must be at most
+ * 64 MiB - 16 bytes (67,108,848); a longer document returns BSORT_E_TOO_LARGE
+ * before any GPU work.  The first call on each device looks up the array's
+ * device address (with that device current), so make that first call before
+ * any stream capture.
+ *
+ * Sharing: every call on a device uses the same array, and it keeps the last
+ * call's contents (each call clears what must start at zero).  Calls whose
+ * work overlaps on the GPU (for example on two streams) race on it and give
+ * wrong results: order them on one stream or synchronise between them.
+ *
+ * Errors: BSORT_E_INVAL (a NULL pointer where one is required),
+ * BSORT_E_TOO_LARGE, BSORT_E_CUDA (no current device, or a launch failed).
+ */
+bsort_status bsort_strip_noalloc(const uint8_t* d_bytes, size_t len, void* stream, uint8_t* d_letters,
+                                 uint32_t* d_starts, uint32_t* d_totals);
+
 /* Marks a result's buffers as no longer needed and zeroes *res.  The memory
  * itself stays with the context for reuse. */
 void bsort_result_release(bsort_ctx* ctx, bsort_result* res);

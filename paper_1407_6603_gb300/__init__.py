@@ -96,6 +96,9 @@ def load(path: str | None = None):
     lib.bsort_profile_read.argtypes = [ctx_p, ctypes.POINTER(bsort_kernel_stat), ctypes.c_int]
     lib.bsort_launch_count.restype = ctypes.c_uint64
     lib.bsort_launch_count.argtypes = [ctx_p]
+    lib.bsort_strip_noalloc.restype = ctypes.c_int
+    lib.bsort_strip_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]
     if path is None:
         _lib = lib
     return lib
@@ -174,6 +177,17 @@ def bsort_profile_read(h) -> dict:
 
 def bsort_launch_count(h) -> int:
     return int(load().bsort_launch_count(h))
+
+
+NOALLOC_MAX_BYTES = (64 << 20) - 16
+
+
+def bsort_strip_noalloc(ptr: int, nbytes: int, stream: int, letters_ptr: int, starts_ptr: int,
+                        totals_ptr: int) -> int:
+    """Strip + tokenize one device document into caller-provided device
+    buffers without allocating; returns the bsort_status of the call."""
+    return int(load().bsort_strip_noalloc(ptr or None, nbytes, stream or None, letters_ptr or None,
+                                          starts_ptr or None, totals_ptr or None))
 
 
 # ---- convenience layer ----

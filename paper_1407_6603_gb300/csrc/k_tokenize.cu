@@ -20,100 +20,10 @@
 // whitespace byte, so ((T + (Ws << 1)) ^ T) & Letters marks exactly the
 // letters whose previous event is whitespace.
 #include "bsort_dev.cuh"
+#include "tok_common.cuh"
 
 namespace bsort {
 namespace {
-
-constexpr uint32_t kFull = 0xFFFFFFFFu;
-
-__device__ __forceinline__ uint32_t pack4(uint32_t bytemask) {
-  // bytes 0x00/0xFF -> 4 bits, bit i = byte i
-  return (((bytemask & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
-}
-
-// Letter and whitespace bit masks of 64 bytes held as 16 little-endian words.
-__device__ __forceinline__ void classify64(const uint32_t (&w)[16], uint64_t& letters, uint64_t& spaces) {
-  uint64_t lm = 0, sm = 0;
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const uint32_t x = w[i];
-    const uint32_t lower = x | 0x20202020u;
-    const uint32_t is_letter = __vcmpltu4(__vsub4(lower, 0x61616161u), 0x1a1a1a1au);
-    const uint32_t is_space = __vcmpeq4(x, 0x20202020u) | __vcmpltu4(__vsub4(x, 0x09090909u), 0x05050505u);
-    lm |= (uint64_t)pack4(is_letter) << (4 * i);
-    sm |= (uint64_t)pack4(is_space) << (4 * i);
-  }
-  letters = lm;
-  spaces = sm;
-}
-
-// Letters whose previous letter-or-space byte is a space.  `ws_before` says
-// whether the last such byte before these 64 is a space.
-__device__ __forceinline__ uint64_t start_mask(uint64_t letters, uint64_t spaces, bool ws_before) {
-  const uint64_t transparent = ~(letters | spaces);
-  const uint64_t seeds = (spaces << 1) | (ws_before ? 1ull : 0ull);
-  return ((transparent + seeds) ^ transparent) & letters;
-}
-
-__device__ __forceinline__ TokSum seg_summary(uint64_t letters, uint64_t spaces, bool doc_start) {
-  TokSum s;
-  s.letters = __popcll(letters);
-  s.words = __popcll(start_mask(letters, spaces, doc_start));
-  const uint64_t ev = letters | spaces;
-  uint32_t flags = 0;
-  if (ev) {
-    flags |= kEv;
-    const int hi = 63 - __clzll(ev);
-    if ((spaces >> hi) & 1ull) flags |= kWs;
-    const int lo = __ffsll(ev) - 1;
-    if (!doc_start && ((letters >> lo) & 1ull)) flags |= kU;
-  } else if (doc_start) {
-    flags = kEv | kWs;
-  }
-  s.flags = flags;
-  return s;
-}
-
-__device__ __forceinline__ TokSum shfl_up_sum(const TokSum& v, int off) {
-  TokSum r;
-  r.letters = __shfl_up_sync(kFull, v.letters, off);
-  r.words = __shfl_up_sync(kFull, v.words, off);
-  r.flags = __shfl_up_sync(kFull, v.flags, off);
-  return r;
-}
-
-__device__ __forceinline__ TokSum warp_inclusive(TokSum v) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const TokSum u = shfl_up_sum(v, off);
-    if (lane >= off) v = tok_combine(u, v);
-  }
-  return v;
-}
-
-// Exclusive scan over the CTA (blockDim.x == kTokThreads).  Returns this
-// thread's exclusive prefix and the CTA total.
-__device__ TokSum block_exclusive(const TokSum v, TokSum* total) {
-  __shared__ TokSum warp_tot[kTokThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const TokSum inc = warp_inclusive(v);
-  if (lane == 31) warp_tot[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    TokSum w = {0, 0, 0};
-    if (lane < kTokThreads / 32) w = warp_tot[lane];
-    w = warp_inclusive(w);
-    if (lane < kTokThreads / 32) warp_tot[lane] = w;
-  }
-  __syncthreads();
-  TokSum ex = shfl_up_sum(inc, 1);
-  if (lane == 0) ex = TokSum{0, 0, 0};
-  if (warp > 0) ex = tok_combine(warp_tot[warp - 1], ex);
-  *total = warp_tot[kTokThreads / 32 - 1];
-  __syncthreads();
-  return ex;
-}
 
 __device__ __forceinline__ uint32_t find_doc_of_chunk(const DocDesc* docs, uint32_t ndocs, uint32_t c) {
   // last document whose chunk0 <= c among documents that have chunks
@@ -163,17 +73,6 @@ __device__ bool load_chunk(const uint8_t* in, const DocDesc* docs, uint32_t ndoc
   const bool doc_first = c == d.chunk0;
   __syncthreads();
   return doc_first;
-}
-
-__device__ __forceinline__ void thread_words(const uint4* buf, uint32_t (&w)[16]) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const uint4 v = buf[threadIdx.x * 4 + i];
-    w[4 * i + 0] = v.x;
-    w[4 * i + 1] = v.y;
-    w[4 * i + 2] = v.z;
-    w[4 * i + 3] = v.w;
-  }
 }
 
 // K1a: one summary per chunk.
