@@ -34,10 +34,6 @@ struct HostBuf {
   size_t cap = 0;
 };
 
-// Key widths of the classes and the lengths each one holds.
-constexpr uint32_t kClassLmin[kNumClasses] = {1, 9, 17, 33, 65, 129};
-constexpr uint32_t kClassLmax[kNumClasses] = {8, 16, 32, 64, 128, 255};
-
 uint32_t merge_passes(uint64_t n, uint64_t tile) {
   uint32_t p = 0;
   while ((tile << p) < n) ++p;
@@ -59,11 +55,6 @@ struct MetaLayout {
   }
 };
 
-struct ClassPlan {
-  uint32_t sbeg = 0, send = 0, tiles = 0, passes = 0;
-  uint64_t key_bytes = 0;  // keys of the class, in bytes
-};
-
 enum Kind { kTokSummary, kTokScan, kTokWrite, kHistK, kScatter, kTileSort, kMerge, kEmit, kKinds };
 const char* const kKindName[kKinds] = {"tok_summary", "tok_scan", "tok_write", "hist",
                                        "scatter",     "tile_sort", "merge_pass", "emit"};
@@ -81,6 +72,8 @@ struct bsort_ctx {
   int device = 0;
   int sm_count = 0;
   cudaStream_t own_stream = nullptr;
+  cudaStream_t side_stream = nullptr;         // K4 of one-tile buckets runs here, beside the clusters
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   std::string err;
   bool busy = false;
 
@@ -92,7 +85,8 @@ struct bsort_ctx {
   // results of the last run (host view)
   MetaLayout ml;
   uint32_t ndocs = 0;
-  std::vector<Segment> segv;
+  std::vector<Segment> segv, segv2;
+  std::vector<uint8_t> groupv;
   std::vector<uint32_t> lookupv;
   std::vector<uint32_t> doc_status;
 
@@ -327,66 +321,115 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     }
   }
 
-  // ---- bucket layout: one segment per (document, length), ordered by class ----
+  // ---- bucket layout: one segment per (document, length) ----
+  // Groups, in table order:
+  //   0..4  keys of W = 1, 2, 4, 8, 16 words needing merge passes after K4:
+  //         K4 with clusters of 8, then K5 (one launch per pass and width)
+  //   5     keys of <= 16 words, more than one K4 tile, no pass: K4 with clusters of 8
+  //   6     keys of <= 16 words, one K4 tile: K4 with single CTAs
+  //   7     keys of 32 words (129..255 letters): the narrow-tile kernels of k_sort.cu
+  constexpr int kGroups = 8;
   c->lookupv.assign((size_t)ndocs * kHist, kNoSegment);
-  c->segv.clear();
   for (uint32_t d = 0; d < ndocs; ++d)
     if (h_hist[(size_t)d * kHist] != 0) c->doc_status[d] = BSORT_E_WORD_TOO_LONG;
-  ClassPlan cp[kNumClasses];
-  uint64_t key_words = 0;
-  uint32_t etile = 0;
-  for (int cl = 0; cl < kNumClasses; ++cl) {
-    const int W = width_of_class(cl);
-    const uint32_t T = (uint32_t)tile_of_width(W);
-    cp[cl].sbeg = (uint32_t)c->segv.size();
-    uint32_t tile = 0, passes = 0;
-    for (uint32_t d = 0; d < ndocs; ++d) {
-      if (c->doc_status[d] != BSORT_OK) continue;
-      const uint32_t* h = h_hist + (size_t)d * kHist;
-      uint32_t word_before = h_wbase[d] + d, byte_before = h_lbase[d];
-      for (uint32_t L = 1; L < kClassLmin[cl]; ++L) {
-        word_before += h[L];
-        byte_before += L * h[L];
-      }
-      for (uint32_t L = kClassLmin[cl]; L <= kClassLmax[cl]; ++L) {
-        const uint32_t n = h[L];
-        if (n) {
-          Segment s{};
-          s.key_off = key_words;
-          s.n = n;
-          s.L = L;
-          s.doc = d;
-          s.tile0 = tile;
-          s.etile0 = etile;
-          s.out_word = word_before;
-          s.stream_off = byte_before;
-          s.doc_stream0 = h_lbase[d];
-          const uint32_t p = merge_passes(n, T);
-          s.final_buf = p & 1u;
-          passes = std::max(passes, p);
-          const uint32_t nt = (n + T - 1) / T;
-          tile += nt;
-          etile += nt;
-          key_words += align_up((size_t)n * W, 16);
-          c->lookupv[(size_t)d * kHist + L] = (uint32_t)c->segv.size();
-          c->segv.push_back(s);
+  std::vector<Segment>& cand = c->segv;
+  cand.clear();
+  std::vector<uint8_t>& group = c->groupv;
+  group.clear();
+  uint32_t group_n[kGroups] = {};
+  for (uint32_t d = 0; d < ndocs; ++d) {
+    if (c->doc_status[d] != BSORT_OK) continue;
+    const uint32_t* h = h_hist + (size_t)d * kHist;
+    uint32_t word_before = h_wbase[d] + d, byte_before = h_lbase[d];
+    for (uint32_t L = 1; L < (uint32_t)kHist; ++L) {
+      const uint32_t n = h[L];
+      if (n) {
+        Segment sg{};
+        sg.n = n;
+        sg.L = L;
+        sg.doc = d;
+        sg.out_word = word_before;
+        sg.stream_off = byte_before;
+        sg.doc_stream0 = h_lbase[d];
+        const int W = width_of_len(L);
+        uint8_t gi;
+        if (W == 32) {
+          gi = 7;
+          sg.run0 = (uint32_t)tile_of_width(32);
+          sg.passes = merge_passes(n, sg.run0);
+        } else if (n <= tile2_keys(W)) {
+          gi = 6;
+          sg.run0 = n;
+          sg.passes = 0;
+        } else {
+          sg.run0 = kSuperCluster * tile2_keys(W);
+          sg.passes = merge_passes(n, sg.run0);
+          gi = sg.passes ? (uint8_t)class_of_width(W) : 5;
         }
-        word_before += n;
-        byte_before += L * n;
+        sg.final_buf = sg.passes & 1u;
+        cand.push_back(sg);
+        group.push_back(gi);
+        ++group_n[gi];
       }
+      word_before += n;
+      byte_before += L * n;
     }
-    cp[cl].send = (uint32_t)c->segv.size();
-    cp[cl].tiles = tile;
-    cp[cl].passes = passes;
-    for (uint32_t i = cp[cl].sbeg; i < cp[cl].send; ++i) cp[cl].key_bytes += 8ull * W * c->segv[i].n;
   }
-  const uint32_t nseg = (uint32_t)c->segv.size();
+  const uint32_t nseg = (uint32_t)cand.size();
+  // stable counting sort of the candidates by group
+  uint32_t gbeg[kGroups + 1] = {};
+  for (int g = 0; g < kGroups; ++g) gbeg[g + 1] = gbeg[g] + group_n[g];
+  std::vector<Segment>& segs = c->segv2;
+  segs.resize(nseg);
+  {
+    uint32_t at[kGroups];
+    for (int g = 0; g < kGroups; ++g) at[g] = gbeg[g];
+    for (uint32_t i = 0; i < nseg; ++i) segs[at[group[i]]++] = cand[i];
+  }
+  const uint32_t g01 = gbeg[6], g012 = gbeg[7];  // clustered K4 range ends, single-CTA range ends
+  uint64_t key_words = 0, kb[kGroups] = {};
+  uint32_t etile = 0, stile8 = 0, stile1 = 0, wtile = 0, passes3 = 0;
+  uint32_t mtiles[5] = {}, mpasses[5] = {};
+  int max_w8 = 1, max_w1 = 1;  // widest key of each K4 launch
+  for (uint32_t i = 0; i < nseg; ++i) {
+    Segment& sg = segs[i];
+    const int W = width_of_len(sg.L);
+    int gi = 0;
+    while (i >= gbeg[gi + 1]) ++gi;
+    sg.key_off = key_words;
+    key_words += align_up((size_t)sg.n * W, 16);
+    kb[gi] += 8ull * W * sg.n;
+    sg.etile0 = etile;
+    etile += (sg.n + tile_of_width(W) - 1) / tile_of_width(W);
+    if (gi < 5) {
+      sg.tile0 = mtiles[gi];
+      mtiles[gi] += (sg.n + merge2_keys(W) - 1) / merge2_keys(W);
+      mpasses[gi] = std::max(mpasses[gi], sg.passes);
+    }
+    if (gi <= 5) {
+      sg.stile0 = stile8;
+      stile8 += (sg.n + sg.run0 - 1) / sg.run0;
+      max_w8 = std::max(max_w8, W);
+    } else if (gi == 6) {
+      sg.stile0 = stile1++;
+      max_w1 = std::max(max_w1, W);
+    } else {
+      sg.tile0 = wtile;
+      wtile += (sg.n + sg.run0 - 1) / sg.run0;
+      passes3 = std::max(passes3, sg.passes);
+    }
+    c->lookupv[(size_t)sg.doc * kHist + sg.L] = i;
+  }
+  uint64_t kb_clustered = 0;
+  for (int g = 0; g <= 5; ++g) kb_clustered += kb[g];
+  uint32_t passes2 = 0;
+  for (int g = 0; g < 5; ++g) passes2 = std::max(passes2, mpasses[g]);
 
   // ---- upload the layout, size the key and output buffers ----
   const size_t seg_bytes = sizeof(Segment) * std::max<size_t>(nseg, 1);
   const size_t lookup_bytes = 4ull * ndocs * kHist;
   GROW_HOST(c->h_plan, seg_bytes + lookup_bytes, "layout");
-  std::memcpy(c->h_plan.p, c->segv.data(), sizeof(Segment) * nseg);
+  if (nseg) std::memcpy(c->h_plan.p, segs.data(), sizeof(Segment) * nseg);
   std::memcpy(hptr<char>(c->h_plan, seg_bytes), c->lookupv.data(), lookup_bytes);
   GROW(c->segs, seg_bytes, "segments");
   GROW(c->lookup, lookup_bytes, "segment lookup");
@@ -396,7 +439,9 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   GROW(c->counts, 8ull * ndocs * kHist, "counts");
   GROW(c->offsets, 4ull * ((uint64_t)n_total + ndocs), "offsets");
   GROW(c->stream, (size_t)s_total + 16, "stream");
-  CK(cudaMemcpyAsync(c->segs.p, c->h_plan.p, sizeof(Segment) * nseg, cudaMemcpyHostToDevice, st), "copy segments");
+  if (nseg)
+    CK(cudaMemcpyAsync(c->segs.p, c->h_plan.p, sizeof(Segment) * nseg, cudaMemcpyHostToDevice, st),
+       "copy segments");
   CK(cudaMemcpyAsync(c->lookup.p, hptr<char>(c->h_plan, seg_bytes), lookup_bytes, cudaMemcpyHostToDevice, st),
      "copy segment lookup");
   CK(cudaMemsetAsync(c->cursor.p, 0, 4ull * std::max<uint32_t>(nseg, 1), st), "clear cursors");
@@ -405,7 +450,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   uint64_t* kA = dptr<uint64_t>(c->keysA);
   uint64_t* kB = dptr<uint64_t>(c->keysB);
   uint64_t key_bytes_all = 0;
-  for (int cl = 0; cl < kNumClasses; ++cl) key_bytes_all += cp[cl].key_bytes;
+  for (int g = 0; g < kGroups; ++g) key_bytes_all += kb[g];
   if (items) {
     LAUNCH(kScatter, (double)s_total + 4.0 * n_total + key_bytes_all,
            launch_scatter(dptr<uint32_t>(c->starts), dptr<uint8_t>(c->letters), d_wbase, d_item0, ndocs, items,
@@ -413,25 +458,59 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
            "K3 scatter");
   }
   const uint32_t grid_cap = (uint32_t)c->sm_count * 16;
-  for (int cl = 0; cl < kNumClasses; ++cl) {
-    if (cp[cl].tiles == 0) continue;
-    const int W = width_of_class(cl);
-    const uint32_t grid = std::min(cp[cl].tiles, grid_cap);
-    LAUNCH(kTileSort, 2.0 * cp[cl].key_bytes,
-           launch_tile_sort(W, d_segs, cp[cl].sbeg, cp[cl].send, cp[cl].tiles, grid, kA, d_sticky,
+  // K4: multi-tile buckets in clusters, one-tile buckets in single CTAs, 32-word keys apart
+  if (stile8)
+    LAUNCH(kTileSort, 2.0 * kb_clustered,
+           launch_tile_sort2(kSuperCluster, d_segs, 0, g01, stile8, c->sm_count, max_w8, kA, d_sticky,
+                             c->cfg.wait_limit, st),
+           "K4 tile_sort (clusters)");
+  if (stile1) {
+    // one-tile buckets are independent of the clustered ones: sort them on a
+    // side stream at the same time, joined back before the merge passes
+    cudaStream_t s1 = stile8 ? c->side_stream : st;
+    if (stile8) {
+      CK(cudaEventRecord(c->fork_ev, st), "fork");
+      CK(cudaStreamWaitEvent(s1, c->fork_ev, 0), "fork");
+    }
+    {
+      Trace tr_(c, s1, kTileSort, 2.0 * kb[6]);
+      CK(tr_.done(launch_tile_sort2(1, d_segs, g01, g012, stile1, c->sm_count, max_w1, kA, d_sticky,
+                                    c->cfg.wait_limit, s1)),
+         "K4 tile_sort");
+    }
+    if (stile8) {
+      CK(cudaEventRecord(c->join_ev, s1), "join");
+      CK(cudaStreamWaitEvent(st, c->join_ev, 0), "join");
+    }
+  }
+  if (wtile)
+    LAUNCH(kTileSort, 2.0 * kb[7],
+           launch_tile_sort(32, d_segs, g012, nseg, wtile, std::min(wtile, grid_cap), kA, d_sticky,
                             c->cfg.wait_limit, st),
-           "K4 tile_sort");
-    for (uint32_t p = 0; p < cp[cl].passes; ++p) {
-      // only buckets longer than one run of this pass move
-      const uint64_t run = (uint64_t)tile_of_width(W) << p;
+           "K4 tile_sort (32-word keys)");
+  // K5: merge passes over the buckets that need them, one launch per pass and width
+  for (uint32_t p = 0; p < passes2; ++p) {
+    for (int g = 0; g < 5; ++g) {
+      if (mpasses[g] <= p) continue;
+      const int W = width_of_class(g);
       double moved = 0;
-      for (uint32_t i = cp[cl].sbeg; i < cp[cl].send; ++i)
-        if (c->segv[i].n > run) moved += 16.0 * W * c->segv[i].n;
+      for (uint32_t i = gbeg[g]; i < gbeg[g + 1]; ++i)
+        if (segs[i].passes > p) moved += 16.0 * W * segs[i].n;
       LAUNCH(kMerge, moved,
-             launch_merge_pass(W, d_segs, cp[cl].sbeg, cp[cl].send, cp[cl].tiles, grid, p, (p & 1) ? kB : kA,
-                               (p & 1) ? kA : kB, st),
+             launch_merge_pass2(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g],
+                                std::min<uint32_t>(mtiles[g], (uint32_t)c->sm_count * 8), p, (p & 1) ? kB : kA,
+                                (p & 1) ? kA : kB, st),
              "K5 merge_pass");
     }
+  }
+  for (uint32_t p = 0; p < passes3; ++p) {
+    double moved = 0;
+    for (uint32_t i = g012; i < nseg; ++i)
+      if (segs[i].passes > p) moved += 16.0 * 32 * segs[i].n;
+    LAUNCH(kMerge, moved,
+           launch_merge_pass(32, d_segs, g012, nseg, wtile, std::min(wtile, grid_cap), p, (p & 1) ? kB : kA,
+                             (p & 1) ? kA : kB, st),
+           "K5 merge_pass (32-word keys)");
   }
   const uint32_t emit_grid =
       std::max<uint32_t>(1u, std::min<uint32_t>(std::max(etile, (ndocs * kHist + kSortThreads - 1) / kSortThreads),
@@ -539,9 +618,12 @@ bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
   c->cfg = conf;
   c->device = dev;
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
-    delete c;
+    bsort_destroy(c);  // frees whatever was created
     return BSORT_E_CUDA;
   }
   // the sticky status word starts cleared
@@ -566,6 +648,9 @@ void bsort_destroy(bsort_ctx* c) {
   for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets, &c->h_stream})
     if (b->p) cudaFreeHost(b->p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }

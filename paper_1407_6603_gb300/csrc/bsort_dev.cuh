@@ -91,22 +91,75 @@ struct Meta {
   uint32_t pad[3];
 };
 
-// One (document, length) bucket.  The table is ordered by key class, then
-// document, then length; each class's tiles are numbered from 0 (tile0) and
-// all tiles are numbered across classes too (etile0).
+// One (document, length) bucket.  The host orders the table as
+//   [buckets that need merge passes, by key width] [other buckets of more
+//   than one K4 tile] [buckets of one K4 tile] [buckets of 129..255-letter words]
+// so that each kernel covers a contiguous range of it.
 struct Segment {
   uint64_t key_off;     // first key, in u64 words, in both key buffers
   uint32_t n;           // words in the bucket
   uint32_t L;           // their length
   uint32_t doc;
-  uint32_t tile0;       // first tile within the class
-  uint32_t etile0;      // first tile across all classes
+  uint32_t tile0;       // first merge tile (K5), numbered over the merge range
+  uint32_t etile0;      // first emit tile (K6), numbered over the whole table
+  uint32_t stile0;      // first K4 supertile, numbered within its K4 launch
   uint32_t out_word;    // index in offsets[] of the bucket's first word
   uint32_t stream_off;  // byte offset in the output stream of the bucket's first word
   uint32_t doc_stream0; // first stream byte of the document (offsets are per document)
   uint32_t final_buf;   // 0: sorted keys end in buffer A, 1: in buffer B
-  uint32_t pad;
+  uint32_t passes;      // merge passes the bucket needs after K4
+  uint32_t run0;        // length of the sorted runs K4 leaves
+  uint32_t pad[2];
 };
+
+// K4 v2 / K5 v2 geometry (keys of at most 16 u64 words).
+constexpr int kSuperCluster = 8;    // CTAs per K4 cluster
+// keys per K4 CTA tile: 2048 u64 words, 256 keys of 16 words
+__host__ __device__ inline uint32_t tile2_keys(int W) { return (uint32_t)(W >= 16 ? 256 : 2048 / W); }
+__host__ __device__ inline uint32_t merge2_keys(int W) { return (uint32_t)(256 * (W >= 8 ? 1 : 8 / W)); }
+
+// Work items of the sort and emit kernels are numbered across buckets; a
+// CTA finds the bucket of an item by binary search over the buckets' first
+// item numbers.  When a launch covers at most kSegCache buckets (every single
+// document), the numbers are first copied to shared memory so that the search
+// costs no global loads.
+constexpr uint32_t kSegCache = 256;
+
+#if defined(__CUDACC__)
+// Field selector: which first-item number a kernel searches by.
+enum SegField { kByTile0, kByStile0, kByEtile0 };
+template <SegField F>
+__device__ __forceinline__ uint32_t seg_first_item(const Segment& s) {
+  return F == kByTile0 ? s.tile0 : F == kByStile0 ? s.stile0 : s.etile0;
+}
+// Loads the first-item numbers of segments [sbeg, send) into `cache` when
+// they fit; returns whether they did.  Call from all threads; ends with a
+// barrier.
+template <SegField F>
+__device__ __forceinline__ bool seg_cache_fill(const Segment* segs, uint32_t sbeg, uint32_t send,
+                                               uint32_t* cache) {
+  const bool fits = send - sbeg <= kSegCache;
+  if (fits)
+    for (uint32_t i = threadIdx.x; i < send - sbeg; i += blockDim.x) cache[i] = seg_first_item<F>(segs[sbeg + i]);
+  __syncthreads();
+  return fits;
+}
+// Last segment in [sbeg, send) whose first item is <= it.
+template <SegField F>
+__device__ __forceinline__ uint32_t seg_find(const Segment* segs, uint32_t sbeg, uint32_t send,
+                                             const uint32_t* cache, bool cached, uint32_t it) {
+  uint32_t lo = 0, hi = send - sbeg - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    const uint32_t v = cached ? cache[mid] : seg_first_item<F>(segs[sbeg + mid]);
+    if (v <= it)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return sbeg + lo;
+}
+#endif
 
 // -------- launchers (each returns the launch's cudaError_t) --------
 
@@ -127,6 +180,11 @@ cudaError_t launch_tile_sort(int W, const Segment* segs, uint32_t sbeg, uint32_t
                              uint32_t grid, uint64_t* keys, Meta* meta, uint64_t wait_limit, cudaStream_t st);
 cudaError_t launch_merge_pass(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st);
+cudaError_t launch_tile_sort2(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
+                              int max_grid, int max_width, uint64_t* keys, Meta* meta, uint64_t wait_limit,
+                              cudaStream_t st);
+cudaError_t launch_merge_pass2(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
+                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st);
 cudaError_t launch_emit(const Segment* segs, uint32_t nseg, uint32_t tiles, uint32_t grid, const uint64_t* keysA,
                         const uint64_t* keysB, const uint32_t* hist, const uint32_t* doc_wbase,
                         const uint32_t* doc_lbase, uint32_t ndocs, int want_offsets, uint8_t* stream,

@@ -92,18 +92,6 @@ __global__ void __launch_bounds__(kWordThreads) k_scatter(const uint32_t* __rest
   }
 }
 
-__device__ __forceinline__ uint32_t find_segment_e(const Segment* segs, uint32_t nseg, uint32_t it) {
-  uint32_t lo = 0, hi = nseg - 1;  // last segment with etile0 <= it
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) >> 1;
-    if (segs[mid].etile0 <= it)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
 __global__ void __launch_bounds__(kSortThreads) k_emit(const Segment* __restrict__ segs, uint32_t nseg,
                                                        uint32_t tiles, const uint64_t* __restrict__ keysA,
                                                        const uint64_t* __restrict__ keysB,
@@ -120,8 +108,10 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const Segment* __restrict
     if (L == 0 && want_offsets) offsets[doc_wbase[d + 1] + d] = doc_lbase[d + 1] - doc_lbase[d];
   }
   __shared__ uint32_t s_seg;
+  __shared__ uint32_t s_first[kSegCache];
+  const bool cached = nseg ? seg_cache_fill<kByEtile0>(segs, 0, nseg, s_first) : false;
   for (uint32_t it = blockIdx.x; it < tiles; it += gridDim.x) {
-    if (threadIdx.x == 0) s_seg = find_segment_e(segs, nseg, it);
+    if (threadIdx.x == 0) s_seg = seg_find<kByEtile0>(segs, 0, nseg, s_first, cached, it);
     __syncthreads();
     const Segment sg = segs[s_seg];
     __syncthreads();
