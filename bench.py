@@ -42,9 +42,8 @@ FALLBACK_HBM_GBS = 6800.0
 
 # Kernel families and the source file that holds each (for the traffic record).
 KERNEL_SOURCE = {
-    "tok_summary": "k_tokenize.cu", "tok_scan": "k_tokenize.cu", "tok_write": "k_tokenize.cu",
-    "hist": "k_tokenize.cu", "scatter": "k_scatter.cu", "emit": "k_scatter.cu",
-    "tile_sort": "k_sort.cu", "merge_pass": "k_sort.cu",
+    "tokenize": "k_tokenize1p.cu", "scatter": "k_scatter.cu", "emit": "k_scatter.cu",
+    "tile_sort": "k_sort2.cu", "merge_pass": "k_sort2.cu",
 }
 
 

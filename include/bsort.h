@@ -139,8 +139,8 @@ bsort_status bsort_batch(bsort_ctx* ctx, const uint8_t* const* docs, const size_
  * needs: input, stripped letters, word starts, keys, output).
  */
 typedef struct {
-  const char* name;   /* kernel family: "tok_summary", "tok_scan", "tok_write", "hist", "scatter",
-                         "tile_sort", "merge_pass", "emit" (static string) */
+  const char* name;   /* kernel family: "tokenize", "scatter", "tile_sort", "merge_pass", "emit"
+                         (static string) */
   uint64_t launches;  /* launches since the last read */
   double ms;          /* summed device time of those launches (0 when profiling is off) */
   double bytes;       /* summed algorithmic bytes of those launches */

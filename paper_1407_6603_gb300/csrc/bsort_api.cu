@@ -1,8 +1,8 @@
 // Host runtime and C ABI of libbsort (declared in include/bsort.h).
 //
 // One call runs the whole path for one or more documents on one CUDA stream:
-//   K1a/K1b/K1c  strip + tokenize            (paper Section II, phase 1)
-//   K2           per-document length counts  (phase 2: sub-array sizes)
+//   K1           strip + tokenize and per-document length counts, one pass
+//                (paper Section II, phase 1; the counts size phase 2)
 //   -- the host reads the counts back and lays out one bucket per
 //      (document, length): key offsets, tiles, merge passes --
 //   K3           scatter words into buckets as packed keys (phase 2)
@@ -55,9 +55,8 @@ struct MetaLayout {
   }
 };
 
-enum Kind { kTokSummary, kTokScan, kTokWrite, kHistK, kScatter, kTileSort, kMerge, kEmit, kKinds };
-const char* const kKindName[kKinds] = {"tok_summary", "tok_scan", "tok_write", "hist",
-                                       "scatter",     "tile_sort", "merge_pass", "emit"};
+enum Kind { kTokenize, kScatter, kTileSort, kMerge, kEmit, kKinds };
+const char* const kKindName[kKinds] = {"tokenize", "scatter", "tile_sort", "merge_pass", "emit"};
 
 struct ProfRec {
   int kind;
@@ -79,7 +78,8 @@ struct bsort_ctx {
 
   DevBuf sticky;  // a Meta kept across calls: err_timeout of bounded device waits
   HostBuf h_sticky;
-  DevBuf in, docs, sums, carry, meta, starts, letters, lookup, segs, cursor, keysA, keysB, counts, offsets, stream;
+  DevBuf k1scratch;
+  DevBuf in, docs, meta, starts, letters, lookup, segs, cursor, keysA, keysB, counts, offsets, stream;
   HostBuf h_in, h_docs, h_meta, h_plan, h_counts, h_offsets, h_stream;
 
   // results of the last run (host view)
@@ -234,7 +234,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   // ---- documents and chunks ----
   GROW_HOST(c->h_docs, sizeof(DocDesc) * ndocs, "document table");
   DocDesc* hd = hptr<DocDesc>(c->h_docs);
-  uint64_t chunks = 0, total_len = 0, words_bound = 0, items_bound = 0;
+  uint64_t chunks = 0, total_len = 0, words_bound = 0;
   for (uint32_t i = 0; i < ndocs; ++i) {
     if (lens[i] >= (1ull << 32))
       return fail(c, BSORT_E_TOO_LARGE, "document of 2^32 bytes or more (offsets are 32-bit)");
@@ -245,15 +245,12 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     total_len += lens[i];
     const uint64_t wb = lens[i] / 2 + 1;
     words_bound += wb;
-    items_bound += (wb + kWordBlock - 1) / kWordBlock;
   }
   if (total_len >= (1ull << 32))
     return fail(c, BSORT_E_TOO_LARGE, "2^32 bytes or more in one pass (positions are 32-bit)");
   c->ml.set(ndocs);
   const MetaLayout& ml = c->ml;
   GROW(c->docs, sizeof(DocDesc) * ndocs, "document table");
-  GROW(c->sums, sizeof(TokSum) * (chunks + 1), "chunk summaries");
-  GROW(c->carry, sizeof(TokSum) * (chunks + 1), "chunk prefixes");
   GROW(c->meta, ml.total, "meta");
   GROW(c->starts, 4 * (words_bound + 1), "word starts");
   GROW(c->letters, total_len + 16, "stripped letters");
@@ -268,27 +265,15 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   CK(cudaMemcpyAsync(c->docs.p, hd, sizeof(DocDesc) * ndocs, cudaMemcpyHostToDevice, st), "copy document table");
   CK(cudaMemsetAsync(c->meta.p, 0, ml.total, st), "clear meta");
   const DocDesc* d_docs = dptr<DocDesc>(c->docs);
-  // Algorithmic bytes of K1/K2 are known only after the counts come back;
-  // they are added to the tags below once n and S are read.
-  if (chunks) {
-    LAUNCH(kTokSummary, 0, launch_tok_summary(d_in, d_docs, ndocs, (uint32_t)chunks, dptr<TokSum>(c->sums), st),
-           "K1a tok_summary");
-  }
-  LAUNCH(kTokScan, 0,
-         launch_tok_scan(dptr<TokSum>(c->sums), (uint32_t)chunks, d_docs, ndocs, dptr<TokSum>(c->carry), d_wbase,
-                         d_lbase, d_item0, dptr<uint32_t>(c->starts), d_meta, st),
-         "K1b tok_scan");
-  if (chunks) {
-    LAUNCH(kTokWrite, 0,
-           launch_tok_write(d_in, d_docs, ndocs, (uint32_t)chunks, dptr<TokSum>(c->carry), dptr<uint8_t>(c->letters),
-                            dptr<uint32_t>(c->starts), st),
-           "K1c tok_write");
-  }
-  const uint32_t hist_grid = (uint32_t)std::min<uint64_t>(items_bound, (uint64_t)c->sm_count * 8);
-  LAUNCH(kHistK, 0,
-         launch_hist(dptr<uint32_t>(c->starts), d_wbase, d_item0, ndocs, std::max(hist_grid, 1u), c->cfg.l_cap,
-                     d_hist, d_meta, st),
-         "K2 hist");
+  // K1: strip, tokenize and count lengths in one pass.  Its algorithmic bytes
+  // (input read, letters and word starts written) are known only after the
+  // counts come back; they are added to its tag below.
+  GROW(c->k1scratch, tokenize1p_scratch_bytes((uint32_t)chunks), "tokenizer scratch");
+  LAUNCH(kTokenize, 0,
+         launch_tokenize1p(d_in, d_docs, ndocs, (uint32_t)chunks, dptr<uint8_t>(c->k1scratch),
+                           dptr<uint8_t>(c->letters), dptr<uint32_t>(c->starts), d_hist, d_wbase, d_lbase, d_item0,
+                           d_meta, d_sticky, c->cfg.l_cap, c->cfg.wait_limit, st),
+         "K1 tokenize");
   CK(cudaMemcpyAsync(c->h_meta.p, c->meta.p, ml.total, cudaMemcpyDeviceToHost, st), "read counts");
   CK(cudaMemcpyAsync(c->h_sticky.p, c->sticky.p, sizeof(Meta), cudaMemcpyDeviceToHost, st), "read status");
   CK(cudaStreamSynchronize(st), "wait for counts");
@@ -304,21 +289,14 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   }
   const uint32_t n_total = hm->n_total, s_total = hm->s_total, items = hm->items_total;
   {
-    // algorithmic bytes of the launches above: K1a reads the input; K1b the
-    // chunk summaries; K1c reads the input and writes S and the word starts;
-    // K2 reads the word starts
-    const double N = (double)total_len, S = s_total, n4 = 4.0 * n_total;
-    const double per[4] = {N, 2.0 * sizeof(TokSum) * chunks, N + S + n4, n4};
-    const int kinds[4] = {kTokSummary, kTokScan, kTokWrite, kHistK};
-    for (int i = 0; i < 4; ++i) {
-      if (i != 1 && i != 3 && chunks == 0) continue;
-      c->kind_bytes[kinds[i]] += per[i];
-      for (auto it = c->recs.rbegin(); it != c->recs.rend(); ++it)
-        if (it->kind == kinds[i]) {
-          it->bytes += per[i];
-          break;
-        }
-    }
+    // K1 reads the input and writes the letters and the word starts
+    const double k1 = (double)total_len + s_total + 4.0 * n_total;
+    c->kind_bytes[kTokenize] += k1;
+    for (auto it = c->recs.rbegin(); it != c->recs.rend(); ++it)
+      if (it->kind == kTokenize) {
+        it->bytes += k1;
+        break;
+      }
   }
 
   // ---- bucket layout: one segment per (document, length) ----
@@ -642,7 +620,7 @@ void bsort_destroy(bsort_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
-  for (DevBuf* b : {&c->sticky, &c->in, &c->docs, &c->sums, &c->carry, &c->meta, &c->starts, &c->letters, &c->lookup, &c->segs,
+  for (DevBuf* b : {&c->sticky, &c->k1scratch, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->lookup, &c->segs,
                     &c->cursor, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream})
     if (b->p) cudaFree(b->p);
   for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets, &c->h_stream})

@@ -1,16 +1,14 @@
 // Internal declarations shared by the CUDA translation units of libbsort.
 //
 // Data flow of one call (every kernel covers all documents of the call):
-//   K1a tok_summary   per 16 KiB chunk: letters, word starts, boundary state
-//   K1b tok_scan      one CTA: exclusive scan of the chunk summaries, per-
-//                     document bases of letters / words / word-blocks
-//   K1c tok_write     per chunk: the stripped letter stream S and the start
-//                     offset of every word in S
-//   K2  hist          per 1024-word block: length histogram per document
+//   K1  tokenize      per 16 KiB chunk, one pass (decoupled look-back): the
+//                     stripped letter stream S, the S offset of every word
+//                     start, the per-document length histograms and bases
 //   -- host reads the histograms and lays out one segment per (doc, length)
 //   K3  scatter       per 1024-word block: each word packed into a big-endian
 //                     key of W u64 words, written to its segment
-//   K4  tile_sort     per tile: odd-even transposition sort
+//   K4  tile_sort     per tile: odd-even transposition sort, then merges
+//                     through distributed shared memory inside a cluster
 //   K5  merge_pass    per tile and pass: merge-path merge of run pairs
 //   K6  emit          per tile: keys back to bytes, offsets, counts
 #pragma once
@@ -25,7 +23,7 @@ constexpr int kMaxLen = 255;                // longest word the key layout holds
 constexpr int kTokThreads = 256;            // K1 CTA size
 constexpr int kTokSeg = 64;                 // bytes per K1 thread
 constexpr int kChunk = kTokThreads * kTokSeg;  // bytes per K1 chunk (16 KiB)
-constexpr int kWordBlock = 1024;            // words per K2/K3 work item
+constexpr int kWordBlock = 1024;            // words per K3 work item
 constexpr int kWordThreads = 256;
 constexpr int kSortThreads = 256;           // K4/K5/K6 CTA size
 constexpr int kNumClasses = 6;              // key widths W = 1, 2, 4, 8, 16, 32 u64 words
@@ -163,16 +161,11 @@ __device__ __forceinline__ uint32_t seg_find(const Segment* segs, uint32_t sbeg,
 
 // -------- launchers (each returns the launch's cudaError_t) --------
 
-cudaError_t launch_tok_summary(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
-                               TokSum* sums, cudaStream_t st);
-cudaError_t launch_tok_scan(const TokSum* sums, uint32_t nchunks, const DocDesc* docs, uint32_t ndocs,
-                            TokSum* carry, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0,
-                            uint32_t* starts, Meta* meta, cudaStream_t st);
-cudaError_t launch_tok_write(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
-                             const TokSum* carry, uint8_t* letters, uint32_t* starts, cudaStream_t st);
-cudaError_t launch_hist(const uint32_t* starts, const uint32_t* doc_wbase, const uint32_t* doc_item0,
-                        uint32_t ndocs, uint32_t grid, uint32_t l_cap, uint32_t* hist, Meta* meta,
-                        cudaStream_t st);
+size_t tokenize1p_scratch_bytes(uint32_t nchunks);
+cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
+                              uint8_t* scratch, uint8_t* letters, uint32_t* starts, uint32_t* hist,
+                              uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
+                              Meta* sticky, uint32_t l_cap, uint64_t wait_limit, cudaStream_t st);
 cudaError_t launch_scatter(const uint32_t* starts, const uint8_t* letters, const uint32_t* doc_wbase,
                            const uint32_t* doc_item0, uint32_t ndocs, uint32_t items, const uint32_t* seg_lookup,
                            const Segment* segs, uint32_t* cursor, uint64_t* keys, cudaStream_t st);

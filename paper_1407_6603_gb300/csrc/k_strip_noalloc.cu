@@ -10,9 +10,9 @@
 // one look-back record per 16 KiB chunk, lives in the file-scope device
 // array below, which every GPU that loads the library holds until exit.
 //
-// The kernel is a one-pass variant of K1 in k_tokenize.cu.  Where the main
-// path runs three kernels (chunk summaries, their scan, the writes), here
-// each CTA takes the next chunk from a ticket counter, publishes its chunk's
+// The kernel is a single-document variant of the one-pass K1 of
+// k_tokenize1p.cu without the length histogram: each CTA takes the next chunk
+// from a ticket counter, publishes its chunk's
 // summary, looks back over its predecessors' records until it meets one that
 // holds an inclusive prefix (decoupled look-back), publishes its own
 // inclusive prefix, and writes its letters and word starts.  Tickets are

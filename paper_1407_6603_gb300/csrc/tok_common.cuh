@@ -1,6 +1,14 @@
-// Device helpers of the strip + tokenize step (K1), shared by the
-// three-kernel path in k_tokenize.cu and the one-pass kernel in
-// k_strip_noalloc.cu.  See k_tokenize.cu for the method.
+// Device helpers of the strip + tokenize step (K1), shared by the one-pass
+// kernels of k_tokenize1p.cu (the main path) and k_strip_noalloc.cu.
+//
+// Each thread owns 64 consecutive bytes.  It classifies them four at a time
+// with byte-SIMD compares into two 64-bit masks (letters, whitespace), and
+// finds the word starts among its letters with one addition: adding
+// (whitespace << 1) to the mask of transparent bytes (neither letter nor
+// whitespace) carries each whitespace bit across the transparent run after it
+// and stops on the next letter or whitespace byte, so
+// ((T + (Ws << 1)) ^ T) & Letters marks exactly the letters whose previous
+// letter-or-whitespace byte is whitespace.
 #pragma once
 
 #include "bsort_dev.cuh"
