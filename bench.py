@@ -53,7 +53,9 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="plain_1m38", choices=["plain_190k", "plain_1m38", "plain_256m"])
+    p.add_argument("--workload", default="plain_1m38",
+                   choices=["plain_190k", "plain_1m38", "plain_256m", "batch_4096"])
+    p.add_argument("--batch-docs", type=int, default=None, help="use only the first D documents of batch_4096")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--prefix-bytes", type=int, default=None,
@@ -209,12 +211,30 @@ def run_reference(args) -> None:
     import oracle
     import synth
 
-    data = synth.plain(args.workload)
     cores = os.cpu_count() or 1
-    if args.workload == "plain_256m":
+    if args.workload == "batch_4096":
+        # documents of the batch, concatenated up to 16 MiB, each sorted on its own
+        docs = synth.batch(64, threads=cores)
+        picked, size = [], 0
+        for d in docs:
+            if size + d.size > (16 << 20) and picked:
+                break
+            picked.append(d)
+            size += d.size
+
+        def batch_fn(_sample, nthreads):
+            return {"n_words": sum(oracle.stable(d, nthreads=nthreads)["n_words"] for d in picked)}
+
+        import numpy as np
+
+        sample = np.concatenate(picked)
+        fn, kind_s = batch_fn, f"O2 stable_sort per length bucket on {len(picked)} batch documents"
+    elif args.workload == "plain_256m":
+        data = synth.plain(args.workload)
         sample = data[: 16 << 20]
         fn, kind_s = oracle.stable, "O2 stable_sort per length bucket"
     else:
+        data = synth.plain(args.workload)
         # bubble sort is quadratic in the largest bucket: bound each step with a
         # prefix of the document (about a second of work per step)
         size = min(data.size, 512 << 10)
@@ -247,40 +267,79 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def load_workload(args):
+    """The workload's documents on the host: one document, or the batch."""
+    import numpy as np
+
+    import synth
+
+    if args.workload == "batch_4096":
+        docs = synth.batch(args.batch_docs, threads=os.cpu_count() or 8)
+        lens = [int(d.size) for d in docs]
+        offs = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.int64).tolist()
+        return docs, offs, lens, np.concatenate(docs)
+    data = synth.plain(args.workload)
+    if args.prefix_bytes:
+        data = data[: args.prefix_bytes]
+    return [data], [0], [int(data.size)], data
+
+
+def cpu_baseline_batch(docs) -> dict:
+    """The oracle's stable_sort path (OpenMP over buckets) over the batch's
+    documents one by one, for about ten seconds (a bounded sample)."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    nb = nw = nd = 0
+    for d in docs:
+        nw += oracle.stable(d, nthreads=cores)["n_words"]
+        nb += d.size
+        nd += 1
+        if time.perf_counter() - t0 > 10.0:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": nb / dt / 1e6, "unit": "MB/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {nd} of {len(docs)} batch documents ({nb} B, {nw} words), O2 stable_sort per length "
+                      f"bucket, OpenMP over buckets on {cores} threads, {dt:.2f} s",
+            "words_per_s": nw / dt}
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
 
     import paper_1407_6603_gb300 as bs
-    import synth
 
     rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
     if world > 1:
         import torch.distributed as dist
 
-        torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    else:
-        torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     bs.load()
-    data = synth.plain(args.workload)
-    if args.prefix_bytes:
-        data = data[: args.prefix_bytes]
-    nbytes = int(data.size)
-    d_in = torch.from_numpy(data).to(dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    batch = args.workload == "batch_4096"
+    docs, offs, lens, host = load_workload(args)
+    nbytes = int(host.size)
+    d_in = torch.from_numpy(host).to(dev)
+    flush = None if batch else torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(dev)
     ctx = bs.Context(profile=True, device=local_rank)
     sampler = ClockSampler(local_rank).start()
 
-    r = None
+    def step():
+        if batch:
+            st, rs = ctx.batch_device_raw(d_in, offs, lens, stream)
+            assert st == 0, ctx.last_error()
+            return sum(int(r.n_words) for r in rs), sum(int(r.stream_bytes) for r in rs)
+        r = ctx.text_device_raw(d_in, stream)
+        return int(r.n_words), int(r.stream_bytes)
+
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
-            r = ctx.text_device_raw(d_in, stream)
+            n_words, s_bytes = step()
         stream.synchronize()
-    n_words = int(r.n_words)
-    s_bytes = int(r.stream_bytes)
     ctx.profile_read()  # drop the warm-up records
     launches0 = ctx.launch_count()
 
@@ -290,9 +349,10 @@ def run_ours(args) -> None:
     torch.cuda.synchronize(dev)
     with torch.cuda.stream(stream):
         for i in range(args.steps):
-            flush.fill_(i & 0xFF)  # evict the previous step's data from L2 (not timed)
+            if flush is not None:
+                flush.fill_(i & 0xFF)  # evict the previous step's data from L2 (not timed)
             starts[i].record(stream)
-            ctx.text_device_raw(d_in, stream)
+            step()
             ends[i].record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
@@ -300,17 +360,40 @@ def run_ours(args) -> None:
     launches = ctx.launch_count() - launches0
     prof = ctx.profile_read()
 
-    # end to end through the host entry point: input H2D and results D2H each step
-    e2e_steps = args.e2e_steps or max(3, min(args.steps, 20))
-    host = np.ascontiguousarray(data)
-    ctx.text(host)
+    # the same documents one call each, for the batched-versus-plain comparison
+    plain_per_doc = None
+    if batch:
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                t_a = torch.cuda.Event(enable_timing=True)
+                t_b = torch.cuda.Event(enable_timing=True)
+                t_a.record(stream)
+                for o, ln in zip(offs, lens):
+                    ctx.text_device_raw(d_in[o:o + ln], stream)
+                t_b.record(stream)
+            torch.cuda.synchronize(dev)
+        pd_s = t_a.elapsed_time(t_b) / 1e3
+        plain_per_doc = {"words_per_s": n_words / pd_s, "mb_per_s": nbytes / pd_s / 1e6,
+                         "ms_per_pass": pd_s * 1e3, "calls": len(docs), "entry": "bsort_text_device per document"}
+
+    # end to end through the host entry points: input H2D and results D2H each step
+    e2e_steps = args.e2e_steps or (max(3, min(args.steps, 20)) if not batch else 3)
+
+    def host_step():
+        if batch:
+            st, rs = ctx.batch(docs)
+            assert st == 0
+            return sum(r.n_words for r in rs)
+        return ctx.text(host).n_words
+
+    host_step()
     torch.cuda.synchronize(dev)
     e2e_t = []
     for _ in range(e2e_steps):
         t0 = time.perf_counter()
-        res = ctx.text(host)
+        nw_host = host_step()
         e2e_t.append(time.perf_counter() - t0)
-    assert res.n_words == n_words
+    assert nw_host == n_words
     clocks = sampler.stop()
 
     local_time = sum(step_ms) / 1e3
@@ -339,18 +422,26 @@ def run_ours(args) -> None:
                    "achieved_gbs": (v[2] / (v[1] / 1e3) / 1e9) if v[1] > 0 else None}
                for k, v in fams.items()}
     # the oracle baseline runs on rank 0 at N=1 only
-    cpu = cpu_baseline(data, args.workload) if (world == 1 and not args.no_cpu_baseline) else None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_batch(docs) if batch else cpu_baseline(host, args.workload)
     step_sorted = sorted(step_ms)
-    d2h = 4 * (n_words + 1) + s_bytes + 1536 + 32
+    d2h = 4 * (n_words + len(docs)) + s_bytes + 1536 * len(docs) + 32
+    wl = args.workload + (f" (first {nbytes} B)" if args.prefix_bytes else "")
+    if batch and args.batch_docs:
+        wl += f" (first {len(docs)} documents)"
     line = {
         "metric": METRIC, "value": agg["mb_per_s"], "unit": "MB/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded text generator shaped like the paper's Hamlet files)",
-        "config": {"workload": args.workload + (f" (first {nbytes} B)" if args.prefix_bytes else ""),
-                   "bytes": nbytes, "words": n_words, "stream_bytes": s_bytes,
-                   "entry": "bsort_text_device (input resident in HBM)", "parallelism": f"replicas x{world}",
-                   "l2": "flushed between timed steps by writing a 256 MiB buffer"},
+        "config": {"workload": wl, "documents": len(docs), "bytes": nbytes, "words": n_words,
+                   "stream_bytes": s_bytes,
+                   "entry": ("bsort_batch_device (documents packed in one HBM buffer)" if batch
+                             else "bsort_text_device (input resident in HBM)"),
+                   "parallelism": f"replicas x{world}",
+                   "l2": ("inputs larger than L2 (no flush)" if batch
+                          else "flushed between timed steps by writing a 256 MiB buffer")},
         "words_per_s": agg["words_per_s"],
         "p50_ms": step_sorted[len(step_sorted) // 2],
         "p99_ms": step_sorted[min(len(step_sorted) - 1, int(round(0.99 * (len(step_sorted) - 1))))],
@@ -361,11 +452,14 @@ def run_ours(args) -> None:
         "kernels": kernels,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_agg["mb_per_s"], "unit": "MB/s", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": d2h, "entry": "bsort_text (host buffers)",
+                "d2h_bytes_per_step": d2h, "entry": "bsort_batch (host buffers)" if batch else "bsort_text (host buffers)",
                 "ms_per_step": statistics.mean(e2e_t) * 1e3},
         "clocks": clocks,
         "gpu_launches": launches,
     }
+    if plain_per_doc is not None:
+        plain_per_doc["batched_over_plain_words"] = agg["words_per_s"] / world / plain_per_doc["words_per_s"]
+        line["plain_per_doc"] = plain_per_doc
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

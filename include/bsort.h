@@ -133,6 +133,22 @@ bsort_status bsort_batch(bsort_ctx* ctx, const uint8_t* const* docs, const size_
                          bsort_result* outs);
 
 /*
+ * Sorts n independent documents already in device memory, in one pass of the
+ * path (every kernel launch covers all documents).  Document i is the lens[i]
+ * bytes at d_base + offs[i] (any alignment; documents may be packed back to
+ * back).  offs and lens are HOST arrays.  The total must stay below 2^32
+ * bytes (BSORT_E_TOO_LARGE otherwise).  Like bsort_text_device, the call
+ * enqueues the path on `stream`, waits only for the length histograms, and
+ * returns with the scalar fields of outs[i] filled and DEVICE pointers whose
+ * contents are complete once `stream` reaches the point of return.  Each
+ * document's result is identical to bsort_text_device on that document alone.
+ * Returns BSORT_OK when every document succeeded, otherwise the first failing
+ * document's status (outs[i].status per document).
+ */
+bsort_status bsort_batch_device(bsort_ctx* ctx, const uint8_t* d_base, const uint64_t* offs, const uint64_t* lens,
+                                size_t n, void* stream, bsort_result* outs);
+
+/*
  * Kernel tracing.  Every launch is counted; with config.profile == 1 each one
  * is also bracketed by two CUDA events on the stream it runs on, and tagged
  * with the algorithmic bytes it must move (the reads and writes the method

@@ -90,6 +90,10 @@ def load(path: str | None = None):
     lib.bsort_batch.restype = ctypes.c_int
     lib.bsort_batch.argtypes = [ctx_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_size_t),
                                 ctypes.c_size_t, ctypes.POINTER(bsort_result)]
+    lib.bsort_batch_device.restype = ctypes.c_int
+    lib.bsort_batch_device.argtypes = [ctx_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64),
+                                       ctypes.POINTER(ctypes.c_uint64), ctypes.c_size_t, ctypes.c_void_p,
+                                       ctypes.POINTER(bsort_result)]
     lib.bsort_result_release.restype = None
     lib.bsort_result_release.argtypes = [ctx_p, ctypes.POINTER(bsort_result)]
     lib.bsort_profile_read.restype = ctypes.c_int
@@ -159,6 +163,15 @@ def bsort_batch(h, docs: list) -> tuple[int, list[bsort_result]]:
     lens = (ctypes.c_size_t * max(n, 1))(*[a.size for a in arrs])
     outs = (bsort_result * max(n, 1))()
     st = load().bsort_batch(h, ptrs, lens, n, outs)
+    return st, [outs[i] for i in range(n)]
+
+
+def bsort_batch_device(h, base_ptr: int, offs, lens, stream: int) -> tuple[int, list[bsort_result]]:
+    n = len(offs)
+    o = (ctypes.c_uint64 * max(n, 1))(*[int(x) for x in offs])
+    ln = (ctypes.c_uint64 * max(n, 1))(*[int(x) for x in lens])
+    outs = (bsort_result * max(n, 1))()
+    st = load().bsort_batch_device(h, base_ptr or None, o, ln, n, stream or None, outs)
     return st, [outs[i] for i in range(n)]
 
 
@@ -302,6 +315,37 @@ class Context:
                 "stream": view(r.stream, int(r.stream_bytes), "|u1", torch.uint8),
             }
         return out
+
+    def batch_device_raw(self, base, offs, lens, stream=None) -> tuple[int, list[bsort_result]]:
+        """Documents packed in one CUDA uint8 tensor at host-listed offsets;
+        device pointers out (valid once ``stream`` reaches this point)."""
+        import torch
+
+        assert base.is_cuda and base.dtype == torch.uint8 and base.is_contiguous()
+        s = stream if stream is not None else torch.cuda.current_stream(base.device)
+        return bsort_batch_device(self._h, base.data_ptr() if base.numel() else 0, offs, lens, s.cuda_stream)
+
+    def batch_device(self, base, offs, lens, stream=None) -> tuple[int, list[dict]]:
+        """As batch_device_raw, with each document's outputs copied to torch tensors."""
+        import torch
+
+        st, rs = self.batch_device_raw(base, offs, lens, stream)
+        dev = base.device
+
+        def view(ptr, count, typestr, dtype):
+            if count == 0 or not ptr:
+                return torch.zeros(0, dtype=dtype, device=dev)
+            return torch.as_tensor(_DevView(ptr, count, typestr), device=dev).clone()
+
+        out = []
+        with torch.cuda.stream(stream if stream is not None else torch.cuda.current_stream(dev)):
+            for r in rs:
+                n, ml = int(r.n_words), int(r.max_len)
+                out.append({"status": int(r.status), "max_len": ml, "n_words": n, "stream_bytes": int(r.stream_bytes),
+                            "counts": view(r.counts, ml + 1, "<i8", torch.int64),
+                            "offsets": view(r.offsets, n + 1, "<i4", torch.int32) if self.want_offsets else None,
+                            "stream": view(r.stream, int(r.stream_bytes), "|u1", torch.uint8)})
+        return st, out
 
     def batch(self, docs: list) -> tuple[int, list[Result]]:
         st, rs = bsort_batch(self._h, docs)

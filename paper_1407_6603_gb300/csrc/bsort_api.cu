@@ -796,6 +796,48 @@ int bsort_profile_read(bsort_ctx* c, bsort_kernel_stat* out, int max) {
 
 uint64_t bsort_launch_count(const bsort_ctx* c) { return c ? c->launches : 0; }
 
+bsort_status bsort_batch_device(bsort_ctx* c, const uint8_t* d_base, const uint64_t* offs, const uint64_t* lens,
+                                size_t n, void* stream, bsort_result* outs) {
+  if (!c || (n && (!offs || !lens || !outs))) return c ? fail(c, BSORT_E_INVAL, "null argument") : BSORT_E_INVAL;
+  for (size_t i = 0; i < n; ++i) std::memset(&outs[i], 0, sizeof(bsort_result));
+  if (n == 0) return BSORT_OK;
+  if (n >= (1ull << 24)) return fail(c, BSORT_E_TOO_LARGE, "too many documents in one call");
+  uint64_t total = 0;
+  for (size_t i = 0; i < n; ++i) {
+    if (!d_base && lens[i]) return fail(c, BSORT_E_INVAL, "null base with a non-empty document");
+    total += lens[i];
+  }
+  if (total >= (1ull << 32)) return fail(c, BSORT_E_TOO_LARGE, "2^32 bytes or more in one batch");
+  bsort_status s = enter(c);
+  if (s != BSORT_OK) return s;
+  Busy busy(c);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint8_t* base = d_base ? d_base : dptr<uint8_t>(c->meta);  // never dereferenced when every document is empty
+  s = run_path(c, base, offs, lens, (uint32_t)n, st);
+  if (s != BSORT_OK) return s;
+  const uint32_t* h_wbase = hptr<uint32_t>(c->h_meta, c->ml.wbase);
+  const uint32_t* h_lbase = hptr<uint32_t>(c->h_meta, c->ml.lbase);
+  bsort_status first = BSORT_OK;
+  for (uint32_t i = 0; i < (uint32_t)n; ++i) {
+    bsort_result* r = &outs[i];
+    fill_scalars(c, i, r);
+    if (r->status != BSORT_OK) {
+      if (first == BSORT_OK) {
+        first = (bsort_status)r->status;
+        c->err = "document " + std::to_string(i) + ": a word is longer than l_cap";
+      }
+      const uint32_t keep = r->status;
+      std::memset(r, 0, sizeof(*r));
+      r->status = keep;
+      continue;
+    }
+    r->counts = dptr<uint64_t>(c->counts) + (size_t)i * kHist;
+    r->offsets = c->cfg.want_offsets ? dptr<uint32_t>(c->offsets) + h_wbase[i] + i : nullptr;
+    r->stream = dptr<uint8_t>(c->stream) + h_lbase[i];
+  }
+  return first;
+}
+
 void bsort_result_release(bsort_ctx* c, bsort_result* res) {
   (void)c;
   if (res) std::memset(res, 0, sizeof(*res));

@@ -224,3 +224,39 @@ def test_plain_256m_full(ctx, oracle_mod, synth_mod):
     exp = oracle_mod.stable(data, nthreads=oracle_mod.max_threads())
     assert_same_dev(dev, exp, "plain_256m")
     assert exp["max_len"] > 16  # multi-word keys are exercised
+
+
+def test_batch_device_packed_unaligned(ctx, oracle_mod, synth_mod):
+    """Documents packed back to back in one device buffer (so most start at
+    unaligned addresses), with empty and punctuation-only documents among
+    them; each result equals the oracle's for that document alone."""
+    import torch
+
+    docs = [synth_mod.batch_doc(*s) for s in synth_mod.batch_shapes(24)]
+    docs.insert(5, np.zeros(0, np.uint8))
+    docs.insert(9, np.frombuffer(b"!!", np.uint8))
+    docs.append(np.frombuffer(b"tail", np.uint8))
+    lens = [d.size for d in docs]
+    offs = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.uint64).tolist()
+    base = torch.from_numpy(np.concatenate(docs)).cuda()
+    st, outs = ctx.batch_device(base, offs, lens)
+    torch.cuda.synchronize()
+    assert st == 0, ctx.last_error()
+    for i, d in enumerate(docs):
+        assert_same_dev(outs[i], oracle_mod.stable(d, nthreads=8), f"doc {i}")
+
+
+def test_batch_device_reports_failing_document(bsort_gpu, oracle_mod):
+    import torch
+
+    docs = [b"alpha beta", b"x" * 40, b"", b"gamma"]
+    lens = [len(d) for d in docs]
+    offs = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.uint64).tolist()
+    base = torch.frombuffer(bytearray(b"".join(docs)), dtype=torch.uint8).cuda()
+    with bsort_gpu.Context(l_cap=30) as c:
+        st, outs = c.batch_device(base, offs, lens)
+        torch.cuda.synchronize()
+    assert st == bsort_gpu.BSORT_E_WORD_TOO_LONG
+    assert [o["status"] for o in outs] == [0, bsort_gpu.BSORT_E_WORD_TOO_LONG, 0, 0]
+    for i in (0, 2, 3):
+        assert_same_dev(outs[i], oracle_mod.stable(docs[i]), f"doc {i}")
