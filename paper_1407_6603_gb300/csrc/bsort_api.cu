@@ -71,8 +71,9 @@ struct bsort_ctx {
   int device = 0;
   int sm_count = 0;
   cudaStream_t own_stream = nullptr;
-  cudaStream_t side_stream = nullptr;         // K4 of one-tile buckets runs here, beside the clusters
-  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  static constexpr int kSide = 4;
+  cudaStream_t side[kSide] = {};              // the smaller K4 launches run here, beside the clusters of 8
+  cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
   std::string err;
   bool busy = false;
 
@@ -300,13 +301,15 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   }
 
   // ---- bucket layout: one segment per (document, length) ----
-  // Groups, in table order:
-  //   0..4  keys of W = 1, 2, 4, 8, 16 words needing merge passes after K4:
-  //         K4 with clusters of 8, then K5 (one launch per pass and width)
-  //   5     keys of <= 16 words, more than one K4 tile, no pass: K4 with clusters of 8
-  //   6     keys of <= 16 words, one K4 tile: K4 with single CTAs
-  //   7     keys of 32 words (129..255 letters): the narrow-tile kernels of k_sort.cu
-  constexpr int kGroups = 8;
+  // Groups, in table order (T = one K4 tile of the bucket's key width):
+  //   0..3  W = 1, 2, 4, 8 and more than 8T keys: K4 in clusters of 8, then
+  //         K5 merge passes (one launch per pass and width); group 4 unused
+  //   5     (4T, 8T] keys: K4 in clusters of 8        6   (2T, 4T]: clusters of 4
+  //   7     (T, 2T]: clusters of 2                      8   (32 KPT, T]: single CTAs
+  //   9     at most 32 lanes x KPT keys: one warp each
+  //   10,11 keys of 16 / 32 words (65..128 / 129..255 letters): the narrow-tile
+  //         kernels of k_sort.cu
+  constexpr int kGroups = 12;
   c->lookupv.assign((size_t)ndocs * kHist, kNoSegment);
   for (uint32_t d = 0; d < ndocs; ++d)
     if (h_hist[(size_t)d * kHist] != 0) c->doc_status[d] = BSORT_E_WORD_TOO_LONG;
@@ -330,19 +333,28 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
         sg.stream_off = byte_before;
         sg.doc_stream0 = h_lbase[d];
         const int W = width_of_len(L);
+        const uint32_t T = W >= 16 ? 0u : tile2_keys(W);
         uint8_t gi;
-        if (W == 32) {
+        sg.run0 = n;
+        sg.passes = 0;
+        if (W >= 16) {
+          gi = W == 16 ? 10 : 11;
+          sg.run0 = (uint32_t)tile_of_width(W);
+          sg.passes = merge_passes(n, sg.run0);
+        } else if (n <= warp_keys(W)) {
+          gi = 9;
+        } else if (n <= T) {
+          gi = 8;
+        } else if (n <= 2 * T) {
           gi = 7;
-          sg.run0 = (uint32_t)tile_of_width(32);
-          sg.passes = merge_passes(n, sg.run0);
-        } else if (n <= tile2_keys(W)) {
+        } else if (n <= 4 * T) {
           gi = 6;
-          sg.run0 = n;
-          sg.passes = 0;
+        } else if (n <= (uint32_t)kSuperCluster * T) {
+          gi = 5;
         } else {
-          sg.run0 = kSuperCluster * tile2_keys(W);
+          sg.run0 = kSuperCluster * T;
           sg.passes = merge_passes(n, sg.run0);
-          gi = sg.passes ? (uint8_t)class_of_width(W) : 5;
+          gi = (uint8_t)class_of_width(W);
         }
         sg.final_buf = sg.passes & 1u;
         cand.push_back(sg);
@@ -364,11 +376,18 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     for (int g = 0; g < kGroups; ++g) at[g] = gbeg[g];
     for (uint32_t i = 0; i < nseg; ++i) segs[at[group[i]]++] = cand[i];
   }
-  const uint32_t g01 = gbeg[6], g012 = gbeg[7];  // clustered K4 range ends, single-CTA range ends
+  // K4 launches: cluster size and the groups each covers
+  struct K4Launch {
+    int cluster;
+    int g0, g1;  // groups [g0, g1)
+    uint32_t supertiles = 0;
+    int max_w = 1;
+    uint64_t key_bytes = 0;
+  };
+  K4Launch k4[4] = {{8, 0, 6}, {4, 6, 7}, {2, 7, 8}, {1, 8, 9}};
   uint64_t key_words = 0, kb[kGroups] = {};
-  uint32_t etile = 0, stile8 = 0, stile1 = 0, wtile = 0, passes3 = 0;
-  uint32_t mtiles[5] = {}, mpasses[5] = {};
-  int max_w8 = 1, max_w1 = 1;  // widest key of each K4 launch
+  uint32_t etile = 0, wtiles[2] = {0, 0}, wpasses[2] = {0, 0};
+  uint32_t mtiles[4] = {}, mpasses[4] = {};
   for (uint32_t i = 0; i < nseg; ++i) {
     Segment& sg = segs[i];
     const int W = width_of_len(sg.L);
@@ -379,29 +398,28 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     kb[gi] += 8ull * W * sg.n;
     sg.etile0 = etile;
     etile += (sg.n + tile_of_width(W) - 1) / tile_of_width(W);
-    if (gi < 5) {
+    if (gi < 4) {
       sg.tile0 = mtiles[gi];
       mtiles[gi] += (sg.n + merge2_keys(W) - 1) / merge2_keys(W);
       mpasses[gi] = std::max(mpasses[gi], sg.passes);
     }
-    if (gi <= 5) {
-      sg.stile0 = stile8;
-      stile8 += (sg.n + sg.run0 - 1) / sg.run0;
-      max_w8 = std::max(max_w8, W);
-    } else if (gi == 6) {
-      sg.stile0 = stile1++;
-      max_w1 = std::max(max_w1, W);
-    } else {
-      sg.tile0 = wtile;
-      wtile += (sg.n + sg.run0 - 1) / sg.run0;
-      passes3 = std::max(passes3, sg.passes);
+    for (K4Launch& l : k4)
+      if (gi >= l.g0 && gi < l.g1) {
+        const uint32_t super = (uint32_t)l.cluster * tile2_keys(W);
+        sg.stile0 = l.supertiles;
+        l.supertiles += (sg.n + super - 1) / super;
+        l.max_w = std::max(l.max_w, W);
+        l.key_bytes += 8ull * W * sg.n;
+      }
+    if (gi >= 10) {
+      sg.tile0 = wtiles[gi - 10];
+      wtiles[gi - 10] += (sg.n + sg.run0 - 1) / sg.run0;
+      wpasses[gi - 10] = std::max(wpasses[gi - 10], sg.passes);
     }
     c->lookupv[(size_t)sg.doc * kHist + sg.L] = i;
   }
-  uint64_t kb_clustered = 0;
-  for (int g = 0; g <= 5; ++g) kb_clustered += kb[g];
   uint32_t passes2 = 0;
-  for (int g = 0; g < 5; ++g) passes2 = std::max(passes2, mpasses[g]);
+  for (int g = 0; g < 4; ++g) passes2 = std::max(passes2, mpasses[g]);
 
   // ---- upload the layout, size the key and output buffers ----
   const size_t seg_bytes = sizeof(Segment) * std::max<size_t>(nseg, 1);
@@ -436,39 +454,51 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
            "K3 scatter");
   }
   const uint32_t grid_cap = (uint32_t)c->sm_count * 16;
-  // K4: multi-tile buckets in clusters, one-tile buckets in single CTAs, 32-word keys apart
-  if (stile8)
-    LAUNCH(kTileSort, 2.0 * kb_clustered,
-           launch_tile_sort2(kSuperCluster, d_segs, 0, g01, stile8, c->sm_count, max_w8, kA, d_sticky,
-                             c->cfg.wait_limit, st),
-           "K4 tile_sort (clusters)");
-  if (stile1) {
-    // one-tile buckets are independent of the clustered ones: sort them on a
-    // side stream at the same time, joined back before the merge passes
-    cudaStream_t s1 = stile8 ? c->side_stream : st;
-    if (stile8) {
-      CK(cudaEventRecord(c->fork_ev, st), "fork");
-      CK(cudaStreamWaitEvent(s1, c->fork_ev, 0), "fork");
+  // K4: the clusters of 8 on the call's stream; the smaller kernels, which
+  // sort other buckets, each on a side stream at the same time, joined back
+  // before the merge passes
+  const bool side = gbeg[10] > gbeg[6];
+  if (side) CK(cudaEventRecord(c->fork_ev, st), "fork");
+  int used = 0;
+  cudaStream_t joined[bsort_ctx::kSide];
+  auto side_stream = [&]() -> cudaStream_t {
+    cudaStream_t sx = c->side[used];
+    joined[used++] = sx;
+    return sx;
+  };
+  for (const K4Launch& l : k4) {
+    if (!l.supertiles) continue;
+    cudaStream_t sx = st;
+    if (l.cluster != kSuperCluster) {
+      sx = side_stream();
+      CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
     }
-    {
-      Trace tr_(c, s1, kTileSort, 2.0 * kb[6]);
-      CK(tr_.done(launch_tile_sort2(1, d_segs, g01, g012, stile1, c->sm_count, max_w1, kA, d_sticky,
-                                    c->cfg.wait_limit, s1)),
-         "K4 tile_sort");
-    }
-    if (stile8) {
-      CK(cudaEventRecord(c->join_ev, s1), "join");
-      CK(cudaStreamWaitEvent(st, c->join_ev, 0), "join");
-    }
+    Trace tr_(c, sx, kTileSort, 2.0 * l.key_bytes);
+    CK(tr_.done(launch_tile_sort2(l.cluster, d_segs, gbeg[l.g0], gbeg[l.g1], l.supertiles, c->sm_count, l.max_w, kA,
+                                  d_sticky, c->cfg.wait_limit, sx)),
+       "K4 tile_sort");
   }
-  if (wtile)
-    LAUNCH(kTileSort, 2.0 * kb[7],
-           launch_tile_sort(32, d_segs, g012, nseg, wtile, std::min(wtile, grid_cap), kA, d_sticky,
-                            c->cfg.wait_limit, st),
-           "K4 tile_sort (32-word keys)");
+  if (gbeg[10] > gbeg[9]) {
+    cudaStream_t sx = side_stream();
+    CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
+    Trace tr_(c, sx, kTileSort, 2.0 * kb[9]);
+    CK(tr_.done(launch_warp_sort(d_segs, gbeg[9], gbeg[10], kA, sx)), "K4 warp_sort");
+  }
+  for (int i = 0; i < used; ++i) {
+    CK(cudaEventRecord(c->join_ev[i], joined[i]), "join");
+    CK(cudaStreamWaitEvent(st, c->join_ev[i], 0), "join");
+  }
+  for (int g = 10; g < 12; ++g) {
+    const uint32_t tiles = wtiles[g - 10];
+    if (!tiles) continue;
+    LAUNCH(kTileSort, 2.0 * kb[g],
+           launch_tile_sort(g == 10 ? 16 : 32, d_segs, gbeg[g], gbeg[g + 1], tiles, std::min(tiles, grid_cap), kA,
+                            d_sticky, c->cfg.wait_limit, st),
+           "K4 tile_sort (wide keys)");
+  }
   // K5: merge passes over the buckets that need them, one launch per pass and width
   for (uint32_t p = 0; p < passes2; ++p) {
-    for (int g = 0; g < 5; ++g) {
+    for (int g = 0; g < 4; ++g) {
       if (mpasses[g] <= p) continue;
       const int W = width_of_class(g);
       double moved = 0;
@@ -481,14 +511,18 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
              "K5 merge_pass");
     }
   }
-  for (uint32_t p = 0; p < passes3; ++p) {
-    double moved = 0;
-    for (uint32_t i = g012; i < nseg; ++i)
-      if (segs[i].passes > p) moved += 16.0 * 32 * segs[i].n;
-    LAUNCH(kMerge, moved,
-           launch_merge_pass(32, d_segs, g012, nseg, wtile, std::min(wtile, grid_cap), p, (p & 1) ? kB : kA,
-                             (p & 1) ? kA : kB, st),
-           "K5 merge_pass (32-word keys)");
+  for (int g = 10; g < 12; ++g) {
+    const int W = g == 10 ? 16 : 32;
+    const uint32_t tiles = wtiles[g - 10];
+    for (uint32_t p = 0; p < wpasses[g - 10]; ++p) {
+      double moved = 0;
+      for (uint32_t i = gbeg[g]; i < gbeg[g + 1]; ++i)
+        if (segs[i].passes > p) moved += 16.0 * W * segs[i].n;
+      LAUNCH(kMerge, moved,
+             launch_merge_pass(W, d_segs, gbeg[g], gbeg[g + 1], tiles, std::min(tiles, grid_cap), p, (p & 1) ? kB : kA,
+                               (p & 1) ? kA : kB, st),
+             "K5 merge_pass (wide keys)");
+    }
   }
   const uint32_t emit_grid =
       std::max<uint32_t>(1u, std::min<uint32_t>(std::max(etile, (ndocs * kHist + kSortThreads - 1) / kSortThreads),
@@ -597,13 +631,18 @@ bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
   c->device = dev;
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     bsort_destroy(c);  // frees whatever was created
     return BSORT_E_CUDA;
   }
+  for (int i = 0; i < bsort_ctx::kSide; ++i)
+    if (cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      bsort_destroy(c);
+      return BSORT_E_CUDA;
+    }
   // the sticky status word starts cleared
   if (grow(c, c->sticky, sizeof(Meta), "status") != BSORT_OK ||
       grow_host(c, c->h_sticky, sizeof(Meta), "status") != BSORT_OK ||
@@ -627,8 +666,10 @@ void bsort_destroy(bsort_ctx* c) {
     if (b->p) cudaFreeHost(b->p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
-  if (c->join_ev) cudaEventDestroy(c->join_ev);
-  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  for (int i = 0; i < bsort_ctx::kSide; ++i) {
+    if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
+    if (c->side[i]) cudaStreamDestroy(c->side[i]);
+  }
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
 }

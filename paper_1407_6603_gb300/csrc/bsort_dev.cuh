@@ -89,10 +89,9 @@ struct Meta {
   uint32_t pad[3];
 };
 
-// One (document, length) bucket.  The host orders the table as
-//   [buckets that need merge passes, by key width] [other buckets of more
-//   than one K4 tile] [buckets of one K4 tile] [buckets of 129..255-letter words]
-// so that each kernel covers a contiguous range of it.
+// One (document, length) bucket.  The host orders the table by the K4/K5
+// kernels that sort it (see run_path in bsort_api.cu), so that each launch
+// covers a contiguous range of it.
 struct Segment {
   uint64_t key_off;     // first key, in u64 words, in both key buffers
   uint32_t n;           // words in the bucket
@@ -115,6 +114,8 @@ constexpr int kSuperCluster = 8;    // CTAs per K4 cluster
 // keys per K4 CTA tile: 2048 u64 words, 256 keys of 16 words
 __host__ __device__ inline uint32_t tile2_keys(int W) { return (uint32_t)(W >= 16 ? 256 : 2048 / W); }
 __host__ __device__ inline uint32_t merge2_keys(int W) { return (uint32_t)(256 * (W >= 8 ? 1 : 8 / W)); }
+// keys a single warp sorts on its own (32 lanes x keys per thread)
+__host__ __device__ inline uint32_t warp_keys(int W) { return (uint32_t)(32 * (W >= 8 ? 1 : 8 / W)); }
 
 // Work items of the sort and emit kernels are numbered across buckets; a
 // CTA finds the bucket of an item by binary search over the buckets' first
@@ -173,6 +174,7 @@ cudaError_t launch_tile_sort(int W, const Segment* segs, uint32_t sbeg, uint32_t
                              uint32_t grid, uint64_t* keys, Meta* meta, uint64_t wait_limit, cudaStream_t st);
 cudaError_t launch_merge_pass(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st);
+cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, uint64_t* keys, cudaStream_t st);
 cudaError_t launch_tile_sort2(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                               int max_grid, int max_width, uint64_t* keys, Meta* meta, uint64_t wait_limit,
                               cudaStream_t st);

@@ -1,8 +1,8 @@
-// K4 and K5 for the widest keys: 32 u64 words, words of 129..255 letters.
-// Keys of up to 16 words use k_sort2.cu; these kernels keep one CTA of 256
-// threads per tile of 256 keys (a tile of 32-word keys fills 64 KiB of
-// shared memory), the same three odd-even transposition stages, and
-// merge-path passes of one tile per CTA.
+// K4 and K5 for the widest keys: 16 and 32 u64 words, words of 65..255
+// letters (rare in text).  Keys of up to 8 words use k_sort2.cu; these
+// kernels keep one CTA of 256 threads per tile of 256 keys (a tile of 32-word
+// keys fills 64 KiB of shared memory), the same three odd-even transposition
+// stages, and merge-path passes of one tile per CTA.
 #include "bsort_dev.cuh"
 #include "sort_common.cuh"
 
@@ -174,6 +174,7 @@ cudaError_t merge_pass_w(const Segment* segs, uint32_t sbeg, uint32_t send, uint
 cudaError_t launch_tile_sort(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,
                              uint64_t* keys, Meta* meta, uint64_t wait_limit, cudaStream_t st) {
   if (tiles == 0 || grid == 0) return cudaSuccess;
+  if (W == 16) return tile_sort_w<16, 32>(segs, sbeg, send, tiles, grid, keys, meta, wait_limit, st);
   if (W != 32) return cudaErrorInvalidValue;
   return tile_sort_w<32, 32>(segs, sbeg, send, tiles, grid, keys, meta, wait_limit, st);
 }
@@ -181,6 +182,7 @@ cudaError_t launch_tile_sort(int W, const Segment* segs, uint32_t sbeg, uint32_t
 cudaError_t launch_merge_pass(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st) {
   if (tiles == 0 || grid == 0) return cudaSuccess;
+  if (W == 16) return merge_pass_w<16>(segs, sbeg, send, tiles, grid, pass, src, dst, st);
   if (W != 32) return cudaErrorInvalidValue;
   return merge_pass_w<32>(segs, sbeg, send, tiles, grid, pass, src, dst, st);
 }

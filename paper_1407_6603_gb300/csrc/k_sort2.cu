@@ -1,10 +1,9 @@
-// K4 and K5 for keys of up to 16 u64 words (words of up to 128 letters):
+// K4 and K5 for keys of up to 8 u64 words (words of up to 64 letters):
 // phase 3 of the paper's method, the sort of each length bucket into ASCII
 // order (Section II; Section III step 4).
 //
 // K4 (k_tile_sort2<CL>) sorts "supertiles".  One CTA of 256 threads holds a
-// tile of 2048 u64 words (2048 / W keys; 256 keys of 16 words) in shared
-// memory, staged by a TMA bulk copy, and sorts it with the bubble sort's
+// tile of 2048 u64 words (2048 / W keys) in shared memory, staged by a TMA bulk copy, and sorts it with the bubble sort's
 // compare-exchange in its parallel form, odd-even transposition:
 //   1. each thread sorts its 8 / W keys in registers (odd-even transposition);
 //   2. groups of kLanesG lanes run kLanesG rounds of odd-even transposition
@@ -34,7 +33,17 @@ namespace bsort {
 namespace {
 
 constexpr int kT2Threads = 256;
-constexpr int kLanesG = 8;  // lanes per odd-even transposition group
+// Lanes per odd-even transposition group in K4 (the odd-even/merge cutoff:
+// runs of kLanesG * KPT keys leave the transposition stage, merges take them
+// up to the tile) and the CTAs per SM that K4's register budget aims for.
+// Both are tuning constants, set at build time by the autotuning sweep.
+#ifndef BSORT_K4_LANES
+#define BSORT_K4_LANES 4
+#endif
+#ifndef BSORT_K4_MIN_CTAS
+#define BSORT_K4_MIN_CTAS 4
+#endif
+constexpr int kLanesG = BSORT_K4_LANES;
 
 template <int W>
 __host__ __device__ constexpr int kpt2() {
@@ -206,7 +215,7 @@ __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint6
 }
 
 template <int CL>
-__global__ void __launch_bounds__(kT2Threads) k_tile_sort2(const Segment* __restrict__ segs, uint32_t sbeg,
+__global__ void __launch_bounds__(kT2Threads, BSORT_K4_MIN_CTAS) k_tile_sort2(const Segment* __restrict__ segs, uint32_t sbeg,
                                                            uint32_t send, uint32_t nst, uint32_t buf_words,
                                                            uint64_t* keys, Meta* meta, uint64_t wait_limit) {
   extern __shared__ __align__(128) uint64_t sm[];
@@ -235,8 +244,65 @@ __global__ void __launch_bounds__(kT2Threads) k_tile_sort2(const Segment* __rest
       case 1: sort_supertile<1, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, meta, wait_limit); break;
       case 2: sort_supertile<2, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, meta, wait_limit); break;
       case 4: sort_supertile<4, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, meta, wait_limit); break;
-      case 8: sort_supertile<8, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, meta, wait_limit); break;
-      default: sort_supertile<16, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, meta, wait_limit); break;
+      default: sort_supertile<8, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, meta, wait_limit); break;
+    }
+  }
+}
+
+// ------------------------------------------------------- tiny buckets ----
+// Buckets of at most 32 * KPT keys: one warp each.  The keys go to registers
+// (lane l holds keys l*KPT .. l*KPT+KPT-1, +inf past the end), each lane
+// sorts its KPT keys by odd-even transposition, then G lanes, G the smallest
+// power of two that holds the bucket, run G rounds of odd-even transposition
+// between neighbours.  No shared memory and no barrier.
+template <int W, int G>
+__device__ void warp_sort_g(uint64_t* g, uint32_t n) {
+  constexpr int KPT = kpt2<W>();
+  const int lane = threadIdx.x & 31;
+  Key<W> k[KPT];
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    const uint32_t p = lane * KPT + i;
+    k[i] = p < n ? kload<W>(g + (size_t)p * W) : kinf<W>();
+  }
+  oets_registers<W, KPT>(k);
+  if (G > 1) oets_lanes<W, KPT, (G > 1 ? G : 2)>(k);
+#pragma unroll
+  for (int i = 0; i < KPT; ++i) {
+    const uint32_t p = lane * KPT + i;
+    if (p < n) kstore<W>(g + (size_t)p * W, k[i]);
+  }
+}
+
+template <int W>
+__device__ void warp_sort(uint64_t* g, uint32_t n) {
+  constexpr int KPT = kpt2<W>();
+  const uint32_t lanes = (n + KPT - 1) / KPT;
+  if (lanes <= 1)
+    warp_sort_g<W, 1>(g, n);
+  else if (lanes <= 2)
+    warp_sort_g<W, 2>(g, n);
+  else if (lanes <= 4)
+    warp_sort_g<W, 4>(g, n);
+  else if (lanes <= 8)
+    warp_sort_g<W, 8>(g, n);
+  else if (lanes <= 16)
+    warp_sort_g<W, 16>(g, n);
+  else
+    warp_sort_g<W, 32>(g, n);
+}
+
+__global__ void __launch_bounds__(256) k_warp_sort(const Segment* __restrict__ segs, uint32_t sbeg, uint32_t send,
+                                                   uint64_t* keys) {
+  const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  for (uint32_t i = sbeg + blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; i < send; i += warps) {
+    const Segment& sg = segs[i];
+    uint64_t* g = keys + sg.key_off;
+    switch (width_of_len(sg.L)) {
+      case 1: warp_sort<1>(g, sg.n); break;
+      case 2: warp_sort<2>(g, sg.n); break;
+      case 4: warp_sort<4>(g, sg.n); break;
+      default: warp_sort<8>(g, sg.n); break;
     }
   }
 }
@@ -336,7 +402,7 @@ cudaError_t merge_pass2_w(const Segment* segs, uint32_t sbeg, uint32_t send, uin
                           uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st) {
   constexpr uint32_t words = kM2Threads * (W >= 8 ? 1 : 8 / W) * W;
   const size_t smem = (size_t)padded_words(words) * 8;
-  if (smem > 48 * 1024) {
+  if (smem > 48 * 1024) {  // (keep the default carveout: the merge-path probes live in L1)
     cudaError_t e = cudaFuncSetAttribute(k_merge_pass2<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -350,9 +416,12 @@ cudaError_t merge_pass2_w(const Segment* segs, uint32_t sbeg, uint32_t send, uin
 template <int CL>
 cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t nst, int max_grid,
                           int max_width, uint64_t* keys, Meta* meta, uint64_t wait_limit, cudaStream_t st) {
-  const uint32_t buf_words = padded_words(max_width >= 16 ? 4096u : 2048u);
+  (void)max_width;
+  const uint32_t buf_words = padded_words(2048u);
   const size_t smem = (size_t)(CL > 1 ? 2 : 1) * buf_words * 8;
   cudaError_t e = cudaFuncSetAttribute(k_tile_sort2<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)  // shared memory, not L1, limits how many CTAs fit
+    e = cudaFuncSetAttribute(k_tile_sort2<CL>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kT2Threads, 1, 1);
@@ -379,6 +448,14 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
 
 }  // namespace
 
+cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, uint64_t* keys, cudaStream_t st) {
+  if (send <= sbeg) return cudaSuccess;
+  const uint32_t warps = send - sbeg;
+  const uint32_t grid = (warps + 7) / 8 < 152u * 16u ? (warps + 7) / 8 : 152u * 16u;
+  k_warp_sort<<<grid, 256, 0, st>>>(segs, sbeg, send, keys);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tile_sort2(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                               int max_grid, int max_width, uint64_t* keys, Meta* meta, uint64_t wait_limit,
                               cudaStream_t st) {
@@ -400,7 +477,6 @@ cudaError_t launch_merge_pass2(int W, const Segment* segs, uint32_t sbeg, uint32
     case 2: return merge_pass2_w<2>(segs, sbeg, send, tiles, grid, pass, src, dst, st);
     case 4: return merge_pass2_w<4>(segs, sbeg, send, tiles, grid, pass, src, dst, st);
     case 8: return merge_pass2_w<8>(segs, sbeg, send, tiles, grid, pass, src, dst, st);
-    case 16: return merge_pass2_w<16>(segs, sbeg, send, tiles, grid, pass, src, dst, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -260,3 +260,24 @@ def test_batch_device_reports_failing_document(bsort_gpu, oracle_mod):
     assert [o["status"] for o in outs] == [0, bsort_gpu.BSORT_E_WORD_TOO_LONG, 0, 0]
     for i in (0, 2, 3):
         assert_same_dev(outs[i], oracle_mod.stable(docs[i]), f"doc {i}")
+
+
+@pytest.mark.parametrize("W,lengths", [(1, (3, 4, 5, 6, 7, 8)), (2, (9, 10, 12, 13, 15, 16)),
+                                       (4, (17, 20, 24, 28, 31, 32))])
+def test_bucket_sizes_at_kernel_thresholds(ctx, oracle_mod, W, lengths):
+    """Buckets whose sizes sit at and around every K4 boundary for their key
+    width: the warp sort (32 lanes x 8/W keys), one CTA tile (2048/W keys),
+    clusters of 2, 4 and 8 tiles, and the first merge pass."""
+    rng = np.random.default_rng(100 + W)
+    warp, tile = 32 * (8 // W), 2048 // W
+    sizes = [1, warp - 1, warp, warp + 1, tile, tile + 1, 2 * tile + 1, 4 * tile + 1, 8 * tile, 8 * tile + 1,
+             17 * tile + 5]
+    words = []
+    for j, n in enumerate(sizes):
+        L = lengths[j % len(lengths)] if j < len(lengths) else lengths[j % len(lengths)]
+        # a small alphabet gives duplicates and long shared prefixes
+        letters = rng.choice(np.frombuffer(b"abAB", np.uint8), size=(n, L))
+        words.extend(bytes(r) for r in letters)
+    order = rng.permutation(len(words))
+    data = b" ".join(words[i] for i in order)
+    assert_same(ctx.text(data), oracle_mod.stable(data, nthreads=8))
