@@ -54,7 +54,9 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="plain_1m38",
-                   choices=["plain_190k", "plain_1m38", "plain_256m", "batch_4096"])
+                   choices=["plain_190k", "plain_1m38", "plain_256m", "batch_4096", "serve"])
+    p.add_argument("--duration", type=float, default=10.0, help="seconds of Poisson arrivals (serve)")
+    p.add_argument("--pool", type=int, default=256, help="distinct documents the serve stream cycles through")
     p.add_argument("--batch-docs", type=int, default=None, help="use only the first D documents of batch_4096")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -467,10 +469,119 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def run_serve(args) -> None:
+    """The request stream: Poisson arrivals at 2,000 documents/s, each document
+    log-uniform in [1 KiB, 16 MiB] (a pool of distinct documents cycled
+    through), submitted as they arrive to the continuous-batching server and
+    polled back; p50/p99 of submit-to-result latency and the served rate."""
+    import hashlib
+    import threading
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+    import torch
+
+    import paper_1407_6603_gb300 as bs
+    import synth
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return  # the request stream runs on one GPU
+    bs.load()
+    cores = os.cpu_count() or 8
+    with ThreadPoolExecutor(cores) as ex:
+        pool = list(ex.map(synth.serve_doc, range(args.pool)))
+    rate = synth.SERVE["rate"]
+    n_req = int(rate * args.duration)
+    t_arr = synth.arrivals(n_req, rate=rate)
+    ctx = bs.Context(device=local_rank)
+    ctx.serve_start(hbm_budget=64 << 30, workers=2, max_batch_docs=256)
+    # warm-up: every pool document once (not timed), which also fixes each
+    # document's result digest for the checks below
+    first = {}
+    for i, d in enumerate(pool):
+        assert ctx.submit(d, i) == 0
+    while len(first) < len(pool):
+        for tag, res, _ in ctx.poll(256):
+            first[tag] = hashlib.sha256(res.counts.tobytes() + res.offsets.tobytes() + res.stream.tobytes()).hexdigest()
+        time.sleep(0.001)
+    sampler = ClockSampler(local_rank).start()
+    lat, words, nbytes, bad = [], [0], [0], []
+    done = threading.Event()
+    lag = []
+
+    def consumer():
+        got = 0
+        while got < n_req:
+            for tag, res, ns in ctx.poll(256):
+                got += 1
+                lat.append(ns / 1e6)
+                words[0] += res.n_words
+                if tag < len(pool) * 2 and tag % 97 == 0:  # spot check of digests while running
+                    dg = hashlib.sha256(res.counts.tobytes() + res.offsets.tobytes() + res.stream.tobytes()).hexdigest()
+                    if dg != first[tag % len(pool)]:
+                        bad.append(tag)
+            time.sleep(0.0002)
+        done.set()
+
+    th = threading.Thread(target=consumer)
+    t0 = time.perf_counter()
+    th.start()
+    for i in range(n_req):
+        wait = t0 + t_arr[i] - time.perf_counter()
+        if wait > 0:
+            time.sleep(wait)
+        else:
+            lag.append(-wait)
+        d = pool[i % len(pool)]
+        nbytes[0] += d.size
+        assert ctx.submit(d, i) == 0
+    t_submit_end = time.perf_counter()
+    done.wait()
+    t1 = time.perf_counter()
+    th.join()
+    clocks = sampler.stop()
+    ctx.serve_stop()
+    ctx.close()
+    # correctness of the served results: every pool document's digest against the oracle
+    import oracle
+
+    def oracle_digest(d):
+        r = oracle.stable(d, nthreads=1)
+        return hashlib.sha256(r["counts"].astype(np.uint64).tobytes() + r["offsets"].astype(np.uint32).tobytes()
+                              + r["stream"].tobytes()).hexdigest()
+
+    with ThreadPoolExecutor(cores) as ex:
+        odig = list(ex.map(oracle_digest, pool))
+    mismatched = [i for i in range(len(pool)) if odig[i] != first[i]] + bad
+    wall = t1 - t0
+    lat_sorted = sorted(lat)
+    line = {
+        "metric": METRIC, "value": nbytes[0] / wall / 1e6, "unit": "MB/s", "n_gpus": 1, "steps": n_req,
+        "warmup": len(pool), "ms_per_step": wall / n_req * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded text generator)",
+        "config": {"workload": "serve", "requests": n_req, "arrival_rate_per_s": rate, "duration_s": args.duration,
+                   "distinct_documents": len(pool), "bytes": nbytes[0], "entry": "bsort_submit / bsort_poll",
+                   "workers": 2, "hbm_budget_bytes": 64 << 30},
+        "words_per_s": words[0] / wall,
+        "p50_ms": lat_sorted[len(lat_sorted) // 2],
+        "p99_ms": lat_sorted[min(len(lat_sorted) - 1, int(round(0.99 * (len(lat_sorted) - 1))))],
+        "offered_mb_per_s": nbytes[0] / (t_submit_end - t0) / 1e6,
+        "submit_lag_ms_max": max(lag) * 1e3 if lag else 0.0,
+        "results_checked_against_oracle": len(pool) + len([t for t in range(min(n_req, 2 * len(pool))) if t % 97 == 0]),
+        "results_mismatched": len(mismatched),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main(argv=None) -> None:
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

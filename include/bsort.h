@@ -208,6 +208,56 @@ uint64_t bsort_launch_count(const bsort_ctx* ctx);
 bsort_status bsort_strip_noalloc(const uint8_t* d_bytes, size_t len, void* stream, uint8_t* d_letters,
                                  uint32_t* d_starts, uint32_t* d_totals);
 
+/* The configuration a context was created with (device resolved). */
+bsort_status bsort_context_config(const bsort_ctx* ctx, bsort_config* out);
+
+/*
+ * Serving: a request loop with continuous batching (no counterpart in the
+ * paper; it serves many documents as they arrive, with the batch path).
+ *
+ * bsort_serve_start() starts `workers` threads on the context's device, each
+ * with a context of its own.  bsort_submit() copies a document into the
+ * request queue (the caller may reuse its buffer at once).  A worker takes the
+ * queued requests in arrival order, as many as fit max_batch_docs and the
+ * device-memory budget hbm_budget of the requests in flight (a document of n
+ * bytes counts 16 n + 64 KiB), and sorts them with one bsort_batch call; the
+ * workers' batches overlap on the GPU, and requests arriving meanwhile are
+ * admitted as soon as a worker and enough budget are free.  bsort_poll()
+ * hands out finished requests: their tags, their results (HOST pointers,
+ * outs[i].status per request) and, when latency_ns is not NULL, the time from
+ * submission to completion.  The results of one poll stay valid until the
+ * next bsort_poll on the context, bsort_serve_stop + restart, or
+ * bsort_destroy.  Each result equals what bsort_text returns for the document
+ * alone.
+ *
+ * Threads: bsort_submit and bsort_poll may run on two different threads (one
+ * producer, one consumer); no other call on the context may run meanwhile.
+ * bsort_serve_stop() finishes the queued requests and stops the workers;
+ * finished results stay pollable.  bsort_destroy() stops a running server.
+ */
+typedef struct {
+  uint64_t hbm_budget;      /* device bytes the in-flight requests may use (0 = 64 GiB) */
+  uint32_t workers;         /* batches in flight at once, 1..16 (0 = 2) */
+  uint32_t max_batch_docs;  /* requests per batch (0 = 1024) */
+} bsort_serve_config;
+
+void bsort_serve_config_default(bsort_serve_config* cfg);
+
+/* Errors: BSORT_E_INVAL, BSORT_E_BUSY (already serving), and those of bsort_create. */
+bsort_status bsort_serve_start(bsort_ctx* ctx, const bsort_serve_config* cfg);
+
+/* Errors: BSORT_E_INVAL (not serving, NULL bytes), BSORT_E_TOO_LARGE (1 GiB or more,
+ * or more than the whole budget), BSORT_E_BUSY (stopping). */
+bsort_status bsort_submit(bsort_ctx* ctx, const uint8_t* bytes, size_t len, uint64_t tag);
+
+/* Writes up to max finished requests; returns how many. */
+size_t bsort_poll(bsort_ctx* ctx, uint64_t* tags, bsort_result* outs, uint64_t* latency_ns, size_t max);
+
+/* Requests submitted and not yet taken by a worker. */
+size_t bsort_serve_pending(const bsort_ctx* ctx);
+
+bsort_status bsort_serve_stop(bsort_ctx* ctx);
+
 /* Marks a result's buffers as no longer needed and zeroes *res.  The memory
  * itself stays with the context for reuse. */
 void bsort_result_release(bsort_ctx* ctx, bsort_result* res);

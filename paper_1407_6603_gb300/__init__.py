@@ -49,6 +49,10 @@ class bsort_result(ctypes.Structure):
                 ("stream", ctypes.c_void_p)]
 
 
+class bsort_serve_config(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("workers", ctypes.c_uint32), ("max_batch_docs", ctypes.c_uint32)]
+
+
 class BsortError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"bsort {STATUS_NAMES.get(status, status)}: {message}")
@@ -100,6 +104,21 @@ def load(path: str | None = None):
     lib.bsort_profile_read.argtypes = [ctx_p, ctypes.POINTER(bsort_kernel_stat), ctypes.c_int]
     lib.bsort_launch_count.restype = ctypes.c_uint64
     lib.bsort_launch_count.argtypes = [ctx_p]
+    lib.bsort_context_config.restype = ctypes.c_int
+    lib.bsort_context_config.argtypes = [ctx_p, ctypes.POINTER(bsort_config)]
+    lib.bsort_serve_config_default.restype = None
+    lib.bsort_serve_config_default.argtypes = [ctypes.POINTER(bsort_serve_config)]
+    lib.bsort_serve_start.restype = ctypes.c_int
+    lib.bsort_serve_start.argtypes = [ctx_p, ctypes.POINTER(bsort_serve_config)]
+    lib.bsort_submit.restype = ctypes.c_int
+    lib.bsort_submit.argtypes = [ctx_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64]
+    lib.bsort_poll.restype = ctypes.c_size_t
+    lib.bsort_poll.argtypes = [ctx_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(bsort_result),
+                               ctypes.POINTER(ctypes.c_uint64), ctypes.c_size_t]
+    lib.bsort_serve_pending.restype = ctypes.c_size_t
+    lib.bsort_serve_pending.argtypes = [ctx_p]
+    lib.bsort_serve_stop.restype = ctypes.c_int
+    lib.bsort_serve_stop.argtypes = [ctx_p]
     lib.bsort_strip_noalloc.restype = ctypes.c_int
     lib.bsort_strip_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]
@@ -190,6 +209,44 @@ def bsort_profile_read(h) -> dict:
 
 def bsort_launch_count(h) -> int:
     return int(load().bsort_launch_count(h))
+
+
+def bsort_serve_start(h, hbm_budget: int = 0, workers: int = 0, max_batch_docs: int = 0) -> None:
+    cfg = bsort_serve_config()
+    load().bsort_serve_config_default(ctypes.byref(cfg))
+    if hbm_budget:
+        cfg.hbm_budget = hbm_budget
+    if workers:
+        cfg.workers = workers
+    if max_batch_docs:
+        cfg.max_batch_docs = max_batch_docs
+    st = load().bsort_serve_start(h, ctypes.byref(cfg))
+    if st != BSORT_OK:
+        raise BsortError(st, "bsort_serve_start failed")
+
+
+def bsort_submit(h, data, tag: int) -> int:
+    a = _as_u8(data)
+    return int(load().bsort_submit(h, a.ctypes.data if a.size else None, a.size, tag))
+
+
+def bsort_poll(h, max_results: int = 256, want_offsets: bool = True) -> list:
+    """Finished requests: [(tag, Result, latency_ns)], results copied out."""
+    tags = (ctypes.c_uint64 * max_results)()
+    outs = (bsort_result * max_results)()
+    lat = (ctypes.c_uint64 * max_results)()
+    k = int(load().bsort_poll(h, tags, outs, lat, max_results))
+    return [(int(tags[i]), _host_result(outs[i], want_offsets), int(lat[i])) for i in range(k)]
+
+
+def bsort_serve_pending(h) -> int:
+    return int(load().bsort_serve_pending(h))
+
+
+def bsort_serve_stop(h) -> None:
+    st = load().bsort_serve_stop(h)
+    if st != BSORT_OK:
+        raise BsortError(st, "bsort_serve_stop failed")
 
 
 NOALLOC_MAX_BYTES = (64 << 20) - 16
@@ -353,6 +410,21 @@ class Context:
 
     def last_error(self) -> str:
         return bsort_last_error(self._h)
+
+    def serve_start(self, hbm_budget: int = 0, workers: int = 0, max_batch_docs: int = 0) -> None:
+        bsort_serve_start(self._h, hbm_budget, workers, max_batch_docs)
+
+    def submit(self, data, tag: int) -> int:
+        return bsort_submit(self._h, data, tag)
+
+    def poll(self, max_results: int = 256) -> list:
+        return bsort_poll(self._h, max_results, self.want_offsets)
+
+    def serve_pending(self) -> int:
+        return bsort_serve_pending(self._h)
+
+    def serve_stop(self) -> None:
+        bsort_serve_stop(self._h)
 
     def profile_read(self) -> dict:
         return bsort_profile_read(self._h)

@@ -657,6 +657,7 @@ bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
 
 void bsort_destroy(bsort_ctx* c) {
   if (!c) return;
+  bsort_serve_shutdown(c);
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
   for (DevBuf* b : {&c->sticky, &c->k1scratch, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->lookup, &c->segs,
@@ -675,6 +676,13 @@ void bsort_destroy(bsort_ctx* c) {
 }
 
 const char* bsort_last_error(const bsort_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+bsort_status bsort_context_config(const bsort_ctx* c, bsort_config* out) {
+  if (!c || !out) return BSORT_E_INVAL;
+  *out = c->cfg;
+  out->device = c->device;
+  return BSORT_OK;
+}
 
 bsort_status bsort_text(bsort_ctx* c, const uint8_t* bytes, size_t len, bsort_result* out) {
   if (!c || !out || (!bytes && len)) return c ? fail(c, BSORT_E_INVAL, "null argument") : BSORT_E_INVAL;

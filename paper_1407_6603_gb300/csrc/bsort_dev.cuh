@@ -160,6 +160,12 @@ __device__ __forceinline__ uint32_t seg_find(const Segment* segs, uint32_t sbeg,
 }
 #endif
 
+}  // namespace bsort
+// Stops the serving loop of a context, if it runs one (bsort_serve.cu).
+struct bsort_ctx;
+void bsort_serve_shutdown(const struct bsort_ctx* ctx);
+namespace bsort {
+
 // -------- launchers (each returns the launch's cudaError_t) --------
 
 size_t tokenize1p_scratch_bytes(uint32_t nchunks);

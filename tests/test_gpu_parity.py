@@ -281,3 +281,53 @@ def test_bucket_sizes_at_kernel_thresholds(ctx, oracle_mod, W, lengths):
     order = rng.permutation(len(words))
     data = b" ".join(words[i] for i in order)
     assert_same(ctx.text(data), oracle_mod.stable(data, nthreads=8))
+
+
+def test_serving_results_equal_alone(bsort_gpu, oracle_mod, synth_mod):
+    """Continuous batching: requests submitted from one thread while another
+    polls; every result (including a failing one and an empty one) equals the
+    oracle's for that document alone, whatever batch it was served in."""
+    import threading
+    import time
+
+    docs = [synth_mod.batch_doc(*s) for s in synth_mod.batch_shapes(30)]
+    docs[4] = np.zeros(0, np.uint8)
+    docs[7] = np.frombuffer(b"fine " + b"y" * 300 + b" words", np.uint8)  # 300 letters: too long
+    results, lat = {}, {}
+    with bsort_gpu.Context() as c:
+        c.serve_start(hbm_budget=1 << 30, workers=2, max_batch_docs=8)
+
+        def producer():
+            rng = random.Random(1)
+            for i, d in enumerate(docs):
+                assert c.submit(d, i) == 0
+                time.sleep(rng.random() * 0.003)
+
+        th = threading.Thread(target=producer)
+        th.start()
+        deadline = time.time() + 120
+        while len(results) < len(docs) and time.time() < deadline:
+            for tag, res, ns in c.poll(16):
+                results[tag] = res
+                lat[tag] = ns
+            time.sleep(0.001)
+        th.join()
+        c.serve_stop()
+    assert sorted(results) == list(range(len(docs)))
+    for i, d in enumerate(docs):
+        if i == 7:
+            assert results[i].status == bsort_gpu.BSORT_E_WORD_TOO_LONG
+            continue
+        assert results[i].status == 0
+        assert_same(results[i], oracle_mod.stable(d, nthreads=8), f"request {i}")
+        assert lat[i] > 0
+
+
+def test_serving_rejects_over_budget(bsort_gpu):
+    with bsort_gpu.Context() as c:
+        c.serve_start(hbm_budget=1 << 20, workers=1)
+        assert c.submit(np.zeros(1 << 20, np.uint8), 1) == bsort_gpu.BSORT_E_TOO_LARGE
+        assert c.submit(b"small doc", 2) == 0
+        c.serve_stop()
+        got = c.poll(8)
+        assert [t for t, _, _ in got] == [2] and got[0][1].words() == [b"doc", b"small"]
