@@ -60,6 +60,7 @@ def parse_args(argv=None):
     p.add_argument("--batch-docs", type=int, default=None, help="use only the first D documents of batch_4096")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the batched-form summary of the default run")
     p.add_argument("--prefix-bytes", type=int, default=None,
                    help="use only the first B bytes of the workload (profiling captures on smaller cases)")
     return p.parse_args(argv)
@@ -107,10 +108,12 @@ def measured_peaks() -> tuple[float, str]:
 
 
 def kernel_source_sha(family: str) -> str:
-    src = os.path.join(ROOT, "paper_1407_6603_gb300", "csrc", KERNEL_SOURCE[family])
+    """sha256 (16 hex digits) of the family's .cu file and every shared header."""
+    csrc = os.path.join(ROOT, "paper_1407_6603_gb300", "csrc")
     h = hashlib.sha256()
-    for f in (src, os.path.join(ROOT, "paper_1407_6603_gb300", "csrc", "bsort_dev.cuh")):
-        with open(f, "rb") as fh:
+    files = [KERNEL_SOURCE[family]] + sorted(f for f in os.listdir(csrc) if f.endswith(".cuh"))
+    for f in files:
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -308,6 +311,29 @@ def cpu_baseline_batch(docs) -> dict:
 
 
 def run_ours(args) -> None:
+    line = measure(args)
+    if line is None:
+        return
+    if args.workload == "plain_1m38" and not args.no_forms and line["n_gpus"] == 1:
+        # the batched form beside the plain one, on the same GPU (a short run)
+        import torch
+
+        torch.cuda.empty_cache()
+        try:
+            b = measure(parse_args(["--workload", "batch_4096", "--steps", "3", "--warmup", "3", "--no-cpu-baseline",
+                                    "--e2e-steps", "1"]), quiet=True)
+            line["forms"] = {"batch_4096": {
+                "value": b["value"], "unit": "MB/s", "words_per_s": b["words_per_s"], "ms_per_step": b["ms_per_step"],
+                "documents": b["config"]["documents"], "bytes": b["config"]["bytes"],
+                "plain_per_doc_words_per_s": b["plain_per_doc"]["words_per_s"],
+                "batched_over_plain_words": b["plain_per_doc"]["batched_over_plain_words"],
+                "roofline": b["roofline"]}}
+        except Exception as e:  # the main line stands on its own
+            line["forms"] = {"batch_4096": {"error": repr(e)[:200]}}
+    print(json.dumps(line), flush=True)
+
+
+def measure(args, quiet: bool = False):
     import numpy as np
     import torch
 
@@ -318,7 +344,8 @@ def run_ours(args) -> None:
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        if not dist.is_initialized():
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     dev = torch.device("cuda", local_rank)
     bs.load()
     batch = args.workload == "batch_4096"
@@ -410,7 +437,7 @@ def run_ours(args) -> None:
             import torch.distributed as dist
 
             dist.destroy_process_group()
-        return
+        return None
 
     # roofline of the dominant kernel family (largest device time in the timed region)
     fams = {k: v for k, v in prof.items() if v[0] > 0}
@@ -462,11 +489,11 @@ def run_ours(args) -> None:
     if plain_per_doc is not None:
         plain_per_doc["batched_over_plain_words"] = agg["words_per_s"] / world / plain_per_doc["words_per_s"]
         line["plain_per_doc"] = plain_per_doc
-    print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
 
         dist.destroy_process_group()
+    return line
 
 
 def run_serve(args) -> None:
