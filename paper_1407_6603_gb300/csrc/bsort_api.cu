@@ -80,7 +80,7 @@ struct bsort_ctx {
   DevBuf sticky;  // a Meta kept across calls: err_timeout of bounded device waits
   HostBuf h_sticky;
   DevBuf k1scratch;
-  DevBuf in, docs, meta, starts, letters, lookup, segs, cursor, keysA, keysB, counts, offsets, stream;
+  DevBuf in, docs, meta, starts, letters, plan, keysA, keysB, counts, offsets, stream;
   HostBuf h_in, h_docs, h_meta, h_plan, h_counts, h_offsets, h_stream;
 
   // results of the last run (host view)
@@ -422,27 +422,28 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   for (int g = 0; g < 4; ++g) passes2 = std::max(passes2, mpasses[g]);
 
   // ---- upload the layout, size the key and output buffers ----
-  const size_t seg_bytes = sizeof(Segment) * std::max<size_t>(nseg, 1);
-  const size_t lookup_bytes = 4ull * ndocs * kHist;
-  GROW_HOST(c->h_plan, seg_bytes + lookup_bytes, "layout");
+  // segments, the (document, length) -> segment lookup and the zeroed slot
+  // cursors of K3 go to the device in one copy
+  const size_t seg_bytes = align_up(sizeof(Segment) * std::max<size_t>(nseg, 1), 256);
+  const size_t lookup_bytes = align_up(4ull * ndocs * kHist, 256);
+  const size_t cursor_bytes = align_up(4ull * std::max<uint32_t>(nseg, 1), 256);
+  const size_t plan_bytes = seg_bytes + lookup_bytes + cursor_bytes;
+  GROW_HOST(c->h_plan, plan_bytes, "layout");
   if (nseg) std::memcpy(c->h_plan.p, segs.data(), sizeof(Segment) * nseg);
-  std::memcpy(hptr<char>(c->h_plan, seg_bytes), c->lookupv.data(), lookup_bytes);
-  GROW(c->segs, seg_bytes, "segments");
-  GROW(c->lookup, lookup_bytes, "segment lookup");
-  GROW(c->cursor, 4ull * std::max<uint32_t>(nseg, 1), "segment cursors");
+  std::memcpy(hptr<char>(c->h_plan, seg_bytes), c->lookupv.data(), 4ull * ndocs * kHist);
+  std::memset(hptr<char>(c->h_plan, seg_bytes + lookup_bytes), 0, cursor_bytes);
+  GROW(c->plan, plan_bytes, "layout");
   GROW(c->keysA, 8 * std::max<uint64_t>(key_words, 16), "keys");
   GROW(c->keysB, 8 * std::max<uint64_t>(key_words, 16), "keys");
   GROW(c->counts, 8ull * ndocs * kHist, "counts");
   GROW(c->offsets, 4ull * ((uint64_t)n_total + ndocs), "offsets");
   GROW(c->stream, (size_t)s_total + 16, "stream");
-  if (nseg)
-    CK(cudaMemcpyAsync(c->segs.p, c->h_plan.p, sizeof(Segment) * nseg, cudaMemcpyHostToDevice, st),
-       "copy segments");
-  CK(cudaMemcpyAsync(c->lookup.p, hptr<char>(c->h_plan, seg_bytes), lookup_bytes, cudaMemcpyHostToDevice, st),
-     "copy segment lookup");
-  CK(cudaMemsetAsync(c->cursor.p, 0, 4ull * std::max<uint32_t>(nseg, 1), st), "clear cursors");
+  CK(cudaMemcpyAsync(c->plan.p, c->h_plan.p, plan_bytes, cudaMemcpyHostToDevice, st), "copy layout");
+  Segment* const segs_dev = dptr<Segment>(c->plan);
+  uint32_t* const lookup_dev = dptr<uint32_t>(c->plan, seg_bytes);
+  uint32_t* const cursor_dev = dptr<uint32_t>(c->plan, seg_bytes + lookup_bytes);
 
-  const Segment* d_segs = dptr<Segment>(c->segs);
+  const Segment* d_segs = segs_dev;
   uint64_t* kA = dptr<uint64_t>(c->keysA);
   uint64_t* kB = dptr<uint64_t>(c->keysB);
   uint64_t key_bytes_all = 0;
@@ -450,7 +451,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   if (items) {
     LAUNCH(kScatter, (double)s_total + 4.0 * n_total + key_bytes_all,
            launch_scatter(dptr<uint32_t>(c->starts), dptr<uint8_t>(c->letters), d_wbase, d_item0, ndocs, items,
-                          dptr<uint32_t>(c->lookup), d_segs, dptr<uint32_t>(c->cursor), kA, st),
+                          lookup_dev, d_segs, cursor_dev, kA, st),
            "K3 scatter");
   }
   const uint32_t grid_cap = (uint32_t)c->sm_count * 16;
@@ -660,8 +661,7 @@ void bsort_destroy(bsort_ctx* c) {
   bsort_serve_shutdown(c);
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
-  for (DevBuf* b : {&c->sticky, &c->k1scratch, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->lookup, &c->segs,
-                    &c->cursor, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream})
+  for (DevBuf* b : {&c->sticky, &c->k1scratch, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream})
     if (b->p) cudaFree(b->p);
   for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets, &c->h_stream})
     if (b->p) cudaFreeHost(b->p);

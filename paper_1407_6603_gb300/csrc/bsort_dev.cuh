@@ -166,6 +166,20 @@ struct bsort_ctx;
 void bsort_serve_shutdown(const struct bsort_ctx* ctx);
 namespace bsort {
 
+// Runs `set` (kernel attribute calls and the like) once per device for the
+// calling site instead of before every launch.  Repeating it is harmless, so
+// two threads racing on the first call need no lock.
+template <class F>
+inline cudaError_t once_per_device(int (&done)[64], F set) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+  e = set();
+  if (e == cudaSuccess && dev >= 0 && dev < 64) done[dev] = 1;
+  return e;
+}
+
 // -------- launchers (each returns the launch's cudaError_t) --------
 
 size_t tokenize1p_scratch_bytes(uint32_t nchunks);

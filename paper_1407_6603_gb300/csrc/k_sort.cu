@@ -149,10 +149,13 @@ template <int W, int G>
 cudaError_t tile_sort_w(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,
                         uint64_t* keys, Meta* meta, uint64_t wait_limit, cudaStream_t st) {
   const size_t smem = sort_smem_bytes<W>();
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_tile_sort<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  static int attr_done[64];
+  cudaError_t e = once_per_device(attr_done, [&] {
+    return smem > 48 * 1024
+               ? cudaFuncSetAttribute(k_tile_sort<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+               : cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
   k_tile_sort<W, G><<<grid, kSortThreads, smem, st>>>(segs, sbeg, send, tiles, keys, meta, wait_limit);
   return cudaGetLastError();
 }
@@ -161,10 +164,13 @@ template <int W>
 cudaError_t merge_pass_w(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,
                          uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st) {
   const size_t smem = sort_smem_bytes<W>();
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_merge_pass<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  static int attr_done[64];
+  cudaError_t e = once_per_device(attr_done, [&] {
+    return smem > 48 * 1024
+               ? cudaFuncSetAttribute(k_merge_pass<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+               : cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
   k_merge_pass<W><<<grid, kSortThreads, smem, st>>>(segs, sbeg, send, tiles, pass, src, dst);
   return cudaGetLastError();
 }

@@ -339,7 +339,22 @@ __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t
   const uint64_t* B = A + (size_t)la * W;
   uint64_t* out = dst + sg.key_off + (ps + d0) * W;
   if (lb == 0) {  // odd run at the end of the bucket: carried over
-    for (uint32_t e = t; e < cnt * W; e += kM2Threads) out[e] = A[(size_t)d0 * W + e];
+    constexpr int kPer = (T * W + kM2Threads - 1) / kM2Threads;
+    const uint64_t* a = A + (size_t)d0 * W;
+#pragma unroll
+    for (int j0 = 0; j0 < kPer; j0 += 4) {
+      uint64_t v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t e = t + (j0 + j) * kM2Threads;
+        if (e < cnt * W) v[j] = a[e];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t e = t + (j0 + j) * kM2Threads;
+        if (e < cnt * W) out[e] = v[j];
+      }
+    }
     return;
   }
   const uint32_t a0 = (carry.seg == si && carry.ps == ps && carry.d1 == d0)
@@ -350,8 +365,25 @@ __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t
   const uint32_t na = a1 - a0, nb = (d1 - a1) - (d0 - a0);
   const uint64_t* gA = A + (size_t)a0 * W;
   const uint64_t* gB = B + (size_t)(d0 - a0) * W;
-  for (uint32_t e = t; e < na * W; e += kM2Threads) sm[padw(e)] = gA[e];
-  for (uint32_t e = t; e < nb * W; e += kM2Threads) sm[padw(na * W + e)] = gB[e];
+  {
+    // a thread's loads four at a time before their stores, so they fly together
+    constexpr int kPer = (T * W + kM2Threads - 1) / kM2Threads;
+    const uint32_t wa = na * W, tot = cnt * W;
+#pragma unroll
+    for (int j0 = 0; j0 < kPer; j0 += 4) {
+      uint64_t v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t e = t + (j0 + j) * kM2Threads;
+        if (e < tot) v[j] = e < wa ? gA[e] : gB[e - wa];
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t e = t + (j0 + j) * kM2Threads;
+        if (e < tot) sm[padw(e)] = v[j];
+      }
+    }
+  }
   __syncthreads();
   Key<W> k[KPT];
   const uint32_t pos = t * KPT;
@@ -372,7 +404,7 @@ __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t
 
 // One merge pass over the buckets [sbeg, send) of key width W.
 template <int W>
-__global__ void __launch_bounds__(kM2Threads) k_merge_pass2(const Segment* __restrict__ segs, uint32_t sbeg,
+__global__ void __launch_bounds__(kM2Threads, 5) k_merge_pass2(const Segment* __restrict__ segs, uint32_t sbeg,
                                                             uint32_t send, uint32_t tiles, uint32_t pass,
                                                             uint32_t chunk, const uint64_t* __restrict__ src,
                                                             uint64_t* __restrict__ dst) {
@@ -402,10 +434,14 @@ cudaError_t merge_pass2_w(const Segment* segs, uint32_t sbeg, uint32_t send, uin
                           uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st) {
   constexpr uint32_t words = kM2Threads * (W >= 8 ? 1 : 8 / W) * W;
   const size_t smem = (size_t)padded_words(words) * 8;
-  if (smem > 48 * 1024) {  // (keep the default carveout: the merge-path probes live in L1)
-    cudaError_t e = cudaFuncSetAttribute(k_merge_pass2<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
+  // (the default carveout stays: the merge-path probes live in L1)
+  static int attr_done[64];
+  cudaError_t e = once_per_device(attr_done, [&] {
+    return smem > 48 * 1024
+               ? cudaFuncSetAttribute(k_merge_pass2<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+               : cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
   const uint32_t chunk = tiles >= 4u * grid ? 4u : 1u;
   const uint32_t nchunk = (tiles + chunk - 1) / chunk;
   k_merge_pass2<W><<<nchunk < grid ? nchunk : grid, kM2Threads, smem, st>>>(segs, sbeg, send, tiles, pass, chunk,
@@ -419,9 +455,14 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
   (void)max_width;
   const uint32_t buf_words = padded_words(2048u);
   const size_t smem = (size_t)(CL > 1 ? 2 : 1) * buf_words * 8;
-  cudaError_t e = cudaFuncSetAttribute(k_tile_sort2<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)  // shared memory, not L1, limits how many CTAs fit
-    e = cudaFuncSetAttribute(k_tile_sort2<CL>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  static int attr_done[64];
+  static int clusters_cached[64];
+  cudaError_t e = once_per_device(attr_done, [&] {
+    cudaError_t r = cudaFuncSetAttribute(k_tile_sort2<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (r == cudaSuccess)  // shared memory, not L1, limits how many CTAs fit
+      r = cudaFuncSetAttribute(k_tile_sort2<CL>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return r;
+  });
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(kT2Threads, 1, 1);
@@ -434,12 +475,17 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  int clusters = 0;
-  cfg.gridDim = dim3(CL, 1, 1);
-  e = cudaOccupancyMaxActiveClusters(&clusters, k_tile_sort2<CL>, &cfg);
-  if (e != cudaSuccess || clusters <= 0) {
-    cudaGetLastError();
-    clusters = max(1, max_grid / CL);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int clusters = (dev >= 0 && dev < 64) ? clusters_cached[dev] : 0;
+  if (clusters <= 0) {
+    cfg.gridDim = dim3(CL, 1, 1);
+    e = cudaOccupancyMaxActiveClusters(&clusters, k_tile_sort2<CL>, &cfg);
+    if (e != cudaSuccess || clusters <= 0) {
+      cudaGetLastError();
+      clusters = max(1, max_grid / CL);
+    }
+    if (dev >= 0 && dev < 64) clusters_cached[dev] = clusters;
   }
   const uint32_t ncl = nst < (uint32_t)clusters * 2u ? nst : (uint32_t)clusters * 2u;
   cfg.gridDim = dim3(ncl * CL, 1, 1);

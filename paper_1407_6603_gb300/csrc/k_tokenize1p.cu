@@ -440,7 +440,10 @@ cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t n
   cudaError_t e = cudaMemsetAsync(scratch, 0, tokenize1p_scratch_bytes(nchunks), st);
   if (e != cudaSuccess) return e;
   const size_t smem = (size_t)(kChunk / 2) * sizeof(uint32_t);
-  e = cudaFuncSetAttribute(k_tokenize1p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static int attr_done[64];
+  e = once_per_device(attr_done, [&] {
+    return cudaFuncSetAttribute(k_tokenize1p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
   if (e != cudaSuccess) return e;
   k_tokenize1p<<<nchunks ? nchunks : 1u, kTokThreads, smem, st>>>(in, docs, ndocs, nchunks, scratch, letters, starts,
                                                               hist, doc_wbase, doc_lbase, doc_item0, meta, sticky,
