@@ -441,7 +441,8 @@ def measure(args, quiet: bool = False):
 
     # roofline of the dominant kernel family (largest device time in the timed region)
     fams = {k: v for k, v in prof.items() if v[0] > 0}
-    dom = max(fams, key=lambda k: fams[k][1])
+    # host_gap (the call's one host round trip) is reported but is no kernel
+    dom = max((k for k in fams if k != "host_gap"), key=lambda k: fams[k][1])
     launches_d, ms_d, bytes_d = fams[dom]
     peak, peak_src = measured_peaks()
     achieved = bytes_d / (ms_d / 1e3) / 1e9 if ms_d > 0 else 0.0

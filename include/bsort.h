@@ -155,8 +155,9 @@ bsort_status bsort_batch_device(bsort_ctx* ctx, const uint8_t* d_base, const uin
  * needs: input, stripped letters, word starts, keys, output).
  */
 typedef struct {
-  const char* name;   /* kernel family: "tokenize", "scatter", "tile_sort", "merge_pass", "emit"
-                         (static string) */
+  const char* name;   /* kernel family: "tokenize", "scatter", "tile_sort", "merge_pass", "emit";
+                         and "host_gap", the device time of the call's one host round trip (the
+                         length counts read back, the bucket layout copied in) (static string) */
   uint64_t launches;  /* launches since the last read */
   double ms;          /* summed device time of those launches (0 when profiling is off) */
   double bytes;       /* summed algorithmic bytes of those launches */

@@ -55,8 +55,10 @@ struct MetaLayout {
   }
 };
 
-enum Kind { kTokenize, kScatter, kTileSort, kMerge, kEmit, kKinds };
-const char* const kKindName[kKinds] = {"tokenize", "scatter", "tile_sort", "merge_pass", "emit"};
+enum Kind { kTokenize, kScatter, kTileSort, kMerge, kEmit, kHostGap, kKinds };
+// host_gap is no kernel: the device time between the counts reaching the
+// host and the first launch after the layout (the call's one round trip)
+const char* const kKindName[kKinds] = {"tokenize", "scatter", "tile_sort", "merge_pass", "emit", "host_gap"};
 
 struct ProfRec {
   int kind;
@@ -277,6 +279,11 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
          "K1 tokenize");
   CK(cudaMemcpyAsync(c->h_meta.p, c->meta.p, ml.total, cudaMemcpyDeviceToHost, st), "read counts");
   CK(cudaMemcpyAsync(c->h_sticky.p, c->sticky.p, sizeof(Meta), cudaMemcpyDeviceToHost, st), "read status");
+  cudaEvent_t gap_a = nullptr;
+  if (c->cfg.profile) {
+    gap_a = next_event(c);
+    if (gap_a) cudaEventRecord(gap_a, st);
+  }
   CK(cudaStreamSynchronize(st), "wait for counts");
 
   const Meta* hm = hptr<Meta>(c->h_meta, ml.meta);
@@ -443,6 +450,14 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   uint32_t* const lookup_dev = dptr<uint32_t>(c->plan, seg_bytes);
   uint32_t* const cursor_dev = dptr<uint32_t>(c->plan, seg_bytes + lookup_bytes);
 
+  if (gap_a) {  // the round trip ends where the layout copy is enqueued
+    cudaEvent_t gap_b = next_event(c);
+    if (gap_b) {
+      cudaEventRecord(gap_b, st);
+      c->recs.push_back(ProfRec{kHostGap, gap_a, gap_b, 0.0});
+      c->kind_launches[kHostGap] += 1;
+    }
+  }
   const Segment* d_segs = segs_dev;
   uint64_t* kA = dptr<uint64_t>(c->keysA);
   uint64_t* kB = dptr<uint64_t>(c->keysB);
