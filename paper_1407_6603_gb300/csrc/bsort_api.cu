@@ -389,10 +389,14 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     int g0, g1;  // groups [g0, g1)
     uint32_t supertiles = 0;
     int max_w = 1;
-    uint64_t key_bytes = 0;
+    double key_bytes = 0;
   };
   K4Launch k4[4] = {{8, 0, 6}, {4, 6, 7}, {2, 7, 8}, {1, 8, 9}};
+  // bytes of a bucket's output: its letters and, if asked for, its offsets
+  const uint64_t off_bytes = c->cfg.want_offsets ? 4 : 0;
+  auto out_bytes = [&](const Segment& sg) { return (double)sg.n * (sg.L + off_bytes); };
   uint64_t key_words = 0, kb[kGroups] = {};
+  double ob[kGroups] = {};
   uint32_t etile = 0, wtiles[2] = {0, 0}, wpasses[2] = {0, 0};
   uint32_t mtiles[4] = {}, mpasses[4] = {};
   for (uint32_t i = 0; i < nseg; ++i) {
@@ -403,8 +407,11 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     sg.key_off = key_words;
     key_words += align_up((size_t)sg.n * W, 16);
     kb[gi] += 8ull * W * sg.n;
-    sg.etile0 = etile;
-    etile += (sg.n + tile_of_width(W) - 1) / tile_of_width(W);
+    ob[gi] += out_bytes(sg);
+    if (gi >= 10) {  // only the wide keys go through K6
+      sg.etile0 = etile;
+      etile += (sg.n + tile_of_width(W) - 1) / tile_of_width(W);
+    }
     if (gi < 4) {
       sg.tile0 = mtiles[gi];
       mtiles[gi] += (sg.n + merge2_keys(W) - 1) / merge2_keys(W);
@@ -416,7 +423,8 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
         sg.stile0 = l.supertiles;
         l.supertiles += (sg.n + super - 1) / super;
         l.max_w = std::max(l.max_w, W);
-        l.key_bytes += 8ull * W * sg.n;
+        // keys in, then runs out for K5 or the sorted words out
+        l.key_bytes += 8.0 * W * sg.n + (sg.passes ? 8.0 * W * sg.n : out_bytes(sg));
       }
     if (gi >= 10) {
       sg.tile0 = wtiles[gi - 10];
@@ -463,13 +471,19 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   uint64_t* kB = dptr<uint64_t>(c->keysB);
   uint64_t key_bytes_all = 0;
   for (int g = 0; g < kGroups; ++g) key_bytes_all += kb[g];
-  if (items) {
-    LAUNCH(kScatter, (double)s_total + 4.0 * n_total + key_bytes_all,
-           launch_scatter(dptr<uint32_t>(c->starts), dptr<uint8_t>(c->letters), d_wbase, d_item0, ndocs, items,
-                          lookup_dev, d_segs, cursor_dev, kA, st),
+  const uint32_t grid_cap = (uint32_t)c->sm_count * 16;
+  const EmitOut eo{dptr<uint8_t>(c->stream), dptr<uint32_t>(c->offsets), c->cfg.want_offsets};
+  {
+    // K3 also writes each document's counts and closing offset, so it runs
+    // even when no document has a word
+    const uint32_t count_grid = std::min<uint32_t>((ndocs * kHist + kWordThreads - 1) / kWordThreads, grid_cap);
+    const uint32_t grid = std::max<uint32_t>(std::max(items, count_grid), 1u);
+    LAUNCH(kScatter,
+           (double)s_total + 4.0 * n_total + key_bytes_all + (4.0 + 8.0) * kHist * ndocs + (off_bytes ? 12.0 : 0.0) * ndocs,
+           launch_scatter(dptr<uint32_t>(c->starts), dptr<uint8_t>(c->letters), d_wbase, d_lbase, d_item0, ndocs,
+                          items, grid, lookup_dev, d_segs, cursor_dev, kA, d_hist, dptr<uint64_t>(c->counts), eo, st),
            "K3 scatter");
   }
-  const uint32_t grid_cap = (uint32_t)c->sm_count * 16;
   // K4: the clusters of 8 on the call's stream; the smaller kernels, which
   // sort other buckets, each on a side stream at the same time, joined back
   // before the merge passes
@@ -489,16 +503,16 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       sx = side_stream();
       CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
     }
-    Trace tr_(c, sx, kTileSort, 2.0 * l.key_bytes);
+    Trace tr_(c, sx, kTileSort, l.key_bytes);
     CK(tr_.done(launch_tile_sort2(l.cluster, d_segs, gbeg[l.g0], gbeg[l.g1], l.supertiles, c->sm_count, l.max_w, kA,
-                                  d_sticky, c->cfg.wait_limit, sx)),
+                                  eo, d_sticky, c->cfg.wait_limit, sx)),
        "K4 tile_sort");
   }
   if (gbeg[10] > gbeg[9]) {
     cudaStream_t sx = side_stream();
     CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
-    Trace tr_(c, sx, kTileSort, 2.0 * kb[9]);
-    CK(tr_.done(launch_warp_sort(d_segs, gbeg[9], gbeg[10], kA, sx)), "K4 warp_sort");
+    Trace tr_(c, sx, kTileSort, (double)kb[9] + ob[9]);
+    CK(tr_.done(launch_warp_sort(d_segs, gbeg[9], gbeg[10], kA, eo, sx)), "K4 warp_sort");
   }
   for (int i = 0; i < used; ++i) {
     CK(cudaEventRecord(c->join_ev[i], joined[i]), "join");
@@ -517,13 +531,14 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     for (int g = 0; g < 4; ++g) {
       if (mpasses[g] <= p) continue;
       const int W = width_of_class(g);
-      double moved = 0;
+      double moved = 0;  // keys in, then keys out or, at a bucket's last pass, its words
       for (uint32_t i = gbeg[g]; i < gbeg[g + 1]; ++i)
-        if (segs[i].passes > p) moved += 16.0 * W * segs[i].n;
+        if (segs[i].passes > p)
+          moved += 8.0 * W * segs[i].n + (segs[i].passes == p + 1 ? out_bytes(segs[i]) : 8.0 * W * segs[i].n);
       LAUNCH(kMerge, moved,
              launch_merge_pass2(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g],
                                 std::min<uint32_t>(mtiles[g], (uint32_t)c->sm_count * 8), p, (p & 1) ? kB : kA,
-                                (p & 1) ? kA : kB, st),
+                                (p & 1) ? kA : kB, eo, st),
              "K5 merge_pass");
     }
   }
@@ -540,15 +555,11 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
              "K5 merge_pass (wide keys)");
     }
   }
-  const uint32_t emit_grid =
-      std::max<uint32_t>(1u, std::min<uint32_t>(std::max(etile, (ndocs * kHist + kSortThreads - 1) / kSortThreads),
-                                                grid_cap));
-  const double emit_bytes = (double)key_bytes_all + s_total +
-                            (c->cfg.want_offsets ? 4.0 * ((double)n_total + ndocs) : 0.0) + 8.0 * kHist * ndocs;
-  LAUNCH(kEmit, emit_bytes,
-         launch_emit(d_segs, nseg, etile, emit_grid, kA, kB, d_hist, d_wbase, d_lbase, ndocs, c->cfg.want_offsets,
-                     dptr<uint8_t>(c->stream), dptr<uint32_t>(c->offsets), dptr<uint64_t>(c->counts), st),
-         "K6 emit");
+  // K6: the words of the wide keys (every other bucket was emitted by its sort)
+  if (etile) {
+    LAUNCH(kEmit, (double)kb[10] + kb[11] + ob[10] + ob[11],
+           launch_emit(d_segs, gbeg[10], gbeg[12], etile, std::min(etile, grid_cap), kA, kB, eo, st), "K6 emit");
+  }
   return BSORT_OK;
 }
 

@@ -124,7 +124,80 @@ __host__ __device__ inline uint32_t warp_keys(int W) { return (uint32_t)(32 * (W
 // costs no global loads.
 constexpr uint32_t kSegCache = 256;
 
+// Where sorted words go: the output stream and per-word offsets.
+struct EmitOut {
+  uint8_t* stream;
+  uint32_t* offsets;
+  int want_offsets;
+};
+
 #if defined(__CUDACC__)
+// Quotient n / L by one wide multiply with m = ceil(2^32 / L), a 33-bit
+// number for L = 1 (division by an invariant integer through its scaled
+// reciprocal, after Granlund and Montgomery, 1994).  With e = m L - 2^32 < L,
+// n m / 2^32 exceeds n / L by n e / (L 2^32), under 1 / L while n e < 2^32,
+// which leaves the floor unchanged: exact for every n < 2^24 and L < 256.
+__host__ __device__ __forceinline__ uint64_t recip_of(uint32_t L) { return ((1ull << 32) + L - 1) / L; }
+__host__ __device__ __forceinline__ uint32_t quot(uint32_t n, uint64_t m) { return (uint32_t)(((uint64_t)n * m) >> 32); }
+
+// Emits keys [k0, k0 + cnt) of bucket sg, sorted, as the letters of the
+// words (phase 3's output, Section II: each length's sorted words, shorter
+// lengths first) and the words' offsets within their document.  key_word(j, q)
+// gives u64 word q of key k0 + j: big-endian letters, zero past the word's L
+// letters.  The tile's bytes are one contiguous range of the stream (at most
+// 2^24 bytes): the NTH threads write its 16-byte aligned middle with whole
+// 16-byte stores, each gathering its 16 bytes piece by piece (one piece = the
+// rest of one key word, at most 8 bytes), and its ragged ends byte by byte,
+// so no byte outside the range is touched and tiles never overlap.
+template <int NTH, class F>
+__device__ __forceinline__ void emit_tile(const Segment& sg, uint32_t k0, uint32_t cnt, F key_word,
+                                          const EmitOut& eo) {
+  const uint32_t L = sg.L;
+  const uint64_t m = recip_of(L);
+  const int t = threadIdx.x;
+  uint8_t* const p0 = eo.stream + sg.stream_off + (size_t)k0 * L;
+  const uint32_t nbytes = cnt * L;
+  const uint32_t head = min(nbytes, (uint32_t)((16u - ((uintptr_t)p0 & 15u)) & 15u));
+  const uint32_t chunks = (nbytes - head) >> 4;
+  const uint32_t tail0 = head + chunks * 16u;
+  for (uint32_t off = t; off < head + (nbytes - tail0); off += NTH) {  // the ragged ends
+    const uint32_t o = off < head ? off : tail0 + (off - head);
+    const uint32_t j = quot(o, m), b = o - j * L;
+    p0[o] = (uint8_t)(key_word(j, b >> 3) >> (56 - 8 * (b & 7)));
+  }
+  for (uint32_t c = t; c < chunks; c += NTH) {
+    const uint32_t off = head + c * 16u;
+    uint32_t j = quot(off, m), b = off - j * L;
+    uint64_t hi = 0, lo = 0;  // the chunk, big-endian from the top of hi
+    uint32_t nb = 0;          // bytes gathered so far
+    do {
+      const uint32_t s = b & 7;
+      const uint32_t take = min(8u, L - (b & ~7u)) - s;  // letters left in this key word
+      const uint64_t v = key_word(j, b >> 3) << (8 * s);
+      if (nb < 8) {
+        hi |= v >> (8 * nb);
+        if (nb) lo |= v << (64 - 8 * nb);
+      } else {
+        lo |= v >> (8 * (nb - 8));
+      }
+      nb += take;
+      b += take;
+      if (b == L) {
+        b = 0;
+        ++j;
+      }
+    } while (nb < 16);
+    const uint32_t h1 = (uint32_t)(hi >> 32), h0 = (uint32_t)hi, l1 = (uint32_t)(lo >> 32), l0 = (uint32_t)lo;
+    *reinterpret_cast<uint4*>(p0 + off) =
+        make_uint4(__byte_perm(h1, 0, 0x0123), __byte_perm(h0, 0, 0x0123), __byte_perm(l1, 0, 0x0123),
+                   __byte_perm(l0, 0, 0x0123));
+  }
+  if (eo.want_offsets) {
+    const uint32_t rel = sg.stream_off - sg.doc_stream0 + k0 * L;
+    for (uint32_t j = t; j < cnt; j += NTH) eo.offsets[sg.out_word + k0 + j] = rel + j * L;
+  }
+}
+
 // Field selector: which first-item number a kernel searches by.
 enum SegField { kByTile0, kByStile0, kByEtile0 };
 template <SegField F>
@@ -188,21 +261,22 @@ cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t n
                               uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
                               Meta* sticky, uint32_t l_cap, uint64_t wait_limit, cudaStream_t st);
 cudaError_t launch_scatter(const uint32_t* starts, const uint8_t* letters, const uint32_t* doc_wbase,
-                           const uint32_t* doc_item0, uint32_t ndocs, uint32_t items, const uint32_t* seg_lookup,
-                           const Segment* segs, uint32_t* cursor, uint64_t* keys, cudaStream_t st);
+                           const uint32_t* doc_lbase, const uint32_t* doc_item0, uint32_t ndocs, uint32_t items,
+                           uint32_t grid, const uint32_t* seg_lookup, const Segment* segs, uint32_t* cursor,
+                           uint64_t* keys, const uint32_t* hist, uint64_t* counts, EmitOut eo, cudaStream_t st);
 cudaError_t launch_tile_sort(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
                              uint32_t grid, uint64_t* keys, Meta* meta, uint64_t wait_limit, cudaStream_t st);
 cudaError_t launch_merge_pass(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st);
-cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, uint64_t* keys, cudaStream_t st);
+cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, uint64_t* keys, EmitOut eo,
+                             cudaStream_t st);
 cudaError_t launch_tile_sort2(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
-                              int max_grid, int max_width, uint64_t* keys, Meta* meta, uint64_t wait_limit,
-                              cudaStream_t st);
+                              int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
+                              uint64_t wait_limit, cudaStream_t st);
 cudaError_t launch_merge_pass2(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
-                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st);
-cudaError_t launch_emit(const Segment* segs, uint32_t nseg, uint32_t tiles, uint32_t grid, const uint64_t* keysA,
-                        const uint64_t* keysB, const uint32_t* hist, const uint32_t* doc_wbase,
-                        const uint32_t* doc_lbase, uint32_t ndocs, int want_offsets, uint8_t* stream,
-                        uint32_t* offsets, uint64_t* counts, cudaStream_t st);
+                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, EmitOut eo,
+                               cudaStream_t st);
+cudaError_t launch_emit(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,
+                        const uint64_t* keysA, const uint64_t* keysB, EmitOut eo, cudaStream_t st);
 
 }  // namespace bsort

@@ -10,8 +10,10 @@
 // of a bucket come out in no fixed order (the sort that follows makes the
 // result unique anyway).
 //
-// K6 writes the result: the buckets in ascending length, each word unpacked
-// back to its L letters, the per-word offsets and the per-length counts.
+// The sort kernels write each bucket's words as soon as its keys are final
+// (emit_tile in bsort_dev.cuh); K3 also writes the per-length counts and each
+// document's closing offset, and K6 only emits the buckets of words of 65 or
+// more letters, which the narrow-tile kernels sort.
 #include "bsort_dev.cuh"
 
 namespace bsort {
@@ -31,13 +33,19 @@ __device__ __forceinline__ uint32_t doc_of_item(const uint32_t* doc_item0, uint3
 
 constexpr int kWordsPerThread = kWordBlock / kWordThreads;
 
-__global__ void __launch_bounds__(kWordThreads) k_scatter(const uint32_t* __restrict__ starts,
-                                                          const uint8_t* __restrict__ letters,
-                                                          const uint32_t* __restrict__ doc_wbase,
-                                                          const uint32_t* __restrict__ doc_item0, uint32_t ndocs,
-                                                          uint32_t items, const uint32_t* __restrict__ seg_lookup,
-                                                          const Segment* __restrict__ segs,
-                                                          uint32_t* __restrict__ cursor, uint64_t* __restrict__ keys) {
+__global__ void __launch_bounds__(kWordThreads) k_scatter(
+    const uint32_t* __restrict__ starts, const uint8_t* __restrict__ letters, const uint32_t* __restrict__ doc_wbase,
+    const uint32_t* __restrict__ doc_lbase, const uint32_t* __restrict__ doc_item0, uint32_t ndocs, uint32_t items,
+    const uint32_t* __restrict__ seg_lookup, const Segment* __restrict__ segs, uint32_t* __restrict__ cursor,
+    uint64_t* __restrict__ keys, const uint32_t* __restrict__ hist, uint64_t* __restrict__ counts, EmitOut eo) {
+  // per-document counts (bin 0 is always 0 in a result) and each document's
+  // closing offset; the words themselves are emitted by the sort kernels
+  const uint32_t gsz = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ndocs * kHist; i += gsz) {
+    const uint32_t d = i / kHist, L = i % kHist;
+    counts[i] = L ? hist[i] : 0ull;
+    if (L == 0 && eo.want_offsets) eo.offsets[doc_wbase[d + 1] + d] = doc_lbase[d + 1] - doc_lbase[d];
+  }
   __shared__ uint32_t cnt[kHist];
   __shared__ uint32_t base[kHist];
   __shared__ uint32_t s_doc;
@@ -92,67 +100,44 @@ __global__ void __launch_bounds__(kWordThreads) k_scatter(const uint32_t* __rest
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_emit(const Segment* __restrict__ segs, uint32_t nseg,
+// K6: words of the buckets whose keys the narrow-tile kernels sorted (keys of
+// 16 and 32 words), from the key buffer they ended in.
+__global__ void __launch_bounds__(kSortThreads) k_emit(const Segment* __restrict__ segs, uint32_t sbeg, uint32_t send,
                                                        uint32_t tiles, const uint64_t* __restrict__ keysA,
-                                                       const uint64_t* __restrict__ keysB,
-                                                       const uint32_t* __restrict__ hist,
-                                                       const uint32_t* __restrict__ doc_wbase,
-                                                       const uint32_t* __restrict__ doc_lbase, uint32_t ndocs,
-                                                       int want_offsets, uint8_t* __restrict__ stream,
-                                                       uint32_t* __restrict__ offsets, uint64_t* __restrict__ counts) {
-  // per-document counts (bin 0 is always 0 in a result) and the closing offset
-  const uint32_t gsz = gridDim.x * blockDim.x;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ndocs * kHist; i += gsz) {
-    const uint32_t d = i / kHist, L = i % kHist;
-    counts[i] = L ? hist[i] : 0ull;
-    if (L == 0 && want_offsets) offsets[doc_wbase[d + 1] + d] = doc_lbase[d + 1] - doc_lbase[d];
-  }
+                                                       const uint64_t* __restrict__ keysB, EmitOut eo) {
   __shared__ uint32_t s_seg;
   __shared__ uint32_t s_first[kSegCache];
-  const bool cached = nseg ? seg_cache_fill<kByEtile0>(segs, 0, nseg, s_first) : false;
+  const bool cached = seg_cache_fill<kByEtile0>(segs, sbeg, send, s_first);
   for (uint32_t it = blockIdx.x; it < tiles; it += gridDim.x) {
-    if (threadIdx.x == 0) s_seg = seg_find<kByEtile0>(segs, 0, nseg, s_first, cached, it);
+    if (threadIdx.x == 0) s_seg = seg_find<kByEtile0>(segs, sbeg, send, s_first, cached, it);
     __syncthreads();
     const Segment sg = segs[s_seg];
     __syncthreads();
-    const uint32_t L = sg.L;
-    const int W = width_of_len(L);
+    const int W = width_of_len(sg.L);
     const uint32_t T = (uint32_t)tile_of_width(W);
     const uint32_t j0 = (it - sg.etile0) * T;
     const uint32_t cnt = min(T, sg.n - j0);
-    const uint64_t* src = (sg.final_buf ? keysB : keysA) + sg.key_off;
-    for (uint32_t j = threadIdx.x; j < cnt; j += kSortThreads) {
-      const uint32_t k = j0 + j;
-      const uint64_t* kp = src + (size_t)k * W;
-      uint8_t* dst = stream + sg.stream_off + (size_t)k * L;
-      uint64_t v = 0;
-      for (uint32_t b = 0; b < L; ++b) {
-        if ((b & 7) == 0) v = kp[b >> 3];
-        dst[b] = (uint8_t)(v >> (56 - 8 * (b & 7)));
-      }
-      if (want_offsets) offsets[sg.out_word + k] = sg.stream_off - sg.doc_stream0 + k * L;
-    }
+    const uint64_t* src = (sg.final_buf ? keysB : keysA) + sg.key_off + (size_t)j0 * W;
+    emit_tile<kSortThreads>(sg, j0, cnt, [&](uint32_t j, uint32_t q) { return src[(size_t)j * W + q]; }, eo);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_scatter(const uint32_t* starts, const uint8_t* letters, const uint32_t* doc_wbase,
-                           const uint32_t* doc_item0, uint32_t ndocs, uint32_t items, const uint32_t* seg_lookup,
-                           const Segment* segs, uint32_t* cursor, uint64_t* keys, cudaStream_t st) {
-  if (items == 0) return cudaSuccess;
-  k_scatter<<<items, kWordThreads, 0, st>>>(starts, letters, doc_wbase, doc_item0, ndocs, items, seg_lookup, segs,
-                                            cursor, keys);
+                           const uint32_t* doc_lbase, const uint32_t* doc_item0, uint32_t ndocs, uint32_t items,
+                           uint32_t grid, const uint32_t* seg_lookup, const Segment* segs, uint32_t* cursor,
+                           uint64_t* keys, const uint32_t* hist, uint64_t* counts, EmitOut eo, cudaStream_t st) {
+  if (grid == 0) return cudaSuccess;
+  k_scatter<<<grid, kWordThreads, 0, st>>>(starts, letters, doc_wbase, doc_lbase, doc_item0, ndocs, items, seg_lookup,
+                                           segs, cursor, keys, hist, counts, eo);
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const Segment* segs, uint32_t nseg, uint32_t tiles, uint32_t grid, const uint64_t* keysA,
-                        const uint64_t* keysB, const uint32_t* hist, const uint32_t* doc_wbase,
-                        const uint32_t* doc_lbase, uint32_t ndocs, int want_offsets, uint8_t* stream,
-                        uint32_t* offsets, uint64_t* counts, cudaStream_t st) {
-  if (grid == 0) return cudaSuccess;
-  k_emit<<<grid, kSortThreads, 0, st>>>(nseg ? segs : nullptr, nseg, nseg ? tiles : 0u, keysA, keysB, hist,
-                                        doc_wbase, doc_lbase, ndocs, want_offsets, stream, offsets, counts);
+cudaError_t launch_emit(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,
+                        const uint64_t* keysA, const uint64_t* keysB, EmitOut eo, cudaStream_t st) {
+  if (tiles == 0 || grid == 0 || send <= sbeg) return cudaSuccess;
+  k_emit<<<grid, kSortThreads, 0, st>>>(segs, sbeg, send, tiles, keysA, keysB, eo);
   return cudaGetLastError();
 }
 

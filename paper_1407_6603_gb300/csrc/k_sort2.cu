@@ -55,6 +55,10 @@ __host__ __device__ constexpr uint32_t tile_words2() {
 }
 
 constexpr int kM2Threads = 256;
+// CTAs per SM that K5's register budget aims for (a tuning constant).
+#ifndef BSORT_K5_MIN_CTAS
+#define BSORT_K5_MIN_CTAS 4
+#endif
 
 // Shared-memory layout of a tile: one pad word after every 16 u64 words, so
 // that threads reading keys KPT*W words apart (their own runs) or at random
@@ -180,7 +184,8 @@ __device__ void cluster_merge(uint64_t* buf0, uint64_t* buf1, uint32_t r) {
 
 template <int W, int CL>
 __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint64_t* keys, uint64_t* buf0,
-                               uint64_t* buf1, uint64_t* bar, uint32_t& phase, Meta* meta, uint64_t wait_limit) {
+                               uint64_t* buf1, uint64_t* bar, uint32_t& phase, const EmitOut& eo, Meta* meta,
+                               uint64_t wait_limit) {
   constexpr int KPT = kpt2<W>();
   constexpr uint32_t T = kT2Threads * KPT;
   constexpr uint32_t TW = T * W;
@@ -210,14 +215,19 @@ __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint6
   }
   cta_sort<W, kLanesG>(buf0);
   if constexpr (CL > 1) cluster_merge<W, CL>(buf0, buf1, r);
-  for (uint32_t e = t; e < cnt * W; e += kT2Threads) g[e] = buf0[padw(e)];
+  if (sg.passes == 0) {  // the bucket is sorted: its words go straight out
+    emit_tile<kT2Threads>(sg, (uint32_t)j0, cnt, [&](uint32_t j, uint32_t q) { return buf0[padw(j * W + q)]; }, eo);
+  } else {  // a run of CL tiles for K5
+    for (uint32_t e = t; e < cnt * W; e += kT2Threads) g[e] = buf0[padw(e)];
+  }
   __syncthreads();
 }
 
 template <int CL>
 __global__ void __launch_bounds__(kT2Threads, BSORT_K4_MIN_CTAS) k_tile_sort2(const Segment* __restrict__ segs, uint32_t sbeg,
                                                            uint32_t send, uint32_t nst, uint32_t buf_words,
-                                                           uint64_t* keys, Meta* meta, uint64_t wait_limit) {
+                                                           uint64_t* keys, EmitOut eo, Meta* meta,
+                                                           uint64_t wait_limit) {
   extern __shared__ __align__(128) uint64_t sm[];
   uint64_t* buf0 = sm;
   uint64_t* buf1 = sm + buf_words;
@@ -241,10 +251,10 @@ __global__ void __launch_bounds__(kT2Threads, BSORT_K4_MIN_CTAS) k_tile_sort2(co
     const Segment sg = segs[s_seg];
     __syncthreads();
     switch (width_of_len(sg.L)) {
-      case 1: sort_supertile<1, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, meta, wait_limit); break;
-      case 2: sort_supertile<2, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, meta, wait_limit); break;
-      case 4: sort_supertile<4, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, meta, wait_limit); break;
-      default: sort_supertile<8, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, meta, wait_limit); break;
+      case 1: sort_supertile<1, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
+      case 2: sort_supertile<2, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
+      case 4: sort_supertile<4, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
+      default: sort_supertile<8, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
     }
   }
 }
@@ -256,7 +266,7 @@ __global__ void __launch_bounds__(kT2Threads, BSORT_K4_MIN_CTAS) k_tile_sort2(co
 // power of two that holds the bucket, run G rounds of odd-even transposition
 // between neighbours.  No shared memory and no barrier.
 template <int W, int G>
-__device__ void warp_sort_g(uint64_t* g, uint32_t n) {
+__device__ void warp_sort_g(const Segment& sg, const uint64_t* g, uint32_t n, const EmitOut& eo) {
   constexpr int KPT = kpt2<W>();
   const int lane = threadIdx.x & 31;
   Key<W> k[KPT];
@@ -267,42 +277,52 @@ __device__ void warp_sort_g(uint64_t* g, uint32_t n) {
   }
   oets_registers<W, KPT>(k);
   if (G > 1) oets_lanes<W, KPT, (G > 1 ? G : 2)>(k);
+  // the bucket is sorted: each lane writes its keys' letters and offsets
+  const uint32_t L = sg.L;
 #pragma unroll
   for (int i = 0; i < KPT; ++i) {
     const uint32_t p = lane * KPT + i;
-    if (p < n) kstore<W>(g + (size_t)p * W, k[i]);
+    if (p < n) {
+      uint8_t* dst = eo.stream + sg.stream_off + (size_t)p * L;
+#pragma unroll
+      for (int q = 0; q < W; ++q)
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+          if ((uint32_t)(q * 8 + b) < L) dst[q * 8 + b] = (uint8_t)(k[i].w[q] >> (56 - 8 * b));
+      if (eo.want_offsets) eo.offsets[sg.out_word + p] = sg.stream_off - sg.doc_stream0 + p * L;
+    }
   }
 }
 
 template <int W>
-__device__ void warp_sort(uint64_t* g, uint32_t n) {
+__device__ void warp_sort(const Segment& sg, const uint64_t* g, uint32_t n, const EmitOut& eo) {
   constexpr int KPT = kpt2<W>();
   const uint32_t lanes = (n + KPT - 1) / KPT;
   if (lanes <= 1)
-    warp_sort_g<W, 1>(g, n);
+    warp_sort_g<W, 1>(sg, g, n, eo);
   else if (lanes <= 2)
-    warp_sort_g<W, 2>(g, n);
+    warp_sort_g<W, 2>(sg, g, n, eo);
   else if (lanes <= 4)
-    warp_sort_g<W, 4>(g, n);
+    warp_sort_g<W, 4>(sg, g, n, eo);
   else if (lanes <= 8)
-    warp_sort_g<W, 8>(g, n);
+    warp_sort_g<W, 8>(sg, g, n, eo);
   else if (lanes <= 16)
-    warp_sort_g<W, 16>(g, n);
+    warp_sort_g<W, 16>(sg, g, n, eo);
   else
-    warp_sort_g<W, 32>(g, n);
+    warp_sort_g<W, 32>(sg, g, n, eo);
 }
 
 __global__ void __launch_bounds__(256) k_warp_sort(const Segment* __restrict__ segs, uint32_t sbeg, uint32_t send,
-                                                   uint64_t* keys) {
+                                                   const uint64_t* keys, EmitOut eo) {
   const uint32_t warps = gridDim.x * (blockDim.x / 32);
   for (uint32_t i = sbeg + blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; i < send; i += warps) {
     const Segment& sg = segs[i];
-    uint64_t* g = keys + sg.key_off;
+    const uint64_t* g = keys + sg.key_off;
     switch (width_of_len(sg.L)) {
-      case 1: warp_sort<1>(g, sg.n); break;
-      case 2: warp_sort<2>(g, sg.n); break;
-      case 4: warp_sort<4>(g, sg.n); break;
-      default: warp_sort<8>(g, sg.n); break;
+      case 1: warp_sort<1>(sg, g, sg.n, eo); break;
+      case 2: warp_sort<2>(sg, g, sg.n, eo); break;
+      case 4: warp_sort<4>(sg, g, sg.n, eo); break;
+      default: warp_sort<8>(sg, g, sg.n, eo); break;
     }
   }
 }
@@ -322,7 +342,7 @@ struct SplitCarry {
 template <int W>
 __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t pass,
                            const uint64_t* __restrict__ src, uint64_t* __restrict__ dst, uint64_t* sm,
-                           SplitCarry& carry) {
+                           SplitCarry& carry, const EmitOut& eo) {
   constexpr int KPT = W >= 8 ? 1 : 8 / W;
   constexpr uint32_t T = kM2Threads * KPT;
   const int t = threadIdx.x;
@@ -338,6 +358,12 @@ __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t
   const uint64_t* A = src + sg.key_off + ps * W;
   const uint64_t* B = A + (size_t)la * W;
   uint64_t* out = dst + sg.key_off + (ps + d0) * W;
+  const bool last = pass + 1 == sg.passes;  // this pass's output is the sorted bucket
+  if (lb == 0 && last) {  // odd run at the end of the bucket, already in place
+    const uint64_t* a = A + (size_t)d0 * W;
+    emit_tile<kM2Threads>(sg, (uint32_t)out0, cnt, [&](uint32_t j, uint32_t q) { return a[(size_t)j * W + q]; }, eo);
+    return;
+  }
   if (lb == 0) {  // odd run at the end of the bucket: carried over
     constexpr int kPer = (T * W + kM2Threads - 1) / kM2Threads;
     const uint64_t* a = A + (size_t)d0 * W;
@@ -398,16 +424,19 @@ __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t
   for (int s = 0; s < KPT; ++s)
     if (pos + s < cnt) kstore<W>(pkey<W>(sm, pos + s), k[s]);
   __syncthreads();
-  for (uint32_t e = t; e < cnt * W; e += kM2Threads) out[e] = sm[padw(e)];
+  if (last)
+    emit_tile<kM2Threads>(sg, (uint32_t)out0, cnt, [&](uint32_t j, uint32_t q) { return sm[padw(j * W + q)]; }, eo);
+  else
+    for (uint32_t e = t; e < cnt * W; e += kM2Threads) out[e] = sm[padw(e)];
   __syncthreads();
 }
 
 // One merge pass over the buckets [sbeg, send) of key width W.
 template <int W>
-__global__ void __launch_bounds__(kM2Threads, 5) k_merge_pass2(const Segment* __restrict__ segs, uint32_t sbeg,
+__global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_pass2(const Segment* __restrict__ segs, uint32_t sbeg,
                                                             uint32_t send, uint32_t tiles, uint32_t pass,
                                                             uint32_t chunk, const uint64_t* __restrict__ src,
-                                                            uint64_t* __restrict__ dst) {
+                                                            uint64_t* __restrict__ dst, EmitOut eo) {
   extern __shared__ __align__(128) uint64_t sm[];
   __shared__ uint32_t s_seg;
   __shared__ uint32_t s_first[kSegCache];
@@ -425,13 +454,13 @@ __global__ void __launch_bounds__(kM2Threads, 5) k_merge_pass2(const Segment* __
       const Segment sg = segs[si];
       __syncthreads();
       if (sg.passes <= pass) continue;  // this bucket is already one run
-      merge_tile<W>(sg, si, it, pass, src, dst, sm, carry);
+      merge_tile<W>(sg, si, it, pass, src, dst, sm, carry, eo);
     }
 }
 
 template <int W>
 cudaError_t merge_pass2_w(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,
-                          uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st) {
+                          uint32_t pass, const uint64_t* src, uint64_t* dst, const EmitOut& eo, cudaStream_t st) {
   constexpr uint32_t words = kM2Threads * (W >= 8 ? 1 : 8 / W) * W;
   const size_t smem = (size_t)padded_words(words) * 8;
   // (the default carveout stays: the merge-path probes live in L1)
@@ -445,13 +474,14 @@ cudaError_t merge_pass2_w(const Segment* segs, uint32_t sbeg, uint32_t send, uin
   const uint32_t chunk = tiles >= 4u * grid ? 4u : 1u;
   const uint32_t nchunk = (tiles + chunk - 1) / chunk;
   k_merge_pass2<W><<<nchunk < grid ? nchunk : grid, kM2Threads, smem, st>>>(segs, sbeg, send, tiles, pass, chunk,
-                                                                            src, dst);
+                                                                            src, dst, eo);
   return cudaGetLastError();
 }
 
 template <int CL>
 cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t nst, int max_grid,
-                          int max_width, uint64_t* keys, Meta* meta, uint64_t wait_limit, cudaStream_t st) {
+                          int max_width, uint64_t* keys, const EmitOut& eo, Meta* meta, uint64_t wait_limit,
+                          cudaStream_t st) {
   (void)max_width;
   const uint32_t buf_words = padded_words(2048u);
   const size_t smem = (size_t)(CL > 1 ? 2 : 1) * buf_words * 8;
@@ -489,40 +519,42 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
   }
   const uint32_t ncl = nst < (uint32_t)clusters * 2u ? nst : (uint32_t)clusters * 2u;
   cfg.gridDim = dim3(ncl * CL, 1, 1);
-  return cudaLaunchKernelEx(&cfg, k_tile_sort2<CL>, segs, sbeg, send, nst, buf_words, keys, meta, wait_limit);
+  return cudaLaunchKernelEx(&cfg, k_tile_sort2<CL>, segs, sbeg, send, nst, buf_words, keys, eo, meta, wait_limit);
 }
 
 }  // namespace
 
-cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, uint64_t* keys, cudaStream_t st) {
+cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, uint64_t* keys, EmitOut eo,
+                             cudaStream_t st) {
   if (send <= sbeg) return cudaSuccess;
   const uint32_t warps = send - sbeg;
   const uint32_t grid = (warps + 7) / 8 < 152u * 16u ? (warps + 7) / 8 : 152u * 16u;
-  k_warp_sort<<<grid, 256, 0, st>>>(segs, sbeg, send, keys);
+  k_warp_sort<<<grid, 256, 0, st>>>(segs, sbeg, send, keys, eo);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tile_sort2(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
-                              int max_grid, int max_width, uint64_t* keys, Meta* meta, uint64_t wait_limit,
-                              cudaStream_t st) {
+                              int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
+                              uint64_t wait_limit, cudaStream_t st) {
   if (supertiles == 0) return cudaSuccess;
   switch (cluster) {
-    case 1: return tile_sort2_cl<1>(segs, sbeg, send, supertiles, max_grid, max_width, keys, meta, wait_limit, st);
-    case 2: return tile_sort2_cl<2>(segs, sbeg, send, supertiles, max_grid, max_width, keys, meta, wait_limit, st);
-    case 4: return tile_sort2_cl<4>(segs, sbeg, send, supertiles, max_grid, max_width, keys, meta, wait_limit, st);
-    case 8: return tile_sort2_cl<8>(segs, sbeg, send, supertiles, max_grid, max_width, keys, meta, wait_limit, st);
+    case 1: return tile_sort2_cl<1>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 2: return tile_sort2_cl<2>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 4: return tile_sort2_cl<4>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 8: return tile_sort2_cl<8>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_merge_pass2(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
-                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st) {
+                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, EmitOut eo,
+                               cudaStream_t st) {
   if (tiles == 0 || grid == 0) return cudaSuccess;
   switch (W) {
-    case 1: return merge_pass2_w<1>(segs, sbeg, send, tiles, grid, pass, src, dst, st);
-    case 2: return merge_pass2_w<2>(segs, sbeg, send, tiles, grid, pass, src, dst, st);
-    case 4: return merge_pass2_w<4>(segs, sbeg, send, tiles, grid, pass, src, dst, st);
-    case 8: return merge_pass2_w<8>(segs, sbeg, send, tiles, grid, pass, src, dst, st);
+    case 1: return merge_pass2_w<1>(segs, sbeg, send, tiles, grid, pass, src, dst, eo, st);
+    case 2: return merge_pass2_w<2>(segs, sbeg, send, tiles, grid, pass, src, dst, eo, st);
+    case 4: return merge_pass2_w<4>(segs, sbeg, send, tiles, grid, pass, src, dst, eo, st);
+    case 8: return merge_pass2_w<8>(segs, sbeg, send, tiles, grid, pass, src, dst, eo, st);
     default: return cudaErrorInvalidValue;
   }
 }
