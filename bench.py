@@ -43,7 +43,7 @@ FALLBACK_HBM_GBS = 6800.0
 # Kernel families and the source file that holds each (for the traffic record).
 KERNEL_SOURCE = {
     "tokenize": "k_tokenize1p.cu", "scatter": "k_scatter.cu", "emit": "k_scatter.cu",
-    "tile_sort": "k_sort2.cu", "merge_pass": "k_sort2.cu",
+    "tile_sort": "k_sort2.cu", "merge_pass": "k_sort2.cu", "merge_cut": "k_sort2.cu",
 }
 
 

@@ -155,7 +155,8 @@ bsort_status bsort_batch_device(bsort_ctx* ctx, const uint8_t* d_base, const uin
  * needs: input, stripped letters, word starts, keys, output).
  */
 typedef struct {
-  const char* name;   /* kernel family: "tokenize", "scatter", "tile_sort", "merge_pass", "emit";
+  const char* name;   /* kernel family: "tokenize", "scatter", "tile_sort", "merge_pass",
+                         "merge_cut" (the tile cuts of a pipelined merge pass), "emit";
                          and "host_gap", the device time of the call's one host round trip (the
                          length counts read back, the bucket layout copied in) (static string) */
   uint64_t launches;  /* launches since the last read */

@@ -55,10 +55,11 @@ struct MetaLayout {
   }
 };
 
-enum Kind { kTokenize, kScatter, kTileSort, kMerge, kEmit, kHostGap, kKinds };
+enum Kind { kTokenize, kScatter, kTileSort, kMerge, kMergeCut, kEmit, kHostGap, kKinds };
 // host_gap is no kernel: the device time between the counts reaching the
 // host and the first launch after the layout (the call's one round trip)
-const char* const kKindName[kKinds] = {"tokenize", "scatter", "tile_sort", "merge_pass", "emit", "host_gap"};
+const char* const kKindName[kKinds] = {"tokenize", "scatter",  "tile_sort", "merge_pass",
+                                       "merge_cut", "emit",     "host_gap"};
 
 struct ProfRec {
   int kind;
@@ -82,7 +83,7 @@ struct bsort_ctx {
   DevBuf sticky;  // a Meta kept across calls: err_timeout of bounded device waits
   HostBuf h_sticky;
   DevBuf k1scratch;
-  DevBuf in, docs, meta, starts, letters, plan, keysA, keysB, counts, offsets, stream;
+  DevBuf in, docs, meta, starts, letters, plan, keysA, keysB, counts, offsets, stream, jobs;
   HostBuf h_in, h_docs, h_meta, h_plan, h_counts, h_offsets, h_stream;
 
   // results of the last run (host view)
@@ -526,7 +527,18 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
                             d_sticky, c->cfg.wait_limit, st),
            "K4 tile_sort (wide keys)");
   }
-  // K5: merge passes over the buckets that need them, one launch per pass and width
+  // K5: merge passes over the buckets that need them, one launch per pass and
+  // width.  With at least two tiles per resident CTA the pass is pipelined: a
+  // cut kernel lists every tile's slices first, so that the merge kernel can
+  // load one tile while it merges another.
+  const uint32_t piped_grid = (uint32_t)(c->sm_count * merge_piped_ctas_per_sm());
+  uint64_t job_at[4] = {}, jobs_total = 0;
+  for (int g = 0; g < 4; ++g)
+    if (mtiles[g] >= 2 * piped_grid) {
+      job_at[g] = jobs_total;
+      jobs_total += mtiles[g];
+    }
+  if (jobs_total) GROW(c->jobs, sizeof(TileJob) * jobs_total, "merge jobs");
   for (uint32_t p = 0; p < passes2; ++p) {
     for (int g = 0; g < 4; ++g) {
       if (mpasses[g] <= p) continue;
@@ -535,11 +547,19 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       for (uint32_t i = gbeg[g]; i < gbeg[g + 1]; ++i)
         if (segs[i].passes > p)
           moved += 8.0 * W * segs[i].n + (segs[i].passes == p + 1 ? out_bytes(segs[i]) : 8.0 * W * segs[i].n);
-      LAUNCH(kMerge, moved,
-             launch_merge_pass2(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g],
-                                std::min<uint32_t>(mtiles[g], (uint32_t)c->sm_count * 8), p, (p & 1) ? kB : kA,
-                                (p & 1) ? kA : kB, eo, st),
-             "K5 merge_pass");
+      const uint64_t* src = (p & 1) ? kB : kA;
+      uint64_t* dst = (p & 1) ? kA : kB;
+      if (mtiles[g] >= 2 * piped_grid) {
+        TileJob* jobs = dptr<TileJob>(c->jobs) + job_at[g];
+        LAUNCH(kMergeCut, 0.0, launch_merge_cut(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g], p, src, jobs, st),
+               "K5 merge cut");
+        LAUNCH(kMerge, moved, launch_merge_piped(W, jobs, mtiles[g], piped_grid, src, dst, eo, st), "K5 merge_pass");
+      } else {
+        LAUNCH(kMerge, moved,
+               launch_merge_pass2(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g],
+                                  std::min<uint32_t>(mtiles[g], (uint32_t)c->sm_count * 8), p, src, dst, eo, st),
+               "K5 merge_pass");
+      }
     }
   }
   for (int g = 10; g < 12; ++g) {
@@ -687,7 +707,7 @@ void bsort_destroy(bsort_ctx* c) {
   bsort_serve_shutdown(c);
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
-  for (DevBuf* b : {&c->sticky, &c->k1scratch, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream})
+  for (DevBuf* b : {&c->sticky, &c->k1scratch, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream, &c->jobs})
     if (b->p) cudaFree(b->p);
   for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets, &c->h_stream})
     if (b->p) cudaFreeHost(b->p);

@@ -109,6 +109,22 @@ struct Segment {
   uint32_t pad[2];
 };
 
+// One output tile of a pipelined merge pass (K5), as the cut kernel leaves it:
+// where the tile's slices of the two runs start, how many keys each gives,
+// and where its output goes.
+struct TileJob {
+  uint64_t a_src;   // word offset in the source key buffer of the tile's slice of run A
+  uint64_t b_src;   // the same for run B
+  uint64_t dst;     // word offset in the destination key buffer of the tile's first output
+  uint32_t na, nb;  // keys taken from A and from B; both 0: nothing to do
+  uint32_t L;       // 0: the merged keys go to dst; else this pass finishes the bucket
+                    // and its words (of L letters) are emitted:
+  uint32_t stream;  //   stream byte offset of the tile's first word
+  uint32_t word;    //   offsets[] index of that word
+  uint32_t rel;     //   its offset within its document
+};
+static_assert(sizeof(TileJob) == 48, "TileJob is three 16-byte copies");
+
 // K4 v2 / K5 v2 geometry (keys of at most 16 u64 words).
 constexpr int kSuperCluster = 8;    // CTAs per K4 cluster
 // keys per K4 CTA tile: 2048 u64 words, 256 keys of 16 words
@@ -140,22 +156,20 @@ struct EmitOut {
 __host__ __device__ __forceinline__ uint64_t recip_of(uint32_t L) { return ((1ull << 32) + L - 1) / L; }
 __host__ __device__ __forceinline__ uint32_t quot(uint32_t n, uint64_t m) { return (uint32_t)(((uint64_t)n * m) >> 32); }
 
-// Emits keys [k0, k0 + cnt) of bucket sg, sorted, as the letters of the
-// words (phase 3's output, Section II: each length's sorted words, shorter
-// lengths first) and the words' offsets within their document.  key_word(j, q)
-// gives u64 word q of key k0 + j: big-endian letters, zero past the word's L
-// letters.  The tile's bytes are one contiguous range of the stream (at most
-// 2^24 bytes): the NTH threads write its 16-byte aligned middle with whole
-// 16-byte stores, each gathering its 16 bytes piece by piece (one piece = the
-// rest of one key word, at most 8 bytes), and its ragged ends byte by byte,
-// so no byte outside the range is touched and tiles never overlap.
+// Emits cnt sorted keys of L letters as the letters of the words (phase 3's
+// output, Section II: each length's sorted words, shorter lengths first) at p0
+// and, when offs is set, word j's offset within its document, rel0 + j L, at
+// offs[j].  key_word(j, q) gives u64 word q of key j: big-endian letters, zero
+// past the word's L letters.  The run's bytes are one contiguous range of the
+// stream (at most 2^24 bytes): the NTH threads write its 16-byte aligned
+// middle with whole 16-byte stores, each gathering its 16 bytes piece by piece
+// (one piece = the rest of one key word, at most 8 bytes), and its ragged ends
+// byte by byte, so no byte outside the range is touched and runs never overlap.
 template <int NTH, class F>
-__device__ __forceinline__ void emit_tile(const Segment& sg, uint32_t k0, uint32_t cnt, F key_word,
-                                          const EmitOut& eo) {
-  const uint32_t L = sg.L;
+__device__ __forceinline__ void emit_run(uint32_t L, uint8_t* p0, uint32_t* offs, uint32_t rel0, uint32_t cnt,
+                                         F key_word) {
   const uint64_t m = recip_of(L);
   const int t = threadIdx.x;
-  uint8_t* const p0 = eo.stream + sg.stream_off + (size_t)k0 * L;
   const uint32_t nbytes = cnt * L;
   const uint32_t head = min(nbytes, (uint32_t)((16u - ((uintptr_t)p0 & 15u)) & 15u));
   const uint32_t chunks = (nbytes - head) >> 4;
@@ -192,10 +206,17 @@ __device__ __forceinline__ void emit_tile(const Segment& sg, uint32_t k0, uint32
         make_uint4(__byte_perm(h1, 0, 0x0123), __byte_perm(h0, 0, 0x0123), __byte_perm(l1, 0, 0x0123),
                    __byte_perm(l0, 0, 0x0123));
   }
-  if (eo.want_offsets) {
-    const uint32_t rel = sg.stream_off - sg.doc_stream0 + k0 * L;
-    for (uint32_t j = t; j < cnt; j += NTH) eo.offsets[sg.out_word + k0 + j] = rel + j * L;
-  }
+  if (offs)
+    for (uint32_t j = t; j < cnt; j += NTH) offs[j] = rel0 + j * L;
+}
+
+// emit_run for keys [k0, k0 + cnt) of bucket sg.
+template <int NTH, class F>
+__device__ __forceinline__ void emit_tile(const Segment& sg, uint32_t k0, uint32_t cnt, F key_word,
+                                          const EmitOut& eo) {
+  emit_run<NTH>(sg.L, eo.stream + sg.stream_off + (size_t)k0 * sg.L,
+                eo.want_offsets ? eo.offsets + sg.out_word + k0 : nullptr, sg.stream_off - sg.doc_stream0 + k0 * sg.L,
+                cnt, key_word);
 }
 
 // Field selector: which first-item number a kernel searches by.
@@ -276,6 +297,15 @@ cudaError_t launch_tile_sort2(int cluster, const Segment* segs, uint32_t sbeg, u
 cudaError_t launch_merge_pass2(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
                                uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, EmitOut eo,
                                cudaStream_t st);
+// Pipelined K5 for passes with many tiles: the cut kernel finds every tile's
+// slices (one warp per tile), then the merge kernel streams the tiles through
+// two shared-memory buffers, loading one while it merges the other.
+cudaError_t launch_merge_cut(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t pass,
+                             const uint64_t* src, TileJob* jobs, cudaStream_t st);
+cudaError_t launch_merge_piped(int W, const TileJob* jobs, uint32_t tiles, uint32_t grid, const uint64_t* src,
+                               uint64_t* dst, EmitOut eo, cudaStream_t st);
+// CTAs per SM of the pipelined merge kernel.
+int merge_piped_ctas_per_sm();
 cudaError_t launch_emit(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,
                         const uint64_t* keysA, const uint64_t* keysB, EmitOut eo, cudaStream_t st);
 

@@ -458,6 +458,139 @@ __global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_pass2(c
     }
 }
 
+// ------------------------------------------------- pipelined K5 ----
+// The cut kernel: one warp per output tile of the pass.  Its two half-warps
+// find, by a 16-way merge-path search each, where the tile's first and its
+// last-plus-one outputs cut the two runs; lane 0 writes the tile's job.
+template <int W>
+__global__ void __launch_bounds__(256) k_merge_cut(const Segment* __restrict__ segs, uint32_t sbeg, uint32_t send,
+                                                   uint32_t tiles, uint32_t pass, const uint64_t* __restrict__ src,
+                                                   TileJob* __restrict__ jobs) {
+  constexpr int KPT = W >= 8 ? 1 : 8 / W;
+  constexpr uint32_t T = kM2Threads * KPT;
+  __shared__ uint32_t s_first[kSegCache];
+  const bool cached = seg_cache_fill<kByTile0>(segs, sbeg, send, s_first);
+  const int lane = threadIdx.x & 31, half = lane >> 4, h = lane & 15;
+  const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  for (uint32_t it = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < tiles; it += warps) {
+    const uint32_t si = seg_find<kByTile0>(segs, sbeg, send, s_first, cached, it);
+    const Segment& sg = segs[si];
+    TileJob job{};
+    const uint32_t passes = sg.passes;
+    if (passes > pass) {  // else the bucket is one run already: nothing to do
+      const uint64_t n = sg.n, R = (uint64_t)sg.run0 << pass;
+      const uint64_t out0 = (uint64_t)(it - sg.tile0) * T;
+      const uint64_t ps = out0 / (2 * R) * (2 * R);
+      const uint32_t la = (uint32_t)min(R, n - ps);
+      const uint32_t lb = n - ps > R ? (uint32_t)min(R, n - ps - R) : 0u;
+      const uint32_t d0 = (uint32_t)(out0 - ps);
+      const uint32_t d1 = d0 + min(T, la + lb - d0);
+      const uint64_t* A = src + sg.key_off + ps * W;
+      const uint64_t* B = A + (size_t)la * W;
+      const uint32_t d = half ? d1 : d0;
+      uint32_t lo = d > lb ? d - lb : 0u, hi = d < la ? d : la;
+      for (;;) {
+        const bool more = hi > lo;
+        if (!__any_sync(kFull, more)) break;
+        const uint32_t span = hi - lo;
+        const uint32_t step = span <= 16u ? 1u : (span + 15u) / 16u;
+        const uint32_t m = lo + (uint32_t)h * step;
+        bool f = false;  // A[m] goes before the diagonal's B key: the cut is past m
+        if (more && m < hi) f = !klt(kload<W>(B + (size_t)(d - 1 - m) * W), kload<W>(A + (size_t)m * W));
+        const uint32_t nf = __popc((__ballot_sync(kFull, f) >> (16 * half)) & 0xffffu);
+        if (more) {  // the cut lies after the last probe that says so, up to the next probe
+          const uint32_t nhi = lo + nf * step < hi ? lo + nf * step : hi;
+          lo = nf == 0 ? lo : lo + (nf - 1) * step + 1;
+          hi = nhi;
+        }
+      }
+      const uint32_t a0 = __shfl_sync(kFull, lo, 0), a1 = __shfl_sync(kFull, lo, 16);
+      job.a_src = sg.key_off + (ps + a0) * W;
+      job.b_src = sg.key_off + (ps + la + (d0 - a0)) * W;
+      job.dst = sg.key_off + out0 * W;
+      job.na = a1 - a0;
+      job.nb = (d1 - a1) - (d0 - a0);
+      if (pass + 1 == passes) {
+        job.L = sg.L;
+        job.stream = sg.stream_off + (uint32_t)out0 * sg.L;
+        job.word = sg.out_word + (uint32_t)out0;
+        job.rel = job.stream - sg.doc_stream0;
+      }
+    }
+    if (lane == 0) jobs[it] = job;
+  }
+}
+
+// The merge kernel: each CTA takes every gridDim.x-th tile.  Per tile: wait
+// for its slices (and the next tile's job), start the copies of the next
+// tile's slices into the other buffer and the job after it, then merge this
+// tile (merge path per thread in shared memory) and write it out.
+template <int W>
+__global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_piped(const TileJob* __restrict__ jobs,
+                                                                              uint32_t tiles,
+                                                                              const uint64_t* __restrict__ src,
+                                                                              uint64_t* __restrict__ dst, EmitOut eo) {
+  constexpr int KPT = W >= 8 ? 1 : 8 / W;
+  constexpr uint32_t TW = kM2Threads * KPT * W;
+  extern __shared__ __align__(128) uint64_t sm[];  // two tile buffers, padded layout
+  __shared__ __align__(16) TileJob s_job[3];
+  const uint32_t bw = padded_words(TW);
+  const int t = threadIdx.x;
+  const uint32_t G = gridDim.x;
+  auto fetch_job = [&](uint32_t k) {  // the CTA's k-th job into ring slot k % 3
+    const uint32_t it = blockIdx.x + k * G;
+    if (it < tiles && t < 3)
+      cp_async16(reinterpret_cast<uint4*>(&s_job[k % 3]) + t, reinterpret_cast<const uint4*>(jobs + it) + t);
+  };
+  auto fetch_data = [&](uint32_t k) {  // its slices into buffer k & 1: A's keys, then B's
+    if (blockIdx.x + k * G >= tiles) return;
+    const TileJob& j = s_job[k % 3];
+    const uint32_t wa = j.na * W, tot = (j.na + j.nb) * W;
+    uint64_t* buf = sm + (k & 1) * bw;
+    for (uint32_t e = t; e < tot; e += kM2Threads) cp_async8(buf + padw(e), src + (e < wa ? j.a_src + e : j.b_src + (e - wa)));
+  };
+  fetch_job(0);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  fetch_data(0);
+  fetch_job(1);
+  cp_async_commit();
+  for (uint32_t k = 0; blockIdx.x + k * G < tiles; ++k) {
+    cp_async_wait_all();
+    __syncthreads();  // tile k's slices and job k+1 are in; tile k-1 is out
+    fetch_data(k + 1);
+    fetch_job(k + 2);
+    cp_async_commit();
+    const TileJob& j = s_job[k % 3];
+    const uint32_t na = j.na, nb = j.nb, cnt = na + nb;
+    if (cnt == 0) continue;
+    uint64_t* buf = sm + (k & 1) * bw;
+    Key<W> kk[KPT];
+    const uint32_t pos = t * KPT;
+    if (pos < cnt) {
+      auto sA = [&](uint32_t i) { return kload<W>(pkey<W>(buf, i)); };
+      auto sB = [&](uint32_t i) { return kload<W>(pkey<W>(buf, na + i)); };
+      const uint32_t a = mp_split_f<W>(sA, na, sB, nb, pos);
+      merge_run_f<W, KPT>(sA, na, sB, nb, a, pos - a, kk);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < KPT; ++s)
+      if (pos + s < cnt) kstore<W>(pkey<W>(buf, pos + s), kk[s]);
+    __syncthreads();
+    const uint32_t L = j.L;
+    if (L) {
+      emit_run<kM2Threads>(L, eo.stream + j.stream, eo.want_offsets ? eo.offsets + j.word : nullptr, j.rel, cnt,
+                           [&](uint32_t q, uint32_t w) { return buf[padw(q * W + w)]; });
+    } else {
+      uint64_t* out = dst + j.dst;
+      for (uint32_t e = t; e < cnt * W; e += kM2Threads) out[e] = buf[padw(e)];
+    }
+  }
+  cp_async_wait_all();
+}
+
 template <int W>
 cudaError_t merge_pass2_w(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,
                           uint32_t pass, const uint64_t* src, uint64_t* dst, const EmitOut& eo, cudaStream_t st) {
@@ -542,6 +675,50 @@ cudaError_t launch_tile_sort2(int cluster, const Segment* segs, uint32_t sbeg, u
     case 2: return tile_sort2_cl<2>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
     case 4: return tile_sort2_cl<4>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
     case 8: return tile_sort2_cl<8>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int merge_piped_ctas_per_sm() { return BSORT_K5_MIN_CTAS; }
+
+cudaError_t launch_merge_cut(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t pass,
+                             const uint64_t* src, TileJob* jobs, cudaStream_t st) {
+  if (tiles == 0) return cudaSuccess;
+  const uint32_t grid = (tiles + 7) / 8;
+  switch (W) {
+    case 1: k_merge_cut<1><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, jobs); break;
+    case 2: k_merge_cut<2><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, jobs); break;
+    case 4: k_merge_cut<4><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, jobs); break;
+    case 8: k_merge_cut<8><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, jobs); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t merge_piped_w(const TileJob* jobs, uint32_t tiles, uint32_t grid, const uint64_t* src, uint64_t* dst,
+                          const EmitOut& eo, cudaStream_t st) {
+  constexpr uint32_t words = kM2Threads * (W >= 8 ? 1 : 8 / W) * W;
+  const size_t smem = 2 * (size_t)padded_words(words) * 8;
+  static int attr_done[64];
+  cudaError_t e = once_per_device(attr_done, [&] {
+    return smem > 48 * 1024
+               ? cudaFuncSetAttribute(k_merge_piped<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+               : cudaSuccess;
+  });
+  if (e != cudaSuccess) return e;
+  k_merge_piped<W><<<grid < tiles ? grid : tiles, kM2Threads, smem, st>>>(jobs, tiles, src, dst, eo);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_piped(int W, const TileJob* jobs, uint32_t tiles, uint32_t grid, const uint64_t* src,
+                               uint64_t* dst, EmitOut eo, cudaStream_t st) {
+  if (tiles == 0 || grid == 0) return cudaSuccess;
+  switch (W) {
+    case 1: return merge_piped_w<1>(jobs, tiles, grid, src, dst, eo, st);
+    case 2: return merge_piped_w<2>(jobs, tiles, grid, src, dst, eo, st);
+    case 4: return merge_piped_w<4>(jobs, tiles, grid, src, dst, eo, st);
+    case 8: return merge_piped_w<8>(jobs, tiles, grid, src, dst, eo, st);
     default: return cudaErrorInvalidValue;
   }
 }

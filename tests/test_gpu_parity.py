@@ -126,6 +126,21 @@ def test_giant_single_bucket(ctx, oracle_mod):
     assert_same(ctx.text(data), oracle_mod.stable(data, nthreads=8))
 
 
+def test_pipelined_merge_passes(ctx, oracle_mod):
+    """Enough one-word keys for the pipelined merge (cut kernel, then merge
+    kernel with two buffers): one bucket of 3M words (about 1,500 tiles), one
+    that finishes after two passes and sits idle in the later ones, and one of
+    an odd number of runs (a run carried through a pass alone)."""
+    rng = np.random.default_rng(9)
+    parts = []
+    for L, n in ((5, 3_000_000), (3, 40_000), (7, 17 * 2048 * 8 + 5)):
+        letters = rng.choice(np.frombuffer(b"abcdefgh", np.uint8), size=(n, L))
+        parts.append(np.concatenate([letters, np.full((n, 1), 32, np.uint8)], axis=1).reshape(-1))
+    cut = 6 * 1_000_000  # whole words of the first part
+    data = np.concatenate([parts[1], parts[0][:cut], parts[2], parts[0][cut:]])
+    assert_same(ctx.text(data), oracle_mod.stable(data, nthreads=8))
+
+
 def test_all_equal_keys_and_reverse_order(ctx, oracle_mod):
     data = b" ".join([b"same"] * 100_000 + [b"%04d" % 0 + b"z"] + [bytes([122 - i % 26]) * 3 for i in range(50_000)])
     assert_same(ctx.text(data), oracle_mod.stable(data))
