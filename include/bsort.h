@@ -169,6 +169,22 @@ typedef struct {
  * returns the number of families written (or -1 on error). */
 int bsort_profile_read(bsort_ctx* ctx, bsort_kernel_stat* out, int max);
 
+/* One traced launch (config.profile == 1): its family, when it ran and the
+ * algorithmic bytes it moved. */
+typedef struct {
+  const char* name;   /* kernel family, as in bsort_kernel_stat (static string) */
+  double start_ms;    /* start, in ms after the first traced launch since the last bsort_profile_read */
+  double end_ms;      /* end, on the same clock */
+  double bytes;       /* algorithmic bytes */
+  uint32_t stream;    /* 0: the call's stream; 1..4: the side streams K4 uses */
+  uint32_t pad;
+} bsort_trace_rec;
+
+/* Writes up to `max` traced launches, in launch order, into out[] (waiting for
+ * their events) and returns how many there are (may exceed max), or -1 on
+ * error.  Leaves them in place: bsort_profile_read clears them. */
+int bsort_trace_read(bsort_ctx* ctx, bsort_trace_rec* out, int max);
+
 /* Kernel launches made by this context since it was created. */
 uint64_t bsort_launch_count(const bsort_ctx* ctx);
 

@@ -43,6 +43,11 @@ class bsort_kernel_stat(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
+class bsort_trace_rec(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("stream", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
 class bsort_result(ctypes.Structure):
     _fields_ = [("max_len", ctypes.c_uint32), ("status", ctypes.c_uint32), ("n_words", ctypes.c_uint64),
                 ("stream_bytes", ctypes.c_uint64), ("counts", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
@@ -102,6 +107,8 @@ def load(path: str | None = None):
     lib.bsort_result_release.argtypes = [ctx_p, ctypes.POINTER(bsort_result)]
     lib.bsort_profile_read.restype = ctypes.c_int
     lib.bsort_profile_read.argtypes = [ctx_p, ctypes.POINTER(bsort_kernel_stat), ctypes.c_int]
+    lib.bsort_trace_read.restype = ctypes.c_int
+    lib.bsort_trace_read.argtypes = [ctx_p, ctypes.POINTER(bsort_trace_rec), ctypes.c_int]
     lib.bsort_launch_count.restype = ctypes.c_uint64
     lib.bsort_launch_count.argtypes = [ctx_p]
     lib.bsort_context_config.restype = ctypes.c_int
@@ -205,6 +212,20 @@ def bsort_profile_read(h) -> dict:
     if k < 0:
         raise BsortError(BSORT_E_CUDA, "bsort_profile_read failed")
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms), float(arr[i].bytes)) for i in range(k)}
+
+
+def bsort_trace_read(h) -> list[tuple[str, float, float, float, int]]:
+    """Traced launches since the last profile read, in launch order:
+    (family, start ms, end ms, algorithmic bytes, stream)."""
+    lib = load()
+    n = lib.bsort_trace_read(h, None, 0)
+    if n < 0:
+        raise BsortError(BSORT_E_CUDA, "bsort_trace_read failed")
+    arr = (bsort_trace_rec * max(n, 1))()
+    n = lib.bsort_trace_read(h, arr, n)
+    if n < 0:
+        raise BsortError(BSORT_E_CUDA, "bsort_trace_read failed")
+    return [(arr[i].name.decode(), arr[i].start_ms, arr[i].end_ms, arr[i].bytes, int(arr[i].stream)) for i in range(n)]
 
 
 def bsort_launch_count(h) -> int:
@@ -428,6 +449,9 @@ class Context:
 
     def profile_read(self) -> dict:
         return bsort_profile_read(self._h)
+
+    def trace_read(self) -> list:
+        return bsort_trace_read(self._h)
 
     def launch_count(self) -> int:
         return bsort_launch_count(self._h)

@@ -65,6 +65,7 @@ struct ProfRec {
   int kind;
   cudaEvent_t a, b;
   double bytes;
+  uint32_t stream;  // 0: the call's stream; 1.. the side streams
 };
 
 }  // namespace
@@ -215,7 +216,10 @@ struct Trace {
       cudaEvent_t b = next_event(c);
       if (b) {
         cudaEventRecord(b, st);
-        c->recs.push_back(ProfRec{kind, a, b, bytes});
+        uint32_t sx = 0;
+        for (int i = 0; i < bsort_ctx::kSide; ++i)
+          if (st == c->side[i]) sx = (uint32_t)i + 1;
+        c->recs.push_back(ProfRec{kind, a, b, bytes, sx});
       }
     }
     return e;
@@ -434,8 +438,6 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     }
     c->lookupv[(size_t)sg.doc * kHist + sg.L] = i;
   }
-  uint32_t passes2 = 0;
-  for (int g = 0; g < 4; ++g) passes2 = std::max(passes2, mpasses[g]);
 
   // ---- upload the layout, size the key and output buffers ----
   // segments, the (document, length) -> segment lookup and the zeroed slot
@@ -463,7 +465,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     cudaEvent_t gap_b = next_event(c);
     if (gap_b) {
       cudaEventRecord(gap_b, st);
-      c->recs.push_back(ProfRec{kHostGap, gap_a, gap_b, 0.0});
+      c->recs.push_back(ProfRec{kHostGap, gap_a, gap_b, 0.0, 0u});
       c->kind_launches[kHostGap] += 1;
     }
   }
@@ -530,19 +532,31 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   // K5: merge passes over the buckets that need them, one launch per pass and
   // width.  With at least two tiles per resident CTA the pass is pipelined: a
   // cut kernel lists every tile's slices first, so that the merge kernel can
-  // load one tile while it merges another.
+  // load one tile while it merges another.  The widths' chains of passes are
+  // independent: with more than one, each runs on a side stream of its own,
+  // so that one chain's latency-bound launches overlap another's merges.
   const uint32_t piped_grid = (uint32_t)(c->sm_count * merge_piped_ctas_per_sm());
   uint64_t job_at[4] = {}, jobs_total = 0;
-  for (int g = 0; g < 4; ++g)
+  int chains = 0;
+  for (int g = 0; g < 4; ++g) {
+    if (mpasses[g]) ++chains;
     if (mtiles[g] >= 2 * piped_grid) {
       job_at[g] = jobs_total;
       jobs_total += mtiles[g];
     }
+  }
   if (jobs_total) GROW(c->jobs, sizeof(TileJob) * jobs_total, "merge jobs");
-  for (uint32_t p = 0; p < passes2; ++p) {
-    for (int g = 0; g < 4; ++g) {
-      if (mpasses[g] <= p) continue;
-      const int W = width_of_class(g);
+  if (chains > 1) CK(cudaEventRecord(c->fork_ev, st), "fork");
+  int nj = 0;
+  for (int g = 0; g < 4; ++g) {
+    if (!mpasses[g]) continue;
+    const int W = width_of_class(g);
+    cudaStream_t sx = st;
+    if (chains > 1) {
+      sx = c->side[g];
+      CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
+    }
+    for (uint32_t p = 0; p < mpasses[g]; ++p) {
       double moved = 0;  // keys in, then keys out or, at a bucket's last pass, its words
       for (uint32_t i = gbeg[g]; i < gbeg[g + 1]; ++i)
         if (segs[i].passes > p)
@@ -551,15 +565,23 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       uint64_t* dst = (p & 1) ? kA : kB;
       if (mtiles[g] >= 2 * piped_grid) {
         TileJob* jobs = dptr<TileJob>(c->jobs) + job_at[g];
-        LAUNCH(kMergeCut, 0.0, launch_merge_cut(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g], p, src, jobs, st),
-               "K5 merge cut");
-        LAUNCH(kMerge, moved, launch_merge_piped(W, jobs, mtiles[g], piped_grid, src, dst, eo, st), "K5 merge_pass");
+        {
+          Trace tr_(c, sx, kMergeCut, 0.0);
+          CK(tr_.done(launch_merge_cut(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g], p, src, jobs, sx)), "K5 merge cut");
+        }
+        Trace tr_(c, sx, kMerge, moved);
+        CK(tr_.done(launch_merge_piped(W, jobs, mtiles[g], piped_grid, src, dst, eo, sx)), "K5 merge_pass");
       } else {
-        LAUNCH(kMerge, moved,
-               launch_merge_pass2(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g],
-                                  std::min<uint32_t>(mtiles[g], (uint32_t)c->sm_count * 8), p, src, dst, eo, st),
-               "K5 merge_pass");
+        Trace tr_(c, sx, kMerge, moved);
+        CK(tr_.done(launch_merge_pass2(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g],
+                                       std::min<uint32_t>(mtiles[g], (uint32_t)c->sm_count * 8), p, src, dst, eo,
+                                       sx)),
+           "K5 merge_pass");
       }
+    }
+    if (chains > 1) {
+      CK(cudaEventRecord(c->join_ev[nj], sx), "join");
+      ++nj;
     }
   }
   for (int g = 10; g < 12; ++g) {
@@ -575,6 +597,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
              "K5 merge_pass (wide keys)");
     }
   }
+  for (int i = 0; i < nj; ++i) CK(cudaStreamWaitEvent(st, c->join_ev[i], 0), "join");
   // K6: the words of the wide keys (every other bucket was emitted by its sort)
   if (etile) {
     LAUNCH(kEmit, (double)kb[10] + kb[11] + ob[10] + ob[11],
@@ -886,6 +909,30 @@ int bsort_profile_read(bsort_ctx* c, bsort_kernel_stat* out, int max) {
   }
   c->recs.clear();
   c->ev_used = 0;
+  return k;
+}
+
+int bsort_trace_read(bsort_ctx* c, bsort_trace_rec* out, int max) {
+  if (!c || (!out && max > 0) || max < 0) return -1;
+  if (c->recs.empty()) return 0;
+  if (cudaSetDevice(c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  const cudaEvent_t t0 = c->recs.front().a;
+  int k = 0;
+  for (const ProfRec& r : c->recs) {
+    if (k < max) {
+      float s = 0.f, e = 0.f;
+      if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&s, t0, r.a) != cudaSuccess ||
+          cudaEventElapsedTime(&e, t0, r.b) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+      }
+      out[k] = bsort_trace_rec{kKindName[r.kind], s, e, r.bytes, r.stream, 0u};
+    }
+    ++k;
+  }
   return k;
 }
 

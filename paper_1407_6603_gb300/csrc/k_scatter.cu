@@ -15,6 +15,7 @@
 // document's closing offset, and K6 only emits the buckets of words of 65 or
 // more letters, which the narrow-tile kernels sort.
 #include "bsort_dev.cuh"
+#include "sort_common.cuh"
 
 namespace bsort {
 namespace {
@@ -32,6 +33,9 @@ __device__ __forceinline__ uint32_t doc_of_item(const uint32_t* doc_item0, uint3
 }
 
 constexpr int kWordsPerThread = kWordBlock / kWordThreads;
+// Bytes of letters a CTA stages in shared memory (1024 words of up to 15
+// letters on average); longer ranges are read from global memory.
+constexpr uint32_t kLetterStage = 16384;
 
 __global__ void __launch_bounds__(kWordThreads) k_scatter(
     const uint32_t* __restrict__ starts, const uint8_t* __restrict__ letters, const uint32_t* __restrict__ doc_wbase,
@@ -47,7 +51,10 @@ __global__ void __launch_bounds__(kWordThreads) k_scatter(
     if (L == 0 && eo.want_offsets) eo.offsets[doc_wbase[d + 1] + d] = doc_lbase[d + 1] - doc_lbase[d];
   }
   __shared__ uint32_t cnt[kHist];
-  __shared__ uint32_t base[kHist];
+  __shared__ uint64_t s_out[kHist];  // word offset in `keys` of the CTA's first slot of each length
+  __shared__ uint32_t s_lookup[kHist];
+  __shared__ uint32_t s_st[kWordBlock + 1];
+  __shared__ __align__(16) uint64_t s_let[kLetterStage / 8 + 2];
   __shared__ uint32_t s_doc;
   const int t = threadIdx.x;
   for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
@@ -55,43 +62,65 @@ __global__ void __launch_bounds__(kWordThreads) k_scatter(
     if (t == 0) s_doc = doc_of_item(doc_item0, ndocs, it);
     __syncthreads();
     const uint32_t d = s_doc;
-    const uint32_t* lookup = seg_lookup + (size_t)d * kHist;
     const uint32_t w0 = doc_wbase[d] + (it - doc_item0[d]) * kWordBlock;
-    const uint32_t w1 = min(w0 + kWordBlock, doc_wbase[d + 1]);
-    uint32_t s0[kWordsPerThread], len[kWordsPerThread], rank[kWordsPerThread];
+    const uint32_t nw = min(w0 + kWordBlock, doc_wbase[d + 1]) - w0;
+    // the block's word starts and the document's length -> bucket row
+    for (uint32_t i = t; i <= nw; i += kWordThreads) s_st[i] = starts[w0 + i];
+    for (int i = t; i < kHist; i += kWordThreads) s_lookup[i] = seg_lookup[(size_t)d * kHist + i];
+    __syncthreads();
+    // the block's letters, one contiguous range of S, copied in the
+    // background (S has 16 bytes of slack past its end) while the words are
+    // ranked; a range too long for the stage is read from S directly
+    const uint32_t l0 = s_st[0] & ~15u, l1 = (s_st[nw] + 15u) & ~15u;
+    const bool staged = l1 - l0 <= kLetterStage;
+    if (staged) {
+      for (uint32_t i = t; i < (l1 - l0) / 16; i += kWordThreads) cp_async16(s_let + 2 * i, letters + l0 + 16 * i);
+      cp_async_commit();
+    }
+    uint32_t len[kWordsPerThread], rank[kWordsPerThread];
 #pragma unroll
     for (int k = 0; k < kWordsPerThread; ++k) {
-      const uint32_t wi = w0 + t + k * kWordThreads;
-      len[k] = 0;
-      if (wi < w1) {
-        s0[k] = starts[wi];
-        const uint32_t L = starts[wi + 1] - s0[k];
-        if (L <= (uint32_t)kMaxLen && lookup[L] != kNoSegment) {
-          len[k] = L;
-          rank[k] = atomicAdd(&cnt[L], 1u);
-        }
+      const uint32_t i = t + k * kWordThreads;
+      uint32_t L = 0;
+      if (i < nw) {
+        L = s_st[i + 1] - s_st[i];
+        if (L > (uint32_t)kMaxLen || s_lookup[L] == kNoSegment) L = 0;
       }
+      len[k] = L;
+      if (L) rank[k] = atomicAdd(&cnt[L], 1u);
     }
     __syncthreads();
+    // one thread per length reserves the CTA's slots in the bucket
     for (int L = t; L < kHist; L += kWordThreads)
-      if (cnt[L]) base[L] = atomicAdd(&cursor[lookup[L]], cnt[L]);
+      if (cnt[L]) {
+        const uint32_t si = s_lookup[L];
+        s_out[L] = segs[si].key_off + (uint64_t)atomicAdd(&cursor[si], cnt[L]) * width_of_len(L);
+      }
+    if (staged) cp_async_wait_all();
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < kWordsPerThread; ++k) {
       const uint32_t L = len[k];
       if (L == 0) continue;
-      const Segment& sg = segs[lookup[L]];
+      const uint32_t s0 = s_st[t + k * kWordThreads];
       const int W = width_of_len(L);
-      uint64_t* out = keys + sg.key_off + (size_t)(base[L] + rank[k]) * W;
-      const uint8_t* src = letters + s0[k];
+      uint64_t* out = keys + s_out[L] + (size_t)rank[k] * W;
+      // the letters as aligned 8-byte loads, shifted into place, byte-swapped
+      // to big-endian and cut at L
+      const uint32_t sh = s0 & 7u;
+      const uint64_t* src =
+          staged ? s_let + ((s0 - l0) >> 3) : reinterpret_cast<const uint64_t*>(letters + (s0 & ~7u));
+      uint64_t x0 = src[0];
       for (int q = 0; q < W; ++q) {
         uint64_t v = 0;
         const uint32_t b0 = (uint32_t)q * 8;
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-          const uint32_t i = b0 + b;
-          const uint64_t byte = i < L ? (uint64_t)src[i] : 0ull;
-          v |= byte << (56 - 8 * b);
+        if (b0 < L) {
+          const uint64_t x1 = src[q + 1];
+          const uint64_t le = sh ? (x0 >> (8 * sh)) | (x1 << (64 - 8 * sh)) : x0;
+          x0 = x1;
+          v = ((uint64_t)__byte_perm((uint32_t)le, 0, 0x0123) << 32) | __byte_perm((uint32_t)(le >> 32), 0, 0x0123);
+          const uint32_t valid = L - b0;
+          if (valid < 8) v &= ~0ull << (8 * (8 - valid));
         }
         out[q] = v;
       }
