@@ -65,66 +65,7 @@ __device__ __forceinline__ TokAcc acc_combine(const TokAcc& a, const TokAcc& b) 
   return r;
 }
 
-__device__ __forceinline__ TokAcc acc_leaf(uint64_t letters, uint64_t spaces, bool doc_start, uint32_t doc) {
-  const TokSum s = seg_summary(letters, spaces, doc_start);
-  TokAcc r;
-  r.letters = s.letters;
-  r.words = s.words;
-  r.last = 0;
-  r.ldoc = doc;
-  uint32_t fl = s.flags | (doc << 4);
-  const uint64_t st = start_mask(letters, spaces, doc_start);
-  if (st) {
-    fl |= kHas;
-    const int hb = 63 - __clzll(st);
-    r.last = hb ? __popcll(letters & (~0ull >> (64 - hb))) : 0u;
-  }
-  r.fl = fl;
-  return r;
-}
-
 constexpr TokAcc kAccZero = {0, 0, 0, 0, 0};
-
-__device__ __forceinline__ TokAcc shfl_up_acc(const TokAcc& v, int off) {
-  TokAcc r;
-  r.letters = __shfl_up_sync(kFull, v.letters, off);
-  r.words = __shfl_up_sync(kFull, v.words, off);
-  r.fl = __shfl_up_sync(kFull, v.fl, off);
-  r.last = __shfl_up_sync(kFull, v.last, off);
-  r.ldoc = __shfl_up_sync(kFull, v.ldoc, off);
-  return r;
-}
-
-__device__ __forceinline__ TokAcc warp_inclusive_acc(TokAcc v) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    const TokAcc u = shfl_up_acc(v, off);
-    if (lane >= off) v = acc_combine(u, v);
-  }
-  return v;
-}
-
-__device__ TokAcc block_exclusive_acc(const TokAcc v, TokAcc* total) {
-  __shared__ TokAcc warp_tot[kTokThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const TokAcc inc = warp_inclusive_acc(v);
-  if (lane == 31) warp_tot[warp] = inc;
-  __syncthreads();
-  if (warp == 0) {
-    TokAcc w = kAccZero;
-    if (lane < kTokThreads / 32) w = warp_tot[lane];
-    w = warp_inclusive_acc(w);
-    if (lane < kTokThreads / 32) warp_tot[lane] = w;
-  }
-  __syncthreads();
-  TokAcc ex = shfl_up_acc(inc, 1);
-  if (lane == 0) ex = kAccZero;
-  if (warp > 0) ex = acc_combine(warp_tot[warp - 1], ex);
-  *total = warp_tot[kTokThreads / 32 - 1];
-  __syncthreads();
-  return ex;
-}
 
 struct LookRec {
   uint32_t status;  // 0: not yet, 1: agg published, 2: inc published
@@ -201,6 +142,7 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
   __shared__ uint32_t h_local[kHist];
   __shared__ uint32_t s_c, s_doc, s_last;
   __shared__ TokAcc s_prefix;
+  __shared__ uint32_t s_wlast[kTokThreads / 32];
   const int t = threadIdx.x;
   for (int i = t; i < kHist; i += kTokThreads) h_local[i] = 0;
   if (t == 0) {
@@ -240,9 +182,35 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
     uint64_t lm, sm;
     classify64(w, lm, sm);
     const bool doc_start = (c == dd.chunk0) && t == 0;
-    const TokAcc mine = acc_leaf(lm, sm, doc_start, d);
+    const TokSum leaf = seg_summary(lm, sm, doc_start);
+    uint32_t total_pk;
+    const uint32_t ex = block_exclusive_pk(pk_make(leaf.letters, leaf.words, leaf.flags), &total_pk);
+    // The chunk's last word start that its own bytes decide (its first
+    // letter, when no whitespace precedes it in the chunk, waits for the
+    // chunk's predecessors): one more than its letter offset, 0 for none.
+    {
+      const uint32_t fe = pk_flags(ex);
+      const uint64_t st_loc = start_mask(lm, sm, doc_start || ((fe & kEv) && (fe & kWs)));
+      uint32_t my_last = 0;
+      if (st_loc) {
+        const int hb = 63 - __clzll(st_loc);
+        my_last = pk_letters(ex) + (hb ? __popcll(lm & (~0ull >> (64 - hb))) : 0u) + 1u;
+      }
+      const uint32_t m = __reduce_max_sync(kFull, my_last);
+      if ((t & 31) == 0) s_wlast[t >> 5] = m;
+    }
+    __syncthreads();
     TokAcc total;
-    const TokAcc ex = block_exclusive_acc(mine, &total);  // ends with __syncthreads: buf is free
+    {
+      uint32_t last1 = 0;
+#pragma unroll
+      for (int i = 0; i < kTokThreads / 32; ++i) last1 = max(last1, s_wlast[i]);
+      total.letters = pk_letters(total_pk);
+      total.words = pk_words(total_pk);
+      total.fl = pk_flags(total_pk) | (last1 ? kHas : 0u) | (d << 4);
+      total.last = last1 ? last1 - 1u : 0u;
+      total.ldoc = d;
+    }
 
     if (t < 32) {
       // warp 0 publishes this chunk's summary, then looks back over 32
@@ -306,27 +274,25 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
     }
     __syncthreads();
     const TokAcc cin = s_prefix;
-    const TokAcc pre = acc_combine(cin, ex);
-    const bool ws_before = doc_start || ((pre.fl & kEv) && (pre.fl & kWs));
-    // word starts of this chunk, staged in order (they are contiguous in `starts`)
+    const uint32_t fe = pk_flags(ex);
+    const bool cin_ws = (cin.fl & kEv) && (cin.fl & kWs);
+    const bool ws_before = doc_start || ((fe & kEv) ? (fe & kWs) != 0 : cin_ws);
+    const uint32_t pre_letters = cin.letters + pk_letters(ex);
+    // word starts of this chunk, staged in order (they are contiguous in
+    // `starts`); the chunk's first letter counts before this thread when the
+    // predecessors end in whitespace
     uint64_t starts_m = start_mask(lm, sm, ws_before);
-    uint32_t wpos = pre.words - cin.words;
+    uint32_t wpos = pk_words(ex) + (((fe & kU) && cin_ws) ? 1u : 0u);
     while (starts_m) {
       const int b = __ffsll(starts_m) - 1;
       starts_m &= starts_m - 1;
       const uint64_t below = b ? (lm & (~0ull >> (64 - b))) : 0ull;
-      s_starts[wpos++] = pre.letters + __popcll(below);
+      s_starts[wpos++] = pre_letters + __popcll(below);
     }
     // letters, staged so that stage[k] lands at global byte (cin.letters & ~15) + k
     const uint32_t lead = cin.letters & 15u;
-    uint8_t* stage = reinterpret_cast<uint8_t*>(buf);
-    uint32_t lpos = lead + ex.letters;
-    uint64_t m = lm;
-    while (m) {
-      const int b = __ffsll(m) - 1;
-      m &= m - 1;
-      stage[lpos++] = (uint8_t)(w[b >> 2] >> (8 * (b & 3)));
-    }
+    uint8_t* const stage = reinterpret_cast<uint8_t*>(buf);
+    stage_letters(w, lm, stage, lead + pk_letters(ex));
     __syncthreads();
     // letters out: bytes up to the first 16-byte boundary, 16-byte stores, bytes after the last
     {
@@ -348,25 +314,19 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
     const uint32_t nw = acc_combine(cin, total).words - cin.words;
     for (uint32_t i = t; i < nw; i += kTokThreads) starts[cin.words + i] = s_starts[i];
     const bool carry_word = (cin.fl & kHas) != 0;
-    for (uint32_t base = 0; base < nw; base += kTokThreads) {  // same trip count for every thread
-      const uint32_t i = base + t;
-      uint32_t key = 0xFFFFFFFFu;  // no word
-      if (i < nw && (i > 0 || carry_word)) {
-        const uint32_t L = s_starts[i] - (i > 0 ? s_starts[i - 1] : cin.last);
-        const uint32_t pdoc = i > 0 ? d : cin.ldoc;
-        uint32_t bin = L;
-        if (L > l_cap || L > (uint32_t)kMaxLen) {
-          bin = 0;
-          atomicAdd(&meta->err_long, 1u);
-        }
-        if (pdoc != d)
-          atomicAdd(&hist[(size_t)pdoc * kHist + bin], 1u);  // a word of an earlier document
-        else
-          key = bin;
+    for (uint32_t i = t; i < nw; i += kTokThreads) {
+      if (i == 0 && !carry_word) continue;
+      const uint32_t L = s_starts[i] - (i > 0 ? s_starts[i - 1] : cin.last);
+      const uint32_t pdoc = i > 0 ? d : cin.ldoc;
+      uint32_t bin = L;
+      if (L > l_cap || L > (uint32_t)kMaxLen) {
+        bin = 0;
+        atomicAdd(&meta->err_long, 1u);
       }
-      const uint32_t peers = __match_any_sync(kFull, key);
-      if (key != 0xFFFFFFFFu && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
-        atomicAdd(&h_local[key], (uint32_t)__popc(peers));
+      if (pdoc != d)
+        atomicAdd(&hist[(size_t)pdoc * kHist + bin], 1u);  // a word of an earlier document
+      else
+        atomicAdd(&h_local[bin], 1u);
     }
     __syncthreads();
     for (int i = t; i < kHist; i += kTokThreads)

@@ -107,6 +107,102 @@ __device__ TokSum block_exclusive(const TokSum v, TokSum* total) {
   return ex;
 }
 
+// Packed scan element of a span inside one chunk (one document): letters in
+// bits 0..14, words in bits 15..28, the flags EV / WS / U in bits 29..31.  A
+// chunk holds at most 16384 letters and 8192 word starts, so no field
+// overflows into the next and one 32-bit shuffle carries all three.
+constexpr uint32_t kPkWords = 15, kPkFlags = 29, kPkCounts = (1u << kPkFlags) - 1u;
+__device__ __forceinline__ uint32_t pk_make(uint32_t letters, uint32_t words, uint32_t flags) {
+  return letters | (words << kPkWords) | (flags << kPkFlags);
+}
+__device__ __forceinline__ uint32_t pk_letters(uint32_t v) { return v & ((1u << kPkWords) - 1u); }
+__device__ __forceinline__ uint32_t pk_words(uint32_t v) { return (v & kPkCounts) >> kPkWords; }
+__device__ __forceinline__ uint32_t pk_flags(uint32_t v) { return v >> kPkFlags; }
+// tok_combine on packed elements (0 is the identity)
+__device__ __forceinline__ uint32_t pk_combine(uint32_t a, uint32_t b) {
+  const uint32_t fa = a >> kPkFlags, fb = b >> kPkFlags;
+  const bool resolve = (fb & kU) && (fa & kEv) && (fa & kWs);
+  const uint32_t counts = (a & kPkCounts) + (b & kPkCounts) + (resolve ? (1u << kPkWords) : 0u);
+  const uint32_t ev = (fa | fb) & kEv;
+  const uint32_t ws = (fb & kEv) ? (fb & kWs) : (fa & kWs);
+  const uint32_t u = (fa & kEv) ? (fa & kU) : (fb & kU);
+  return counts | ((ev | ws | u) << kPkFlags);
+}
+
+// Exclusive scan of packed elements over the CTA; returns this thread's
+// prefix and the CTA total.  Ends with a barrier.
+__device__ uint32_t block_exclusive_pk(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_tot[kTokThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t u = __shfl_up_sync(kFull, inc, off);
+    if (lane >= off) inc = pk_combine(u, inc);
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kTokThreads / 32 ? warp_tot[lane] : 0u;
+#pragma unroll
+    for (int off = 1; off < kTokThreads / 32; off <<= 1) {
+      const uint32_t u = __shfl_up_sync(kFull, w, off);
+      if (lane >= off) w = pk_combine(u, w);
+    }
+    if (lane < kTokThreads / 32) warp_tot[lane] = w;
+  }
+  __syncthreads();
+  uint32_t ex = __shfl_up_sync(kFull, inc, 1);
+  if (lane == 0) ex = 0u;
+  if (warp > 0) ex = pk_combine(warp_tot[warp - 1], ex);
+  *total = warp_tot[kTokThreads / 32 - 1];
+  __syncthreads();
+  return ex;
+}
+
+// byte_perm selector that moves the bytes of a 4-bit mask, in order, to the
+// low end of a word and fills the rest with zero bytes: nibble k of entry m
+// is the position of the k-th set bit of m (4 = a zero byte).  Sixteen
+// 16-bit entries, four to a 64-bit constant.
+__device__ __forceinline__ uint32_t compact_sel(uint32_t m4) {
+  const uint64_t t01 = (m4 & 4u) ? 0x4210442144204442ull : 0x4410444144404444ull;
+  const uint64_t t23 = (m4 & 4u) ? 0x3210432143204432ull : 0x4310443144304443ull;
+  const uint64_t t = (m4 & 8u) ? t23 : t01;
+  return (uint32_t)(t >> (16 * (m4 & 3u))) & 0xFFFFu;
+}
+
+// Writes the letters of the thread's 64 bytes (w, letter mask lm), in order,
+// to stage[pos...]: whole aligned 32-bit words where all four bytes are the
+// thread's, single bytes at the two ends (which neighbours share).
+__device__ __forceinline__ void stage_letters(const uint32_t (&w)[16], uint64_t lm, uint8_t* stage, uint32_t pos) {
+  uint32_t* stage32 = reinterpret_cast<uint32_t*>(stage);
+  const uint32_t skew = pos & 3u;
+  uint64_t acc = 0;      // pending bytes, the first at byte 0 (skew junk bytes first)
+  uint32_t na = skew;    // pending byte count
+  uint32_t wi = pos >> 2;
+  bool first = true;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const uint32_t m4 = (uint32_t)(lm >> (4 * j)) & 0xFu;
+    const uint32_t c = __byte_perm(w[j], 0u, compact_sel(m4));
+    acc |= (uint64_t)c << (8 * na);
+    na += __popc(m4);
+    if (na >= 4) {
+      const uint32_t word = (uint32_t)acc;
+      if (first && skew) {
+        for (uint32_t b = skew; b < 4; ++b) stage[4 * wi + b] = (uint8_t)(word >> (8 * b));
+      } else {
+        stage32[wi] = word;
+      }
+      first = false;
+      ++wi;
+      acc >>= 32;
+      na -= 4;
+    }
+  }
+  for (uint32_t b = first ? skew : 0u; b < na; ++b) stage[4 * wi + b] = (uint8_t)(acc >> (8 * b));
+}
+
 __device__ __forceinline__ void thread_words(const uint4* buf, uint32_t (&w)[16]) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
