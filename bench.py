@@ -38,6 +38,11 @@ if ROOT not in sys.path:
 
 METRIC = "input MB/s and words/s sorted on 1 GB300 (% HBM roofline); batched vs plain; p99"
 L2_FLUSH_BYTES = 256 << 20  # larger than the 129 MB L2
+# Integer issue rate behind the tile sort's roofline: 4 x 32 integer lanes per
+# SM per clock, and 4 integer operations per key-level of one-word keys (a
+# 64-bit compare is 2, a 64-bit select 2).
+ALU_LANES_PER_SM = 128
+ALU_OPS_PER_KEY_LEVEL = 4
 FALLBACK_HBM_GBS = 6800.0
 
 # Kernel families and the source file that holds each (for the traffic record).
@@ -443,13 +448,41 @@ def measure(args, quiet: bool = False):
     fams = {k: v for k, v in prof.items() if v[0] > 0}
     # host_gap (the call's one host round trip) is reported but is no kernel
     dom = max((k for k in fams if k != "host_gap"), key=lambda k: fams[k][1])
-    launches_d, ms_d, bytes_d = fams[dom]
     peak, peak_src = measured_peaks()
-    achieved = bytes_d / (ms_d / 1e3) / 1e9 if ms_d > 0 else 0.0
-    traffic = recorded_traffic(dom, args.workload)
+
+    def hbm_roofline(fam):
+        n_l, ms_f, bytes_f, _ = fams[fam]
+        ach = bytes_f / (ms_f / 1e3) / 1e9 if ms_f > 0 else 0.0
+        return {"bound": "hbm", "kernel": fam, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak if peak else None, "peak_source": peak_src,
+                "traffic": recorded_traffic(fam, args.workload), "launches_per_step": n_l / args.steps,
+                "algorithmic_bytes_per_launch": bytes_f / n_l if n_l else None}
+
+    def alu_roofline(fam):
+        # the tile sort is bound by integer compares, not by HBM: key-levels
+        # per second against the integer issue rate of the SMs
+        n_l, ms_f, bytes_f, levels_f = fams[fam]
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        alu_peak = sms * ALU_LANES_PER_SM * mhz * 1e6 / ALU_OPS_PER_KEY_LEVEL / 1e9
+        ach = levels_f / (ms_f / 1e3) / 1e9 if ms_f > 0 else 0.0
+        return {"bound": "alu", "kernel": fam, "achieved": ach, "peak": alu_peak, "unit": "G key-levels/s",
+                "frac": ach / alu_peak, "peak_source": (f"derived: {sms} SMs x {ALU_LANES_PER_SM} integer lanes x "
+                                                        f"{mhz:.0f} MHz / {ALU_OPS_PER_KEY_LEVEL} integer ops per "
+                                                        "key-level (one-word keys)"),
+                "traffic": recorded_traffic(fam, args.workload), "launches_per_step": n_l / args.steps,
+                "key_levels_per_launch": levels_f / n_l if n_l else None,
+                "algorithmic_bytes_per_launch": bytes_f / n_l if n_l else None}
+
+    roofline = alu_roofline(dom) if fams[dom][3] > 0 else hbm_roofline(dom)
+    hbm_fams = [k for k in fams if k != "host_gap" and fams[k][3] == 0 and fams[k][2] > 0]
+    roofline_hbm = hbm_roofline(max(hbm_fams, key=lambda k: fams[k][1])) if hbm_fams else None
     kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps,
                    "algorithmic_bytes_per_step": v[2] / args.steps,
-                   "achieved_gbs": (v[2] / (v[1] / 1e3) / 1e9) if v[1] > 0 else None}
+                   "achieved_gbs": (v[2] / (v[1] / 1e3) / 1e9) if v[1] > 0 else None,
+                   **({"key_levels_per_step": v[3] / args.steps,
+                       "achieved_g_key_levels_s": v[3] / (v[1] / 1e3) / 1e9 if v[1] > 0 else None}
+                      if v[3] > 0 else {})}
                for k, v in fams.items()}
     # the oracle baseline runs on rank 0 at N=1 only
     cpu = None
@@ -475,10 +508,8 @@ def measure(args, quiet: bool = False):
         "words_per_s": agg["words_per_s"],
         "p50_ms": step_sorted[len(step_sorted) // 2],
         "p99_ms": step_sorted[min(len(step_sorted) - 1, int(round(0.99 * (len(step_sorted) - 1))))],
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if peak else None, "peak_source": peak_src,
-                     "traffic": traffic, "launches_per_step": launches_d / args.steps,
-                     "algorithmic_bytes_per_launch": bytes_d / launches_d if launches_d else None},
+        "roofline": roofline,
+        "roofline_hbm": roofline_hbm,
         "kernels": kernels,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_agg["mb_per_s"], "unit": "MB/s", "h2d_bytes_per_step": nbytes,

@@ -162,6 +162,8 @@ typedef struct {
   uint64_t launches;  /* launches since the last read */
   double ms;          /* summed device time of those launches (0 when profiling is off) */
   double bytes;       /* summed algorithmic bytes of those launches */
+  double key_levels;  /* sort kernels: summed key-levels, each key counted once per doubling of the
+                         sorted run it ends in (n * ceil(log2 run) per bucket); 0 for the others */
 } bsort_kernel_stat;
 
 /* Writes up to `max` per-family statistics accumulated since the last read

@@ -40,7 +40,7 @@ class bsort_config(ctypes.Structure):
 
 class bsort_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64), ("ms", ctypes.c_double),
-                ("bytes", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("key_levels", ctypes.c_double)]
 
 
 class bsort_trace_rec(ctypes.Structure):
@@ -206,12 +206,13 @@ def bsort_result_release(h, res: bsort_result) -> None:
 
 
 def bsort_profile_read(h) -> dict:
-    """Per kernel family: {name: (launches, ms, algorithmic bytes)} since the last read."""
+    """Per kernel family: {name: (launches, ms, algorithmic bytes, key-levels)} since the last read."""
     arr = (bsort_kernel_stat * 16)()
     k = load().bsort_profile_read(h, arr, 16)
     if k < 0:
         raise BsortError(BSORT_E_CUDA, "bsort_profile_read failed")
-    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms), float(arr[i].bytes)) for i in range(k)}
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms), float(arr[i].bytes),
+                                   float(arr[i].key_levels)) for i in range(k)}
 
 
 def bsort_trace_read(h) -> list[tuple[str, float, float, float, int]]:

@@ -12,6 +12,7 @@
 // The only host/device synchronisation inside a call is the read of the
 // length counts; everything after it is enqueued without waiting.
 #include <algorithm>
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -34,6 +35,9 @@ struct HostBuf {
   size_t cap = 0;
 };
 
+// ceil(log2(n)) for n >= 1 (0 for n <= 1)
+double ceil_log2(uint64_t n) { return n <= 1 ? 0.0 : (double)(64 - __builtin_clzll(n - 1)); }
+
 uint32_t merge_passes(uint64_t n, uint64_t tile) {
   uint32_t p = 0;
   while ((tile << p) < n) ++p;
@@ -43,15 +47,19 @@ uint32_t merge_passes(uint64_t n, uint64_t tile) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Layout of the device "meta" region, read back in one copy after K2.
+// The meta region: what K1 leaves for the host (read back in one copy of
+// `total` bytes), then K1's look-back scratch; one memset clears both.
 struct MetaLayout {
-  size_t meta = 0, wbase = 0, lbase = 0, item0 = 0, hist = 0, total = 0;
-  void set(uint32_t ndocs) {
+  size_t meta = 0, wbase = 0, lbase = 0, item0 = 0, hist = 0, total = 0, scratch = 0, cleared = 0;
+  void set(uint32_t ndocs, uint32_t chunks) {
     meta = 0;
     wbase = meta + align_up(sizeof(Meta), 128);
     lbase = wbase + align_up((ndocs + 1) * 4ull, 128);
     item0 = lbase + align_up((ndocs + 1) * 4ull, 128);
     hist = item0 + align_up((ndocs + 1) * 4ull, 128);
     total = hist + (size_t)ndocs * kHist * 4;
+    scratch = align_up(total, 256);
+    cleared = scratch + tokenize1p_scratch_bytes(chunks);
   }
 };
 
@@ -78,12 +86,12 @@ struct bsort_ctx {
   static constexpr int kSide = 4;
   cudaStream_t side[kSide] = {};              // the smaller K4 launches run here, beside the clusters of 8
   cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
+  cudaEvent_t counts_ev = nullptr;  // the counts of K1 reached the host
   std::string err;
   bool busy = false;
 
   DevBuf sticky;  // a Meta kept across calls: err_timeout of bounded device waits
   HostBuf h_sticky;
-  DevBuf k1scratch;
   DevBuf in, docs, meta, starts, letters, plan, keysA, keysB, counts, offsets, stream, jobs;
   HostBuf h_in, h_docs, h_meta, h_plan, h_counts, h_offsets, h_stream;
 
@@ -99,6 +107,7 @@ struct bsort_ctx {
   uint64_t launches = 0;
   uint64_t kind_launches[kKinds] = {};
   double kind_bytes[kKinds] = {};
+  double kind_levels[kKinds] = {};  // key-levels of the sort kernels
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<ProfRec> recs;
@@ -200,8 +209,10 @@ struct Trace {
   cudaStream_t st;
   int kind;
   double bytes;
+  double levels;
   cudaEvent_t a = nullptr;
-  Trace(bsort_ctx* c_, cudaStream_t st_, int kind_, double bytes_) : c(c_), st(st_), kind(kind_), bytes(bytes_) {
+  Trace(bsort_ctx* c_, cudaStream_t st_, int kind_, double bytes_, double levels_ = 0.0)
+      : c(c_), st(st_), kind(kind_), bytes(bytes_), levels(levels_) {
     if (c->cfg.profile) {
       a = next_event(c);
       if (a) cudaEventRecord(a, st);
@@ -212,6 +223,7 @@ struct Trace {
     c->launches += 1;
     c->kind_launches[kind] += 1;
     c->kind_bytes[kind] += bytes;
+    c->kind_levels[kind] += levels;
     if (a) {
       cudaEvent_t b = next_event(c);
       if (b) {
@@ -231,6 +243,17 @@ struct Trace {
     Trace tr_(c, st, (kind), (double)(bytes));          \
     CK(tr_.done(call), what);                           \
   } while (0)
+
+// Waits for an event by polling it (the call's one mid-path wait is short,
+// and a poll answers sooner than a blocking wait); after 200 us it blocks.
+cudaError_t spin_wait(cudaEvent_t ev) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(ev);
+    if (e != cudaErrorNotReady) return e;
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(200)) return cudaEventSynchronize(ev);
+  }
+}
 
 // Runs the whole path over `ndocs` documents that sit at d_in + offs[i]
 // (lens[i] bytes each) in device memory.  Leaves the outputs in c->counts,
@@ -256,10 +279,10 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   }
   if (total_len >= (1ull << 32))
     return fail(c, BSORT_E_TOO_LARGE, "2^32 bytes or more in one pass (positions are 32-bit)");
-  c->ml.set(ndocs);
+  c->ml.set(ndocs, (uint32_t)chunks);
   const MetaLayout& ml = c->ml;
   GROW(c->docs, sizeof(DocDesc) * ndocs, "document table");
-  GROW(c->meta, ml.total, "meta");
+  GROW(c->meta, ml.cleared, "meta");
   GROW(c->starts, 4 * (words_bound + 1), "word starts");
   GROW(c->letters, total_len + 16, "stripped letters");
   GROW_HOST(c->h_meta, ml.total, "meta");
@@ -271,28 +294,27 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   uint32_t* d_hist = dptr<uint32_t>(c->meta, ml.hist);
 
   CK(cudaMemcpyAsync(c->docs.p, hd, sizeof(DocDesc) * ndocs, cudaMemcpyHostToDevice, st), "copy document table");
-  CK(cudaMemsetAsync(c->meta.p, 0, ml.total, st), "clear meta");
+  CK(cudaMemsetAsync(c->meta.p, 0, ml.cleared, st), "clear meta");
   const DocDesc* d_docs = dptr<DocDesc>(c->docs);
   // K1: strip, tokenize and count lengths in one pass.  Its algorithmic bytes
   // (input read, letters and word starts written) are known only after the
   // counts come back; they are added to its tag below.
-  GROW(c->k1scratch, tokenize1p_scratch_bytes((uint32_t)chunks), "tokenizer scratch");
   LAUNCH(kTokenize, 0,
-         launch_tokenize1p(d_in, d_docs, ndocs, (uint32_t)chunks, dptr<uint8_t>(c->k1scratch),
+         launch_tokenize1p(d_in, d_docs, ndocs, (uint32_t)chunks, dptr<uint8_t>(c->meta, ml.scratch),
                            dptr<uint8_t>(c->letters), dptr<uint32_t>(c->starts), d_hist, d_wbase, d_lbase, d_item0,
                            d_meta, d_sticky, c->cfg.l_cap, c->cfg.wait_limit, st),
          "K1 tokenize");
   CK(cudaMemcpyAsync(c->h_meta.p, c->meta.p, ml.total, cudaMemcpyDeviceToHost, st), "read counts");
-  CK(cudaMemcpyAsync(c->h_sticky.p, c->sticky.p, sizeof(Meta), cudaMemcpyDeviceToHost, st), "read status");
   cudaEvent_t gap_a = nullptr;
   if (c->cfg.profile) {
     gap_a = next_event(c);
     if (gap_a) cudaEventRecord(gap_a, st);
   }
-  CK(cudaStreamSynchronize(st), "wait for counts");
+  CK(cudaEventRecord(c->counts_ev, st), "counts event");
+  CK(spin_wait(c->counts_ev), "wait for counts");
 
   const Meta* hm = hptr<Meta>(c->h_meta, ml.meta);
-  const Meta* hs = hptr<Meta>(c->h_sticky);
+  const Meta* hs = hm;  // K1 copies the context's sticky timeout count into meta
   const uint32_t* h_wbase = hptr<uint32_t>(c->h_meta, ml.wbase);
   const uint32_t* h_lbase = hptr<uint32_t>(c->h_meta, ml.lbase);
   const uint32_t* h_hist = hptr<uint32_t>(c->h_meta, ml.hist);
@@ -395,6 +417,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     uint32_t supertiles = 0;
     int max_w = 1;
     double key_bytes = 0;
+    double levels = 0;  // key-levels: each key times log2 of the sorted run it ends in
   };
   K4Launch k4[4] = {{8, 0, 6}, {4, 6, 7}, {2, 7, 8}, {1, 8, 9}};
   // bytes of a bucket's output: its letters and, if asked for, its offsets
@@ -430,6 +453,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
         l.max_w = std::max(l.max_w, W);
         // keys in, then runs out for K5 or the sorted words out
         l.key_bytes += 8.0 * W * sg.n + (sg.passes ? 8.0 * W * sg.n : out_bytes(sg));
+        l.levels += (double)sg.n * ceil_log2(std::min<uint64_t>(sg.n, (uint64_t)super));
       }
     if (gi >= 10) {
       sg.tile0 = wtiles[gi - 10];
@@ -506,7 +530,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       sx = side_stream();
       CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
     }
-    Trace tr_(c, sx, kTileSort, l.key_bytes);
+    Trace tr_(c, sx, kTileSort, l.key_bytes, l.levels);
     CK(tr_.done(launch_tile_sort2(l.cluster, d_segs, gbeg[l.g0], gbeg[l.g1], l.supertiles, c->sm_count, l.max_w, kA,
                                   eo, d_sticky, c->cfg.wait_limit, sx)),
        "K4 tile_sort");
@@ -514,7 +538,9 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   if (gbeg[10] > gbeg[9]) {
     cudaStream_t sx = side_stream();
     CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
-    Trace tr_(c, sx, kTileSort, (double)kb[9] + ob[9]);
+    double levels = 0;
+    for (uint32_t i = gbeg[9]; i < gbeg[10]; ++i) levels += (double)segs[i].n * ceil_log2(segs[i].n);
+    Trace tr_(c, sx, kTileSort, (double)kb[9] + ob[9], levels);
     CK(tr_.done(launch_warp_sort(d_segs, gbeg[9], gbeg[10], kA, eo, sx)), "K4 warp_sort");
   }
   for (int i = 0; i < used; ++i) {
@@ -524,10 +550,14 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   for (int g = 10; g < 12; ++g) {
     const uint32_t tiles = wtiles[g - 10];
     if (!tiles) continue;
-    LAUNCH(kTileSort, 2.0 * kb[g],
+    double levels = 0;
+    for (uint32_t k = gbeg[g]; k < gbeg[g + 1]; ++k)
+      levels += (double)segs[k].n * ceil_log2(std::min<uint64_t>(segs[k].n, segs[k].run0));
+    Trace tr_(c, st, kTileSort, 2.0 * kb[g], levels);
+    CK(tr_.done(
            launch_tile_sort(g == 10 ? 16 : 32, d_segs, gbeg[g], gbeg[g + 1], tiles, std::min(tiles, grid_cap), kA,
-                            d_sticky, c->cfg.wait_limit, st),
-           "K4 tile_sort (wide keys)");
+                            d_sticky, c->cfg.wait_limit, st)),
+       "K4 tile_sort (wide keys)");
   }
   // K5: merge passes over the buckets that need them, one launch per pass and
   // width.  With at least two tiles per resident CTA the pass is pipelined: a
@@ -701,7 +731,8 @@ bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
   c->device = dev;
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->counts_ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     bsort_destroy(c);  // frees whatever was created
     return BSORT_E_CUDA;
@@ -730,12 +761,13 @@ void bsort_destroy(bsort_ctx* c) {
   bsort_serve_shutdown(c);
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
-  for (DevBuf* b : {&c->sticky, &c->k1scratch, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream, &c->jobs})
+  for (DevBuf* b : {&c->sticky, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream, &c->jobs})
     if (b->p) cudaFree(b->p);
   for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets, &c->h_stream})
     if (b->p) cudaFreeHost(b->p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->counts_ev) cudaEventDestroy(c->counts_ev);
   for (int i = 0; i < bsort_ctx::kSide; ++i) {
     if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
     if (c->side[i]) cudaStreamDestroy(c->side[i]);
@@ -901,11 +933,13 @@ int bsort_profile_read(bsort_ctx* c, bsort_kernel_stat* out, int max) {
     out[k].launches = c->kind_launches[i];
     out[k].ms = ms[i];
     out[k].bytes = c->kind_bytes[i];
+    out[k].key_levels = c->kind_levels[i];
     ++k;
   }
   for (int i = 0; i < kKinds; ++i) {
     c->kind_launches[i] = 0;
     c->kind_bytes[i] = 0;
+    c->kind_levels[i] = 0;
   }
   c->recs.clear();
   c->ev_used = 0;

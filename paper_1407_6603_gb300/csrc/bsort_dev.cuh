@@ -276,6 +276,9 @@ inline cudaError_t once_per_device(int (&done)[64], F set) {
 
 // -------- launchers (each returns the launch's cudaError_t) --------
 
+// K1's look-back scratch (tokenize1p_scratch_bytes of it) must be zeroed
+// before the launch, and meta's histograms too; the caller clears both with
+// one memset.
 size_t tokenize1p_scratch_bytes(uint32_t nchunks);
 cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
                               uint8_t* scratch, uint8_t* letters, uint32_t* starts, uint32_t* hist,

@@ -91,19 +91,29 @@ __device__ __forceinline__ uint32_t mp_split_f(FA keyA, uint32_t la, FB keyB, ui
   return lo;
 }
 
-template <int W, int KPT, class FA, class FB>
-__device__ __forceinline__ void merge_run_f(FA keyA, uint32_t la, FB keyB, uint32_t lb, uint32_t a, uint32_t b,
-                                            Key<W> (&k)[KPT]) {
+// Sequential merge of KPT outputs from (a, b) when both runs sit in one
+// padded buffer (A's key i at offA + i, B's at offB + i).  The two heads stay
+// in registers and each step loads only the successor of the key it takes;
+// an exhausted run's head is +inf (all ones, which no key of letters equals),
+// so ties and ends need no bounds test in the compare.
+template <int W, int KPT>
+__device__ __forceinline__ void merge_run_buf(const uint64_t* buf, uint32_t offA, uint32_t la, uint32_t offB,
+                                              uint32_t lb, uint32_t a, uint32_t b, Key<W> (&k)[KPT]) {
+  Key<W> ha = a < la ? kload<W>(pkey<W>(buf, offA + a)) : kinf<W>();
+  Key<W> hb = b < lb ? kload<W>(pkey<W>(buf, offB + b)) : kinf<W>();
 #pragma unroll
   for (int s = 0; s < KPT; ++s) {
-    const Key<W> ka = a < la ? keyA(a) : kinf<W>();
-    const Key<W> kb = b < lb ? keyB(b) : kinf<W>();
-    const bool take_a = a < la && (b >= lb || !klt(kb, ka));
-    k[s] = ksel(take_a, ka, kb);
-    if (take_a)
-      ++a;
-    else
-      ++b;
+    const bool take_a = !klt(hb, ha);
+    k[s] = ksel(take_a, ha, hb);
+    if (s + 1 < KPT) {
+      a += take_a ? 1u : 0u;
+      b += take_a ? 0u : 1u;
+      const bool more = take_a ? a < la : b < lb;
+      const uint32_t pos = take_a ? offA + a : offB + b;
+      const Key<W> nx = more ? kload<W>(pkey<W>(buf, pos)) : kinf<W>();
+      ha = take_a ? nx : ha;
+      hb = take_a ? hb : nx;
+    }
   }
 }
 
@@ -133,7 +143,7 @@ __device__ void cta_sort(uint64_t* buf) {
     auto keyA = [&](uint32_t i) { return kload<W>(pkey<W>(buf, base + i)); };
     auto keyB = [&](uint32_t i) { return kload<W>(pkey<W>(buf, base + R + i)); };
     const uint32_t a = mp_split_f<W>(keyA, R, keyB, R, d);
-    merge_run_f<W, KPT>(keyA, R, keyB, R, a, d - a, k);
+    merge_run_buf<W, KPT>(buf, base, R, base + R, R, a, d - a, k);
   }
   __syncthreads();
 #pragma unroll
@@ -175,7 +185,7 @@ __device__ void cluster_merge(uint64_t* buf0, uint64_t* buf1, uint32_t r) {
     auto sA = [&](uint32_t i) { return kload<W>(pkey<W>(buf1, i)); };
     auto sB = [&](uint32_t i) { return kload<W>(pkey<W>(buf1, na + i)); };
     const uint32_t a = mp_split_f<W>(sA, na, sB, nb, pos);
-    merge_run_f<W, KPT>(sA, na, sB, nb, a, pos - a, k);
+    merge_run_buf<W, KPT>(buf1, 0, na, na, nb, a, pos - a, k);
 #pragma unroll
     for (int i = 0; i < KPT; ++i) kstore<W>(pkey<W>(buf0, pos + i), k[i]);
     cluster.sync();  // this level's output is visible to the next level's readers
@@ -417,7 +427,7 @@ __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t
     auto sA = [&](uint32_t i) { return kload<W>(pkey<W>(sm, i)); };
     auto sB = [&](uint32_t i) { return kload<W>(pkey<W>(sm, na + i)); };
     const uint32_t a = mp_split_f<W>(sA, na, sB, nb, pos);
-    merge_run_f<W, KPT>(sA, na, sB, nb, a, pos - a, k);
+    merge_run_buf<W, KPT>(sm, 0, na, na, nb, a, pos - a, k);
   }
   __syncthreads();
 #pragma unroll
@@ -572,7 +582,7 @@ __global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_piped(c
       auto sA = [&](uint32_t i) { return kload<W>(pkey<W>(buf, i)); };
       auto sB = [&](uint32_t i) { return kload<W>(pkey<W>(buf, na + i)); };
       const uint32_t a = mp_split_f<W>(sA, na, sB, nb, pos);
-      merge_run_f<W, KPT>(sA, na, sB, nb, a, pos - a, kk);
+      merge_run_buf<W, KPT>(buf, 0, na, na, nb, a, pos - a, kk);
     }
     __syncthreads();
 #pragma unroll

@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
   __threadfence();
   const TokAcc all = nchunks ? ld_acc(&s->rec[nchunks - 1].inc) : kAccZero;
   if (t == 0) {
+    meta->err_timeout = ld_acquire(&sticky->err_timeout);  // the host reads it with the counts
     meta->n_total = all.words;
     meta->s_total = all.letters;
     starts[all.words] = all.letters;  // the last word ends at the end of S
@@ -397,8 +398,7 @@ cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t n
                               uint8_t* scratch, uint8_t* letters, uint32_t* starts, uint32_t* hist,
                               uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
                               Meta* sticky, uint32_t l_cap, uint64_t wait_limit, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(scratch, 0, tokenize1p_scratch_bytes(nchunks), st);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   const size_t smem = (size_t)(kChunk / 2) * sizeof(uint32_t);
   static int attr_done[64];
   e = once_per_device(attr_done, [&] {
