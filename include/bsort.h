@@ -58,6 +58,23 @@ typedef struct {
                             0 (default): no events are recorded */
   uint64_t wait_limit;   /* iteration limit of every device-side spin wait (0 = default, about
                             a second); when one runs out the call returns BSORT_E_TIMEOUT */
+  const char* tune_table; /* NULL (default): built-in tuning.  Otherwise text of `key=value`
+                            items separated by spaces, semicolons or newlines, '#' to end of
+                            line a comment (the autotuner, paper_1407_6603_gb300/autotune.py,
+                            writes it):
+                              k4_lanes=a,b,c,d  lanes per odd-even transposition group of the
+                                                tile sort (the odd-even/merge cutoff: runs of
+                                                lanes x keys-per-thread keys leave odd-even
+                                                transposition) for buckets sorted by clusters
+                                                of 1, 2, 4 and 8 CTAs; each 2, 4 or 8
+                              piped_min=k       merge passes with at least k tiles per resident
+                                                CTA use the pipelined merge (1..1000000)
+                              k4_streams=0|1    1 (default): the tile sorts of the smaller
+                                                classes run beside the largest on side
+                                                streams; 0: one after another on the call's
+                                                stream (how the autotuner times a class)
+                            Copied at bsort_create; an unknown key or a bad value makes
+                            bsort_create fail with BSORT_E_INVAL. */
 } bsort_config;
 
 /*
@@ -81,7 +98,8 @@ typedef struct {
   const uint8_t* stream;    /* [stream_bytes] */
 } bsort_result;
 
-/* Default configuration: l_cap 255, offsets on, current device, default wait limit. */
+/* Default configuration: l_cap 255, offsets on, current device, default wait limit,
+ * built-in tuning. */
 void bsort_config_default(bsort_config* cfg);
 
 /*
@@ -178,8 +196,9 @@ typedef struct {
   double start_ms;    /* start, in ms after the first traced launch since the last bsort_profile_read */
   double end_ms;      /* end, on the same clock */
   double bytes;       /* algorithmic bytes */
-  uint32_t stream;    /* 0: the call's stream; 1..4: the side streams K4 uses */
-  uint32_t pad;
+  uint32_t stream;    /* 0: the call's stream; 1..4: the side streams of the tile sorts and merges */
+  uint32_t variant;   /* tile_sort: CTAs per cluster (0: the one-warp sort of tiny buckets);
+                         merge_pass / merge_cut: key width in u64 words; else 0 */
 } bsort_trace_rec;
 
 /* Writes up to `max` traced launches, in launch order, into out[] (waiting for

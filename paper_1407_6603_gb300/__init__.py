@@ -35,7 +35,7 @@ STATUS_NAMES = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_TOO_LARG
 
 class bsort_config(ctypes.Structure):
     _fields_ = [("l_cap", ctypes.c_uint32), ("want_offsets", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("wait_limit", ctypes.c_uint64)]
+                ("profile", ctypes.c_int32), ("wait_limit", ctypes.c_uint64), ("tune_table", ctypes.c_char_p)]
 
 
 class bsort_kernel_stat(ctypes.Structure):
@@ -45,7 +45,7 @@ class bsort_kernel_stat(ctypes.Structure):
 
 class bsort_trace_rec(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double),
-                ("bytes", ctypes.c_double), ("stream", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("bytes", ctypes.c_double), ("stream", ctypes.c_uint32), ("variant", ctypes.c_uint32)]
 
 
 class bsort_result(ctypes.Structure):
@@ -217,7 +217,7 @@ def bsort_profile_read(h) -> dict:
 
 def bsort_trace_read(h) -> list[tuple[str, float, float, float, int]]:
     """Traced launches since the last profile read, in launch order:
-    (family, start ms, end ms, algorithmic bytes, stream)."""
+    (family, start ms, end ms, algorithmic bytes, stream, variant)."""
     lib = load()
     n = lib.bsort_trace_read(h, None, 0)
     if n < 0:
@@ -226,7 +226,8 @@ def bsort_trace_read(h) -> list[tuple[str, float, float, float, int]]:
     n = lib.bsort_trace_read(h, arr, n)
     if n < 0:
         raise BsortError(BSORT_E_CUDA, "bsort_trace_read failed")
-    return [(arr[i].name.decode(), arr[i].start_ms, arr[i].end_ms, arr[i].bytes, int(arr[i].stream)) for i in range(n)]
+    return [(arr[i].name.decode(), arr[i].start_ms, arr[i].end_ms, arr[i].bytes, int(arr[i].stream),
+             int(arr[i].variant)) for i in range(n)]
 
 
 def bsort_launch_count(h) -> int:
@@ -330,13 +331,17 @@ class Context:
     """Owns a bsort context (CUDA stream, device arena, pinned host buffers)."""
 
     def __init__(self, l_cap: int = 255, want_offsets: bool = True, device: int = -1, wait_limit: int = 0,
-                 profile: bool = False):
+                 profile: bool = False, tune_table: str | None = None):
+        """tune_table: None for the built-in tuning, else the text of a tune
+        table (see bsort_config.tune_table; autotune.py writes one)."""
         cfg = bsort_config_default()
         cfg.l_cap = l_cap
         cfg.want_offsets = 1 if want_offsets else 0
         cfg.device = device
         cfg.profile = 1 if profile else 0
         cfg.wait_limit = wait_limit
+        self._tune = tune_table.encode() if tune_table is not None else None
+        cfg.tune_table = self._tune
         self.want_offsets = want_offsets
         self._h = bsort_create(cfg)
 

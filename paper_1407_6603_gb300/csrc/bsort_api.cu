@@ -46,6 +46,65 @@ uint32_t merge_passes(uint64_t n, uint64_t tile) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Tuning chosen per bucket-size class (see bsort_config.tune_table).  The
+// built-in values are what the autotuner (autotune.py) picked on a GB300.
+struct Tune {
+  int k4_lanes[4] = {2, 2, 2, 2};  // clusters of 1, 2, 4, 8 CTAs
+  uint32_t piped_min = 4;
+  int k4_streams = 1;  // 1: the tile sorts of the smaller classes run on side streams
+};
+
+// Parses a tune table; false on an unknown key or a bad value.
+bool parse_tune(const char* text, Tune& t) {
+  if (!text) return true;
+  std::string s(text);
+  size_t i = 0;
+  auto is_sep = [](char ch) { return ch == ' ' || ch == '\t' || ch == '\n' || ch == '\r' || ch == ';'; };
+  while (i < s.size()) {
+    if (is_sep(s[i])) {
+      ++i;
+      continue;
+    }
+    if (s[i] == '#') {
+      while (i < s.size() && s[i] != '\n') ++i;
+      continue;
+    }
+    size_t j = i;
+    while (j < s.size() && !is_sep(s[j]) && s[j] != '#') ++j;
+    const std::string item = s.substr(i, j - i);
+    i = j;
+    const size_t eq = item.find('=');
+    if (eq == std::string::npos) return false;
+    const std::string key = item.substr(0, eq), val = item.substr(eq + 1);
+    std::vector<long> nums;
+    size_t k = 0;
+    while (k <= val.size()) {
+      size_t e = val.find(',', k);
+      if (e == std::string::npos) e = val.size();
+      const std::string tok = val.substr(k, e - k);
+      if (tok.empty() || tok.size() > 9 || tok.find_first_not_of("0123456789") != std::string::npos) return false;
+      nums.push_back(std::stol(tok));
+      k = e + 1;
+    }
+    if (key == "k4_lanes") {
+      if (nums.size() != 4) return false;
+      for (int q = 0; q < 4; ++q) {
+        if (nums[q] != 2 && nums[q] != 4 && nums[q] != 8) return false;
+        t.k4_lanes[q] = (int)nums[q];
+      }
+    } else if (key == "k4_streams") {
+      if (nums.size() != 1 || nums[0] > 1) return false;
+      t.k4_streams = (int)nums[0];
+    } else if (key == "piped_min") {
+      if (nums.size() != 1 || nums[0] < 1 || nums[0] > 1000000) return false;
+      t.piped_min = (uint32_t)nums[0];
+    } else {
+      return false;
+    }
+  }
+  return true;
+}
+
 // Layout of the device "meta" region, read back in one copy after K2.
 // The meta region: what K1 leaves for the host (read back in one copy of
 // `total` bytes), then K1's look-back scratch; one memset clears both.
@@ -73,7 +132,8 @@ struct ProfRec {
   int kind;
   cudaEvent_t a, b;
   double bytes;
-  uint32_t stream;  // 0: the call's stream; 1.. the side streams
+  uint32_t stream;   // 0: the call's stream; 1.. the side streams
+  uint32_t variant;  // tile sort: CTAs per cluster (0: warp sort); merge: key width
 };
 
 }  // namespace
@@ -89,6 +149,8 @@ struct bsort_ctx {
   cudaEvent_t counts_ev = nullptr;  // the counts of K1 reached the host
   std::string err;
   bool busy = false;
+  Tune tune;
+  std::string tune_text;  // the caller's tune table, copied
 
   DevBuf sticky;  // a Meta kept across calls: err_timeout of bounded device waits
   HostBuf h_sticky;
@@ -210,6 +272,7 @@ struct Trace {
   int kind;
   double bytes;
   double levels;
+  uint32_t variant = 0;
   cudaEvent_t a = nullptr;
   Trace(bsort_ctx* c_, cudaStream_t st_, int kind_, double bytes_, double levels_ = 0.0)
       : c(c_), st(st_), kind(kind_), bytes(bytes_), levels(levels_) {
@@ -231,7 +294,7 @@ struct Trace {
         uint32_t sx = 0;
         for (int i = 0; i < bsort_ctx::kSide; ++i)
           if (st == c->side[i]) sx = (uint32_t)i + 1;
-        c->recs.push_back(ProfRec{kind, a, b, bytes, sx});
+        c->recs.push_back(ProfRec{kind, a, b, bytes, sx, variant});
       }
     }
     return e;
@@ -489,7 +552,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     cudaEvent_t gap_b = next_event(c);
     if (gap_b) {
       cudaEventRecord(gap_b, st);
-      c->recs.push_back(ProfRec{kHostGap, gap_a, gap_b, 0.0, 0u});
+      c->recs.push_back(ProfRec{kHostGap, gap_a, gap_b, 0.0, 0u, 0u});
       c->kind_launches[kHostGap] += 1;
     }
   }
@@ -514,11 +577,14 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   // K4: the clusters of 8 on the call's stream; the smaller kernels, which
   // sort other buckets, each on a side stream at the same time, joined back
   // before the merge passes
-  const bool side = gbeg[10] > gbeg[6];
+  // (with k4_streams=0 in the tune table every launch stays on the call's
+  // stream, one after another: how the autotuner times each class alone)
+  const bool side = gbeg[10] > gbeg[6] && c->tune.k4_streams;
   if (side) CK(cudaEventRecord(c->fork_ev, st), "fork");
   int used = 0;
   cudaStream_t joined[bsort_ctx::kSide];
   auto side_stream = [&]() -> cudaStream_t {
+    if (!side) return st;
     cudaStream_t sx = c->side[used];
     joined[used++] = sx;
     return sx;
@@ -526,18 +592,20 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   for (const K4Launch& l : k4) {
     if (!l.supertiles) continue;
     cudaStream_t sx = st;
-    if (l.cluster != kSuperCluster) {
+    if (l.cluster != kSuperCluster && side) {
       sx = side_stream();
       CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
     }
     Trace tr_(c, sx, kTileSort, l.key_bytes, l.levels);
-    CK(tr_.done(launch_tile_sort2(l.cluster, d_segs, gbeg[l.g0], gbeg[l.g1], l.supertiles, c->sm_count, l.max_w, kA,
+    tr_.variant = (uint32_t)l.cluster;
+    const int lanes = c->tune.k4_lanes[l.cluster == 1 ? 0 : l.cluster == 2 ? 1 : l.cluster == 4 ? 2 : 3];
+    CK(tr_.done(launch_tile_sort2(l.cluster, lanes, d_segs, gbeg[l.g0], gbeg[l.g1], l.supertiles, c->sm_count, l.max_w, kA,
                                   eo, d_sticky, c->cfg.wait_limit, sx)),
        "K4 tile_sort");
   }
   if (gbeg[10] > gbeg[9]) {
     cudaStream_t sx = side_stream();
-    CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
+    if (side) CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
     double levels = 0;
     for (uint32_t i = gbeg[9]; i < gbeg[10]; ++i) levels += (double)segs[i].n * ceil_log2(segs[i].n);
     Trace tr_(c, sx, kTileSort, (double)kb[9] + ob[9], levels);
@@ -554,6 +622,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     for (uint32_t k = gbeg[g]; k < gbeg[g + 1]; ++k)
       levels += (double)segs[k].n * ceil_log2(std::min<uint64_t>(segs[k].n, segs[k].run0));
     Trace tr_(c, st, kTileSort, 2.0 * kb[g], levels);
+    tr_.variant = 1;
     CK(tr_.done(
            launch_tile_sort(g == 10 ? 16 : 32, d_segs, gbeg[g], gbeg[g + 1], tiles, std::min(tiles, grid_cap), kA,
                             d_sticky, c->cfg.wait_limit, st)),
@@ -570,7 +639,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   int chains = 0;
   for (int g = 0; g < 4; ++g) {
     if (mpasses[g]) ++chains;
-    if (mtiles[g] >= 2 * piped_grid) {
+    if (mtiles[g] >= c->tune.piped_min * piped_grid) {
       job_at[g] = jobs_total;
       jobs_total += mtiles[g];
     }
@@ -593,16 +662,19 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
           moved += 8.0 * W * segs[i].n + (segs[i].passes == p + 1 ? out_bytes(segs[i]) : 8.0 * W * segs[i].n);
       const uint64_t* src = (p & 1) ? kB : kA;
       uint64_t* dst = (p & 1) ? kA : kB;
-      if (mtiles[g] >= 2 * piped_grid) {
+      if (mtiles[g] >= c->tune.piped_min * piped_grid) {
         TileJob* jobs = dptr<TileJob>(c->jobs) + job_at[g];
         {
           Trace tr_(c, sx, kMergeCut, 0.0);
+          tr_.variant = (uint32_t)W;
           CK(tr_.done(launch_merge_cut(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g], p, src, jobs, sx)), "K5 merge cut");
         }
         Trace tr_(c, sx, kMerge, moved);
+        tr_.variant = (uint32_t)W;
         CK(tr_.done(launch_merge_piped(W, jobs, mtiles[g], piped_grid, src, dst, eo, sx)), "K5 merge_pass");
       } else {
         Trace tr_(c, sx, kMerge, moved);
+        tr_.variant = (uint32_t)W;
         CK(tr_.done(launch_merge_pass2(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g],
                                        std::min<uint32_t>(mtiles[g], (uint32_t)c->sm_count * 8), p, src, dst, eo,
                                        sx)),
@@ -703,6 +775,7 @@ void bsort_config_default(bsort_config* cfg) {
   cfg->device = -1;
   cfg->profile = 0;
   cfg->wait_limit = 0;
+  cfg->tune_table = nullptr;
 }
 
 bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
@@ -716,6 +789,8 @@ bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
   if (conf.wait_limit == 0) conf.wait_limit = kDefaultWaitLimit;
   conf.want_offsets = conf.want_offsets ? 1 : 0;
   conf.profile = conf.profile ? 1 : 0;
+  Tune tune;
+  if (!parse_tune(conf.tune_table, tune)) return BSORT_E_INVAL;
   int dev = conf.device;
   if (dev < 0 && cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -729,6 +804,9 @@ bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
   if (!c) return BSORT_E_NOMEM;
   c->cfg = conf;
   c->device = dev;
+  c->tune = tune;
+  if (conf.tune_table) c->tune_text = conf.tune_table;
+  c->cfg.tune_table = conf.tune_table ? c->tune_text.c_str() : nullptr;
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
@@ -963,7 +1041,7 @@ int bsort_trace_read(bsort_ctx* c, bsort_trace_rec* out, int max) {
         cudaGetLastError();
         return -1;
       }
-      out[k] = bsort_trace_rec{kKindName[r.kind], s, e, r.bytes, r.stream, 0u};
+      out[k] = bsort_trace_rec{kKindName[r.kind], s, e, r.bytes, r.stream, r.variant};
     }
     ++k;
   }

@@ -1,273 +1,17 @@
-// K4 and K5 for keys of up to 8 u64 words (words of up to 64 letters):
-// phase 3 of the paper's method, the sort of each length bucket into ASCII
-// order (Section II; Section III step 4).
+// K4's warp sort for tiny buckets and K5, the merge passes, for keys of up
+// to 8 u64 words: phase 3 of the paper's method, the sort of each length
+// bucket into ASCII order (Section II; Section III step 4).  The tile sort
+// itself (clusters of CTAs) is in tile_sort2.cuh.
 //
-// K4 (k_tile_sort2<CL>) sorts "supertiles".  One CTA of 256 threads holds a
-// tile of 2048 u64 words (2048 / W keys) in shared memory, staged by a TMA bulk copy, and sorts it with the bubble sort's
-// compare-exchange in its parallel form, odd-even transposition:
-//   1. each thread sorts its 8 / W keys in registers (odd-even transposition);
-//   2. groups of kLanesG lanes run kLanesG rounds of odd-even transposition
-//      between lane neighbours, whole sorted runs exchanged through warp
-//      shuffles (the merge-split form of the compare-exchange);
-//   3. merge path in shared memory takes those runs up to the tile.
-// With CL > 1 the launch uses thread-block clusters of CL CTAs: a cluster
-// owns CL consecutive tiles of one bucket and merges them into one run of
-// CL tiles through distributed shared memory, each CTA producing its own
-// tile of every merge level from slices it copies out of its peers' shared
-// memory.  Buckets of up to CL tiles leave K4 fully sorted; larger ones leave
-// it as runs of CL tiles (16 Ki u64 words with CL = 8), and K5 merges those.
-//
-// K5 (k_merge_pass2<W>) merges run pairs, one pass per launch and key width,
-// for every bucket of that width.  Each CTA takes chunks of consecutive
-// output tiles; where its output diagonal cuts the two runs (merge path) is
-// found by a 256-way parallel search in global memory, and within a chunk the
-// end of one tile is the start of the next, so one search per tile suffices.
-#include <cooperative_groups.h>
-
-#include "bsort_dev.cuh"
-#include "sort_common.cuh"
-
-namespace cg = cooperative_groups;
+// K5 (k_merge_pass2<W>, and the pipelined k_merge_cut<W> + k_merge_piped<W>)
+// merges run pairs, one pass per launch and key width, for every bucket of
+// that width.  Each CTA produces output tiles; where a tile's output diagonal
+// cuts the two runs (merge path) is found by a parallel search in global
+// memory, and the tile is merged in shared memory.
+#include "tile_sort2.cuh"
 
 namespace bsort {
 namespace {
-
-constexpr int kT2Threads = 256;
-// Lanes per odd-even transposition group in K4 (the odd-even/merge cutoff:
-// runs of kLanesG * KPT keys leave the transposition stage, merges take them
-// up to the tile) and the CTAs per SM that K4's register budget aims for.
-// Both are tuning constants, set at build time by the autotuning sweep.
-#ifndef BSORT_K4_LANES
-#define BSORT_K4_LANES 4
-#endif
-#ifndef BSORT_K4_MIN_CTAS
-#define BSORT_K4_MIN_CTAS 4
-#endif
-constexpr int kLanesG = BSORT_K4_LANES;
-
-template <int W>
-__host__ __device__ constexpr int kpt2() {
-  return W >= 8 ? 1 : 8 / W;
-}
-template <int W>
-__host__ __device__ constexpr uint32_t tile_words2() {
-  return (uint32_t)kT2Threads * kpt2<W>() * W;  // 2048 u64 words, 4096 for W = 16
-}
-
-constexpr int kM2Threads = 256;
-// CTAs per SM that K5's register budget aims for (a tuning constant).
-#ifndef BSORT_K5_MIN_CTAS
-#define BSORT_K5_MIN_CTAS 4
-#endif
-
-// Shared-memory layout of a tile: one pad word after every 16 u64 words, so
-// that threads reading keys KPT*W words apart (their own runs) or at random
-// merge positions spread over all banks.  A key of W <= 16 words never
-// straddles a pad (W divides 16), so its words stay contiguous.
-__device__ __forceinline__ uint32_t padw(uint32_t w) { return w + (w >> 4); }
-__host__ __device__ inline uint32_t padded_words(uint32_t w) { return w + (w >> 4); }
-
-template <int W>
-__device__ __forceinline__ const uint64_t* pkey(const uint64_t* buf, uint32_t k) {
-  return buf + padw(k * W);
-}
-template <int W>
-__device__ __forceinline__ uint64_t* pkey(uint64_t* buf, uint32_t k) {
-  return buf + padw(k * W);
-}
-
-// Merge path over two runs given by accessors: how many of the first d
-// outputs come from A, ties going to A.
-template <int W, class FA, class FB>
-__device__ __forceinline__ uint32_t mp_split_f(FA keyA, uint32_t la, FB keyB, uint32_t lb, uint32_t d) {
-  uint32_t lo = d > lb ? d - lb : 0u, hi = d < la ? d : la;
-  while (lo < hi) {
-    const uint32_t m = (lo + hi) >> 1;
-    if (klt(keyB(d - 1 - m), keyA(m)))
-      hi = m;
-    else
-      lo = m + 1;
-  }
-  return lo;
-}
-
-// Sequential merge of KPT outputs from (a, b) when both runs sit in one
-// padded buffer (A's key i at offA + i, B's at offB + i).  The two heads stay
-// in registers and each step loads only the successor of the key it takes;
-// an exhausted run's head is +inf (all ones, which no key of letters equals),
-// so ties and ends need no bounds test in the compare.
-template <int W, int KPT>
-__device__ __forceinline__ void merge_run_buf(const uint64_t* buf, uint32_t offA, uint32_t la, uint32_t offB,
-                                              uint32_t lb, uint32_t a, uint32_t b, Key<W> (&k)[KPT]) {
-  Key<W> ha = a < la ? kload<W>(pkey<W>(buf, offA + a)) : kinf<W>();
-  Key<W> hb = b < lb ? kload<W>(pkey<W>(buf, offB + b)) : kinf<W>();
-#pragma unroll
-  for (int s = 0; s < KPT; ++s) {
-    const bool take_a = !klt(hb, ha);
-    k[s] = ksel(take_a, ha, hb);
-    if (s + 1 < KPT) {
-      a += take_a ? 1u : 0u;
-      b += take_a ? 0u : 1u;
-      const bool more = take_a ? a < la : b < lb;
-      const uint32_t pos = take_a ? offA + a : offB + b;
-      const Key<W> nx = more ? kload<W>(pkey<W>(buf, pos)) : kinf<W>();
-      ha = take_a ? nx : ha;
-      hb = take_a ? hb : nx;
-    }
-  }
-}
-
-// Sorts the tile staged (unpadded, by TMA) in buf; the sorted tile is left in
-// buf in the padded layout.
-template <int W, int G>
-__device__ void cta_sort(uint64_t* buf) {
-  constexpr int KPT = kpt2<W>();
-  constexpr uint32_t T = kT2Threads * KPT;
-  const int t = threadIdx.x;
-  Key<W> k[KPT];
-  // The tile is unsorted, so any assignment of keys to threads will do:
-  // take them striped, which reads consecutive words across the warp.
-#pragma unroll
-  for (int i = 0; i < KPT; ++i) k[i] = kload<W>(buf + (size_t)(t + i * kT2Threads) * W);
-  oets_registers<W, KPT>(k);
-  oets_lanes<W, KPT, G>(k);
-#pragma unroll 1
-  for (uint32_t R = G * KPT; R < T; R <<= 1) {
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < KPT; ++i) kstore<W>(pkey<W>(buf, t * KPT + i), k[i]);
-    __syncthreads();
-    const uint32_t pos = t * KPT;
-    const uint32_t base = pos & ~(2 * R - 1);
-    const uint32_t d = pos - base;
-    auto keyA = [&](uint32_t i) { return kload<W>(pkey<W>(buf, base + i)); };
-    auto keyB = [&](uint32_t i) { return kload<W>(pkey<W>(buf, base + R + i)); };
-    const uint32_t a = mp_split_f<W>(keyA, R, keyB, R, d);
-    merge_run_buf<W, KPT>(buf, base, R, base + R, R, a, d - a, k);
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < KPT; ++i) kstore<W>(pkey<W>(buf, t * KPT + i), k[i]);
-  __syncthreads();
-}
-
-// Merges the CL sorted tiles of a cluster (CTA q holds supertile positions
-// [q*T, (q+1)*T) in its buf0, padded layout) into one sorted run.
-template <int W, int CL>
-__device__ void cluster_merge(uint64_t* buf0, uint64_t* buf1, uint32_t r) {
-  constexpr int KPT = kpt2<W>();
-  constexpr uint32_t T = kT2Threads * KPT;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int t = threadIdx.x;
-  auto key_at = [&](uint32_t pos) {  // key `pos` of the supertile, in its owner's shared memory
-    return kload<W>(cluster.map_shared_rank(pkey<W>(buf0, pos % T), pos / T));
-  };
-  cluster.sync();
-#pragma unroll 1
-  for (uint32_t R = T; R < CL * T; R <<= 1) {
-    const uint32_t pos0 = r * T;
-    const uint32_t pb = pos0 & ~(2 * R - 1);
-    const uint32_t d0 = pos0 - pb;
-    auto keyA = [&](uint32_t i) { return key_at(pb + i); };
-    auto keyB = [&](uint32_t i) { return key_at(pb + R + i); };
-    const uint32_t a0 = coop_split_fn<W, kT2Threads>(keyA, R, keyB, R, d0);
-    const uint32_t a1 = coop_split_fn<W, kT2Threads>(keyA, R, keyB, R, d0 + T);
-    const uint32_t na = a1 - a0, b0 = d0 - a0, nb = T - na;
-    // copy the two slices into buf1 (keys [0, na) from A, [na, T) from B)
-    for (uint32_t e = t; e < T * W; e += kT2Threads) {
-      const uint32_t kk = e / W, j = e % W;
-      const uint32_t src = kk < na ? pb + a0 + kk : pb + R + b0 + (kk - na);
-      buf1[padw(e)] = cluster.map_shared_rank(pkey<W>(buf0, src % T), src / T)[j];
-    }
-    cluster.sync();  // every peer has its slices: buf0 may be overwritten
-    Key<W> k[KPT];
-    const uint32_t pos = t * KPT;
-    auto sA = [&](uint32_t i) { return kload<W>(pkey<W>(buf1, i)); };
-    auto sB = [&](uint32_t i) { return kload<W>(pkey<W>(buf1, na + i)); };
-    const uint32_t a = mp_split_f<W>(sA, na, sB, nb, pos);
-    merge_run_buf<W, KPT>(buf1, 0, na, na, nb, a, pos - a, k);
-#pragma unroll
-    for (int i = 0; i < KPT; ++i) kstore<W>(pkey<W>(buf0, pos + i), k[i]);
-    cluster.sync();  // this level's output is visible to the next level's readers
-  }
-}
-
-template <int W, int CL>
-__device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint64_t* keys, uint64_t* buf0,
-                               uint64_t* buf1, uint64_t* bar, uint32_t& phase, const EmitOut& eo, Meta* meta,
-                               uint64_t wait_limit) {
-  constexpr int KPT = kpt2<W>();
-  constexpr uint32_t T = kT2Threads * KPT;
-  constexpr uint32_t TW = T * W;
-  const int t = threadIdx.x;
-  const uint64_t j0 = (uint64_t)(st - sg.stile0) * CL * T + (uint64_t)r * T;
-  const uint64_t left = j0 < sg.n ? sg.n - j0 : 0ull;
-  const uint32_t cnt = left < T ? (uint32_t)left : T;
-  uint64_t* g = keys + sg.key_off + j0 * W;
-  const uint32_t tma_bytes = (cnt * W * 8u) & ~15u;
-  if (t == 0) {
-    fence_proxy_async();
-    mbar_arrive_expect_tx(bar, tma_bytes);
-    if (tma_bytes) tma_load_1d(buf0, g, tma_bytes, bar);
-  }
-  for (uint32_t e = tma_bytes / 8 + t; e < TW; e += kT2Threads)
-    buf0[e] = e < cnt * W ? g[e] : ~0ull;  // odd tail word, then +inf padding
-  const bool ok = mbar_wait_bounded(bar, phase, wait_limit);
-  phase ^= 1u;
-  if (__syncthreads_or(!ok)) {
-    // The copy did not land in time: report it and let it drain.  The CTA
-    // stays in step with its cluster (no early exit); the call fails.
-    if (t == 0) {
-      atomicAdd(&meta->err_timeout, 1u);
-      mbar_wait_bounded(bar, phase ^ 1u, wait_limit);
-    }
-    __syncthreads();
-  }
-  cta_sort<W, kLanesG>(buf0);
-  if constexpr (CL > 1) cluster_merge<W, CL>(buf0, buf1, r);
-  if (sg.passes == 0) {  // the bucket is sorted: its words go straight out
-    emit_tile<kT2Threads>(sg, (uint32_t)j0, cnt, [&](uint32_t j, uint32_t q) { return buf0[padw(j * W + q)]; }, eo);
-  } else {  // a run of CL tiles for K5
-    for (uint32_t e = t; e < cnt * W; e += kT2Threads) g[e] = buf0[padw(e)];
-  }
-  __syncthreads();
-}
-
-template <int CL>
-__global__ void __launch_bounds__(kT2Threads, BSORT_K4_MIN_CTAS) k_tile_sort2(const Segment* __restrict__ segs, uint32_t sbeg,
-                                                           uint32_t send, uint32_t nst, uint32_t buf_words,
-                                                           uint64_t* keys, EmitOut eo, Meta* meta,
-                                                           uint64_t wait_limit) {
-  extern __shared__ __align__(128) uint64_t sm[];
-  uint64_t* buf0 = sm;
-  uint64_t* buf1 = sm + buf_words;
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ uint32_t s_seg;
-  __shared__ uint32_t s_first[kSegCache];
-  const int t = threadIdx.x;
-  const bool cached = seg_cache_fill<kByStile0>(segs, sbeg, send, s_first);
-  uint32_t r = 0;
-  if constexpr (CL > 1) r = cg::this_cluster().block_rank();
-  const uint32_t cid = blockIdx.x / CL, ncl = gridDim.x / CL;
-  if (t == 0) {
-    mbar_init(&bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  uint32_t phase = 0;
-  for (uint32_t st = cid; st < nst; st += ncl) {  // uniform across the cluster
-    if (t == 0) s_seg = seg_find<kByStile0>(segs, sbeg, send, s_first, cached, st);
-    __syncthreads();
-    const Segment sg = segs[s_seg];
-    __syncthreads();
-    switch (width_of_len(sg.L)) {
-      case 1: sort_supertile<1, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
-      case 2: sort_supertile<2, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
-      case 4: sort_supertile<4, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
-      default: sort_supertile<8, CL>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
-    }
-  }
-}
 
 // ------------------------------------------------------- tiny buckets ----
 // Buckets of at most 32 * KPT keys: one warp each.  The keys go to registers
@@ -621,50 +365,6 @@ cudaError_t merge_pass2_w(const Segment* segs, uint32_t sbeg, uint32_t send, uin
   return cudaGetLastError();
 }
 
-template <int CL>
-cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t nst, int max_grid,
-                          int max_width, uint64_t* keys, const EmitOut& eo, Meta* meta, uint64_t wait_limit,
-                          cudaStream_t st) {
-  (void)max_width;
-  const uint32_t buf_words = padded_words(2048u);
-  const size_t smem = (size_t)(CL > 1 ? 2 : 1) * buf_words * 8;
-  static int attr_done[64];
-  static int clusters_cached[64];
-  cudaError_t e = once_per_device(attr_done, [&] {
-    cudaError_t r = cudaFuncSetAttribute(k_tile_sort2<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (r == cudaSuccess)  // shared memory, not L1, limits how many CTAs fit
-      r = cudaFuncSetAttribute(k_tile_sort2<CL>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    return r;
-  });
-  if (e != cudaSuccess) return e;
-  cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(kT2Threads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int clusters = (dev >= 0 && dev < 64) ? clusters_cached[dev] : 0;
-  if (clusters <= 0) {
-    cfg.gridDim = dim3(CL, 1, 1);
-    e = cudaOccupancyMaxActiveClusters(&clusters, k_tile_sort2<CL>, &cfg);
-    if (e != cudaSuccess || clusters <= 0) {
-      cudaGetLastError();
-      clusters = max(1, max_grid / CL);
-    }
-    if (dev >= 0 && dev < 64) clusters_cached[dev] = clusters;
-  }
-  const uint32_t ncl = nst < (uint32_t)clusters * 2u ? nst : (uint32_t)clusters * 2u;
-  cfg.gridDim = dim3(ncl * CL, 1, 1);
-  return cudaLaunchKernelEx(&cfg, k_tile_sort2<CL>, segs, sbeg, send, nst, buf_words, keys, eo, meta, wait_limit);
-}
-
 }  // namespace
 
 cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, uint64_t* keys, EmitOut eo,
@@ -676,15 +376,14 @@ cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_sort2(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
-                              int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
+cudaError_t launch_tile_sort2(int cluster, int lanes, const Segment* segs, uint32_t sbeg, uint32_t send,
+                              uint32_t supertiles, int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
                               uint64_t wait_limit, cudaStream_t st) {
   if (supertiles == 0) return cudaSuccess;
-  switch (cluster) {
-    case 1: return tile_sort2_cl<1>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 2: return tile_sort2_cl<2>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 4: return tile_sort2_cl<4>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 8: return tile_sort2_cl<8>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+  switch (lanes) {
+    case 2: return launch_tile_sort2_g2(cluster, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 4: return launch_tile_sort2_g4(cluster, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 8: return launch_tile_sort2_g8(cluster, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -75,3 +75,48 @@ def test_config_default(libpath):
 
     cfg = bs.bsort_config_default()
     assert cfg.l_cap == 255 and cfg.want_offsets == 1 and cfg.device == -1 and cfg.wait_limit == 0
+
+
+def test_config_default_has_builtin_tuning(libpath):
+    import paper_1407_6603_gb300 as bs
+
+    assert bs.bsort_config_default().tune_table is None
+
+
+@pytest.mark.parametrize("table", [
+    "k4_lanes=3,4,4,4",        # lanes must be 2, 4 or 8
+    "k4_lanes=4,4,4",          # one value per cluster size
+    "k4_lanes=4,4,4,4,4",
+    "piped_min=0",             # at least one tile per CTA
+    "piped_min=-1",
+    "piped_min=x",
+    "bogus=1",                 # unknown key
+    "k4_lanes",                # no value
+    "k4_lanes=4,,4,4",
+])
+def test_bad_tune_table_is_rejected_before_any_device_call(libpath, table):
+    import paper_1407_6603_gb300 as bs
+
+    cfg = bs.bsort_config_default()
+    buf = table.encode()
+    cfg.tune_table = buf
+    with pytest.raises(bs.BsortError) as e:
+        bs.bsort_create(cfg)
+    assert e.value.status == bs.BSORT_E_INVAL
+
+
+@pytest.mark.parametrize("table", ["", "# only a comment\n", "k4_lanes=2,4,8,8; piped_min=3",
+                                   "k4_lanes=8,8,8,8\npiped_min=1000000  # forced off\n"])
+def test_good_tune_table_passes_the_parser(libpath, table):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import paper_1407_6603_gb300 as bs
+
+    cfg = bs.bsort_config_default()
+    buf = table.encode()
+    cfg.tune_table = buf
+    with pytest.raises(bs.BsortError) as e:  # parsed, then fails for want of a device
+        bs.bsort_create(cfg)
+    assert e.value.status == bs.BSORT_E_CUDA

@@ -23,11 +23,15 @@ def test_profile_and_timeline(bsort_gpu, synth_mod):
     assert sum(1 for r in tl if r[0] != "host_gap") == launches
     assert sum(1 for r in tl if r[0] == "host_gap") == 1
     assert tl[0][0] == "tokenize" and tl[0][1] == 0.0
-    for name, s, e, b, st in tl:
+    for name, s, e, b, st, var in tl:
         assert 0.0 <= s <= e, name
         assert 0 <= st <= 4
+        if name == "tile_sort":
+            assert var in (0, 1, 2, 4, 8)  # CTAs per cluster, 0 for the warp sort
+        if name in ("merge_pass", "merge_cut"):
+            assert var in (1, 2, 4, 8, 16, 32)  # key width
     for name in {r[0] for r in tl}:
-        ms = sum(e - s for n, s, e, _, _ in tl if n == name)
+        ms = sum(e - s for n, s, e, *_ in tl if n == name)
         assert stats[name][1] == pytest.approx(ms, rel=1e-3, abs=1e-3), name
         assert stats[name][0] == sum(1 for r in tl if r[0] == name)
     # the tokenizer runs first, every sort launch starts after the round trip
