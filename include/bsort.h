@@ -119,7 +119,11 @@ const char* bsort_last_error(const bsort_ctx* ctx);
 /*
  * Sorts one document held in host memory (bytes may be NULL when len == 0).
  * Synchronous: on return, *out holds HOST pointers into buffers owned by the
- * context.  Errors: BSORT_E_INVAL, BSORT_E_TOO_LARGE (len >= 2^32),
+ * context.  When the document lies in page-locked memory (cudaHostAlloc,
+ * cudaHostRegister; its first and last bytes are checked, so a buffer must not
+ * straddle page-locked and pageable memory) the copy engine reads it in
+ * place; otherwise it is first copied into the context's page-locked staging
+ * buffer.  Errors: BSORT_E_INVAL, BSORT_E_TOO_LARGE (len >= 2^32),
  * BSORT_E_WORD_TOO_LONG, BSORT_E_NOMEM, BSORT_E_CUDA, BSORT_E_TIMEOUT.
  */
 bsort_status bsort_text(bsort_ctx* ctx, const uint8_t* bytes, size_t len, bsort_result* out);
@@ -145,7 +149,10 @@ bsort_status bsort_text_device(bsort_ctx* ctx, const uint8_t* d_bytes, size_t le
  * outs[i] receives document i's result (HOST pointers), with outs[i].status
  * set per document; the call returns BSORT_OK when every document succeeded,
  * otherwise the first failing document's status.  Each document's result is
- * identical to what bsort_text returns for it alone.
+ * identical to what bsort_text returns for it alone.  Documents that lie back
+ * to back in host memory (docs[i + 1] == docs[i] + lens[i], empty ones
+ * anywhere) move to the device as one region, read in place when it is
+ * page-locked (as in bsort_text); others are gathered into the staging buffer.
  */
 bsort_status bsort_batch(bsort_ctx* ctx, const uint8_t* const* docs, const size_t* lens, size_t n,
                          bsort_result* outs);

@@ -301,20 +301,64 @@ class Result:
         return [s[off[i]:off[i + 1]] for i in range(len(off) - 1)]
 
 
-def _host_result(r: bsort_result, want_offsets: bool) -> Result:
+def _host_array(ptr, ctype, count, dtype, copy: bool) -> np.ndarray:
+    if count == 0 or not ptr:  # empty, or a failed document (zeroed result)
+        return np.zeros(0, dtype=dtype)
+    v = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctype)), shape=(count,))
+    return v.copy() if copy else v
+
+
+class ViewResult:
+    """A host result whose arrays are views of the context's page-locked
+    buffers, made on first access; valid until the next call on the context
+    (the C ABI's own lifetime).  Same fields as Result."""
+
+    __slots__ = ("_r", "_want_offsets", "max_len", "n_words", "stream_bytes", "status", "_cache")
+
+    def __init__(self, r: bsort_result, want_offsets: bool):
+        self._r = r
+        self._want_offsets = want_offsets
+        self.max_len = int(r.max_len)
+        self.n_words = int(r.n_words)
+        self.stream_bytes = int(r.stream_bytes)
+        self.status = int(r.status)
+        self._cache = {}
+
+    @property
+    def counts(self) -> np.ndarray:
+        if "c" not in self._cache:
+            self._cache["c"] = _host_array(self._r.counts, ctypes.c_uint64, self.max_len + 1, np.uint64, False)
+        return self._cache["c"]
+
+    @property
+    def offsets(self) -> np.ndarray | None:
+        if not self._want_offsets:
+            return None
+        if "o" not in self._cache:
+            self._cache["o"] = _host_array(self._r.offsets, ctypes.c_uint32, self.n_words + 1, np.uint32, False)
+        return self._cache["o"]
+
+    @property
+    def stream(self) -> np.ndarray:
+        if "s" not in self._cache:
+            self._cache["s"] = _host_array(self._r.stream, ctypes.c_uint8, self.stream_bytes, np.uint8, False)
+        return self._cache["s"]
+
+    words = Result.words
+
+
+def _host_result(r: bsort_result, want_offsets: bool, copy: bool = True):
+    """copy=False gives a ViewResult over the context's page-locked result
+    buffers, valid until the next call on the context."""
+    if not copy:
+        return ViewResult(r, want_offsets)
     n = int(r.n_words)
     ml = int(r.max_len)
-
-    def arr(ptr, ctype, count, dtype):
-        if count == 0 or not ptr:  # empty, or a failed document (zeroed result)
-            return np.zeros(0, dtype=dtype)
-        return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctype)), shape=(count,)).copy()
-
     return Result(
         max_len=ml, n_words=n, stream_bytes=int(r.stream_bytes),
-        counts=arr(r.counts, ctypes.c_uint64, ml + 1, np.uint64),
-        offsets=arr(r.offsets, ctypes.c_uint32, n + 1, np.uint32) if want_offsets else None,
-        stream=arr(r.stream, ctypes.c_uint8, int(r.stream_bytes), np.uint8),
+        counts=_host_array(r.counts, ctypes.c_uint64, ml + 1, np.uint64, True),
+        offsets=_host_array(r.offsets, ctypes.c_uint32, n + 1, np.uint32, True) if want_offsets else None,
+        stream=_host_array(r.stream, ctypes.c_uint8, int(r.stream_bytes), np.uint8, True),
         status=int(r.status),
     )
 
@@ -325,6 +369,27 @@ class _DevView:
     def __init__(self, ptr: int, count: int, typestr: str):
         self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr or 0, False),
                                          "version": 3, "strides": None, "stream": None}
+
+
+def pinned_empty(nbytes: int) -> np.ndarray:
+    """A page-locked host uint8 array (torch's pinned allocator), which
+    bsort_text / bsort_batch read in place."""
+    import torch
+
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, pin_memory=True).numpy()[:nbytes]
+
+
+def pack_host(docs: list, pinned: bool = True) -> list[np.ndarray]:
+    """Copies documents back to back into one (page-locked) host buffer and
+    returns views of it, the layout bsort_batch moves in one copy."""
+    lens = [len(d) for d in docs]
+    buf = pinned_empty(sum(lens)) if pinned else np.empty(sum(lens), np.uint8)
+    out, pos = [], 0
+    for d, n in zip(docs, lens):
+        buf[pos:pos + n] = _as_u8(d)
+        out.append(buf[pos:pos + n])
+        pos += n
+    return out
 
 
 class Context:
@@ -363,9 +428,10 @@ class Context:
     def handle(self):
         return self._h
 
-    def text(self, data) -> Result:
-        """Host bytes in, host result out (synchronous)."""
-        return _host_result(bsort_text(self._h, data), self.want_offsets)
+    def text(self, data, copy: bool = True) -> Result:
+        """Host bytes in, host result out (synchronous).  copy=False returns
+        views of the context's result buffers, valid until its next call."""
+        return _host_result(bsort_text(self._h, data), self.want_offsets, copy)
 
     def text_device_raw(self, tensor, stream=None) -> bsort_result:
         """Device tensor in (uint8, contiguous); device pointers out, valid once
@@ -431,9 +497,11 @@ class Context:
                             "stream": view(r.stream, int(r.stream_bytes), "|u1", torch.uint8)})
         return st, out
 
-    def batch(self, docs: list) -> tuple[int, list[Result]]:
+    def batch(self, docs: list, copy: bool = True) -> tuple[int, list[Result]]:
+        """Many host documents in one pass.  Views of one buffer, back to back
+        (as pack_host() makes them), move as one copy; copy=False as in text()."""
         st, rs = bsort_batch(self._h, docs)
-        return st, [_host_result(r, self.want_offsets) for r in rs]
+        return st, [_host_result(r, self.want_offsets, copy) for r in rs]
 
     def last_error(self) -> str:
         return bsort_last_error(self._h)

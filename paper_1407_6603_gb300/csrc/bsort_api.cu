@@ -307,6 +307,22 @@ struct Trace {
     CK(tr_.done(call), what);                           \
   } while (0)
 
+// Whether [p, p + len) is page-locked host memory that a copy engine can read
+// directly: its first and last bytes both are (a buffer is taken to be one
+// allocation; see bsort_text).
+bool host_pinned(const void* p, size_t len) {
+  if (!p || len == 0) return false;
+  for (const void* q : {p, static_cast<const void*>(static_cast<const uint8_t*>(p) + len - 1)}) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, q) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (a.type != cudaMemoryTypeHost) return false;
+  }
+  return true;
+}
+
 // Waits for an event by polling it (the call's one mid-path wait is short,
 // and a poll answers sooner than a blocking wait); after 200 us it blocks.
 cudaError_t spin_wait(cudaEvent_t ev) {
@@ -871,11 +887,15 @@ bsort_status bsort_text(bsort_ctx* c, const uint8_t* bytes, size_t len, bsort_re
   Busy busy(c);
   if ((uint64_t)len >= (1ull << 32)) return fail(c, BSORT_E_TOO_LARGE, "document of 2^32 bytes or more");
   cudaStream_t st = c->own_stream;
-  GROW_HOST(c->h_in, len + 16, "input staging");
   GROW(c->in, len + 16, "input");
   if (len) {
-    std::memcpy(c->h_in.p, bytes, len);
-    CK(cudaMemcpyAsync(c->in.p, c->h_in.p, len, cudaMemcpyHostToDevice, st), "copy input");
+    if (host_pinned(bytes, len)) {  // page-locked: the copy engine reads it directly
+      CK(cudaMemcpyAsync(c->in.p, bytes, len, cudaMemcpyHostToDevice, st), "copy input");
+    } else {
+      GROW_HOST(c->h_in, len + 16, "input staging");
+      std::memcpy(c->h_in.p, bytes, len);
+      CK(cudaMemcpyAsync(c->in.p, c->h_in.p, len, cudaMemcpyHostToDevice, st), "copy input");
+    }
   }
   const uint64_t off = 0, l = len;
   s = run_path(c, dptr<uint8_t>(c->in), &off, &l, 1, st);
@@ -948,18 +968,46 @@ bsort_status bsort_batch(bsort_ctx* c, const uint8_t* const* docs, const size_t*
     uint64_t bytes = 0;
     while (g1 < n && (g1 == g0 || bytes + align_up(lens[g1], 16) <= kGroupBytes)) bytes += align_up(lens[g1++], 16);
     const uint32_t nd = (uint32_t)(g1 - g0);
-    GROW_HOST(c->h_in, bytes + 16, "input staging");
-    GROW(c->in, bytes + 16, "input");
     offs.resize(nd);
     ls.resize(nd);
-    uint64_t pos = 0;
-    for (uint32_t i = 0; i < nd; ++i) {
-      offs[i] = pos;
-      ls[i] = lens[g0 + i];
-      if (ls[i]) std::memcpy(hptr<uint8_t>(c->h_in, pos), docs[g0 + i], ls[i]);
-      pos += align_up(ls[i], 16);
+    // Documents that lie back to back in host memory (the empty ones
+    // anywhere) move as one region: one copy, read directly when it is
+    // page-locked.  Others are gathered into the staging buffer.
+    const uint8_t* region = nullptr;
+    const uint8_t* region_end = nullptr;
+    bool contiguous = true;
+    for (size_t i = g0; i < g1 && contiguous; ++i) {
+      if (!lens[i]) continue;
+      if (!region) region = docs[i];
+      else if (docs[i] != region_end) contiguous = false;
+      region_end = docs[i] + lens[i];
     }
-    if (bytes) CK(cudaMemcpyAsync(c->in.p, c->h_in.p, bytes, cudaMemcpyHostToDevice, st), "copy input");
+    if (contiguous && region) {
+      const size_t rb = (size_t)(region_end - region);
+      GROW(c->in, rb + 16, "input");
+      for (uint32_t i = 0; i < nd; ++i) {
+        ls[i] = lens[g0 + i];
+        offs[i] = ls[i] ? (uint64_t)(docs[g0 + i] - region) : 0;
+      }
+      if (host_pinned(region, rb)) {
+        CK(cudaMemcpyAsync(c->in.p, region, rb, cudaMemcpyHostToDevice, st), "copy input");
+      } else {
+        GROW_HOST(c->h_in, rb + 16, "input staging");
+        std::memcpy(c->h_in.p, region, rb);
+        CK(cudaMemcpyAsync(c->in.p, c->h_in.p, rb, cudaMemcpyHostToDevice, st), "copy input");
+      }
+    } else {
+      GROW_HOST(c->h_in, bytes + 16, "input staging");
+      GROW(c->in, bytes + 16, "input");
+      uint64_t pos = 0;
+      for (uint32_t i = 0; i < nd; ++i) {
+        offs[i] = pos;
+        ls[i] = lens[g0 + i];
+        if (ls[i]) std::memcpy(hptr<uint8_t>(c->h_in, pos), docs[g0 + i], ls[i]);
+        pos += align_up(ls[i], 16);
+      }
+      if (bytes) CK(cudaMemcpyAsync(c->in.p, c->h_in.p, bytes, cudaMemcpyHostToDevice, st), "copy input");
+    }
     s = run_path(c, dptr<uint8_t>(c->in), offs.data(), ls.data(), nd, st);
     if (s != BSORT_OK) return s;
     s = read_back(c, st, off_base, stream_base, (size_t)g0 * kHist);

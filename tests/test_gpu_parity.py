@@ -217,6 +217,27 @@ def test_batch_equals_single(ctx, oracle_mod, synth_mod):
         assert_same(ctx.text(d), exp, f"doc {i} alone")
 
 
+def test_page_locked_and_packed_host_inputs(ctx, bsort_gpu, oracle_mod, synth_mod):
+    """Host inputs read in place from page-locked memory, packed documents
+    moved as one region (page-locked or not), and scattered ones gathered:
+    every form gives the oracle's result."""
+    doc = synth_mod.plain("plain_190k")
+    pinned = bsort_gpu.pinned_empty(doc.size)
+    pinned[:] = doc
+    exp = oracle_mod.stable(doc, nthreads=8)
+    assert_same(ctx.text(pinned), exp)
+    assert_same(ctx.text(pinned, copy=False), exp)
+    docs = [synth_mod.batch_doc(*s) for s in synth_mod.batch_shapes(12)]
+    docs.insert(3, np.zeros(0, np.uint8))
+    docs.insert(7, np.frombuffer(b"!! ??", np.uint8))
+    exps = [oracle_mod.stable(d, nthreads=8) for d in docs]
+    for form in (bsort_gpu.pack_host(docs), bsort_gpu.pack_host(docs, pinned=False), docs):
+        st, rs = ctx.batch(form)
+        assert st == 0
+        for i, (r, e) in enumerate(zip(rs, exps)):
+            assert_same(r, e, f"doc {i}")
+
+
 def test_batch_reports_failing_document(bsort_gpu, oracle_mod):
     docs = [b"fine words here", b"x" * 30, b"also fine"]
     with bsort_gpu.Context(l_cap=20) as c:
