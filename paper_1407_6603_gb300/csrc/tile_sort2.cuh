@@ -132,10 +132,20 @@ __device__ void cta_sort(uint64_t* buf) {
   oets_lanes<W, KPT, G>(k);
 #pragma unroll 1
   for (uint32_t R = G * KPT; R < T; R <<= 1) {
-    __syncthreads();
+    // While both runs of every pair lie in one warp's keys (2R <= 32 KPT),
+    // only that warp reads them: a warp barrier suffices (but the first
+    // store follows the striped load, which read every warp's keys).
+    const bool local = 2 * R <= 32u * KPT && R != (uint32_t)G * KPT;
+    if (local)
+      __syncwarp();
+    else
+      __syncthreads();
 #pragma unroll
     for (int i = 0; i < KPT; ++i) kstore<W>(pkey<W>(buf, t * KPT + i), k[i]);
-    __syncthreads();
+    if (2 * R <= 32u * KPT)
+      __syncwarp();
+    else
+      __syncthreads();
     const uint32_t pos = t * KPT;
     const uint32_t base = pos & ~(2 * R - 1);
     const uint32_t d = pos - base;
@@ -151,15 +161,21 @@ __device__ void cta_sort(uint64_t* buf) {
 }
 
 // Merges the CL sorted tiles of a cluster (CTA q holds supertile positions
-// [q*T, (q+1)*T) in its buf0, padded layout) into one sorted run.
+// [q*T, (q+1)*T) in its buf0, padded layout) into one sorted run, and returns
+// the buffer (buf0 or buf2) that holds this CTA's tile of it.  The levels
+// alternate between buf0 and buf2, so one cluster barrier per level suffices:
+// a level overwrites the buffer its peers read two levels back.  buf1 takes
+// the slices this CTA merges.
 template <int W, int CL>
-__device__ void cluster_merge(uint64_t* buf0, uint64_t* buf1, uint32_t r) {
+__device__ uint64_t* cluster_merge(uint64_t* buf0, uint64_t* buf1, uint64_t* buf2, uint32_t r) {
   constexpr int KPT = kpt2<W>();
   constexpr uint32_t T = kT2Threads * KPT;
   cg::cluster_group cluster = cg::this_cluster();
   const int t = threadIdx.x;
+  uint64_t* cur = buf0;  // this level's input tile (every CTA uses the same buffer)
+  uint64_t* nxt = buf2;
   auto key_at = [&](uint32_t pos) {  // key `pos` of the supertile, in its owner's shared memory
-    return kload<W>(cluster.map_shared_rank(pkey<W>(buf0, pos % T), pos / T));
+    return kload<W>(cluster.map_shared_rank(pkey<W>(cur, pos % T), pos / T));
   };
   cluster.sync();
 #pragma unroll 1
@@ -176,9 +192,9 @@ __device__ void cluster_merge(uint64_t* buf0, uint64_t* buf1, uint32_t r) {
     for (uint32_t e = t; e < T * W; e += kT2Threads) {
       const uint32_t kk = e / W, j = e % W;
       const uint32_t src = kk < na ? pb + a0 + kk : pb + R + b0 + (kk - na);
-      buf1[padw(e)] = cluster.map_shared_rank(pkey<W>(buf0, src % T), src / T)[j];
+      buf1[padw(e)] = cluster.map_shared_rank(pkey<W>(cur, src % T), src / T)[j];
     }
-    cluster.sync();  // every peer has its slices: buf0 may be overwritten
+    __syncthreads();  // the slices are in
     Key<W> k[KPT];
     const uint32_t pos = t * KPT;
     auto sA = [&](uint32_t i) { return kload<W>(pkey<W>(buf1, i)); };
@@ -186,15 +202,19 @@ __device__ void cluster_merge(uint64_t* buf0, uint64_t* buf1, uint32_t r) {
     const uint32_t a = mp_split_f<W>(sA, na, sB, nb, pos);
     merge_run_buf<W, KPT>(buf1, 0, na, na, nb, a, pos - a, k);
 #pragma unroll
-    for (int i = 0; i < KPT; ++i) kstore<W>(pkey<W>(buf0, pos + i), k[i]);
+    for (int i = 0; i < KPT; ++i) kstore<W>(pkey<W>(nxt, pos + i), k[i]);
     cluster.sync();  // this level's output is visible to the next level's readers
+    uint64_t* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
   }
+  return cur;
 }
 
 template <int W, int CL, int G>
 __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint64_t* keys, uint64_t* buf0,
-                               uint64_t* buf1, uint64_t* bar, uint32_t& phase, const EmitOut& eo, Meta* meta,
-                               uint64_t wait_limit) {
+                               uint64_t* buf1, uint64_t* buf2, uint64_t* bar, uint32_t& phase, const EmitOut& eo,
+                               Meta* meta, uint64_t wait_limit) {
   constexpr int KPT = kpt2<W>();
   constexpr uint32_t T = kT2Threads * KPT;
   constexpr uint32_t TW = T * W;
@@ -223,11 +243,12 @@ __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint6
     __syncthreads();
   }
   cta_sort<W, G>(buf0);
-  if constexpr (CL > 1) cluster_merge<W, CL>(buf0, buf1, r);
+  const uint64_t* res = buf0;
+  if constexpr (CL > 1) res = cluster_merge<W, CL>(buf0, buf1, buf2, r);
   if (sg.passes == 0) {  // the bucket is sorted: its words go straight out
-    emit_tile<kT2Threads>(sg, (uint32_t)j0, cnt, [&](uint32_t j, uint32_t q) { return buf0[padw(j * W + q)]; }, eo);
+    emit_tile<kT2Threads>(sg, (uint32_t)j0, cnt, [&](uint32_t j, uint32_t q) { return res[padw(j * W + q)]; }, eo);
   } else {  // a run of CL tiles for K5
-    for (uint32_t e = t; e < cnt * W; e += kT2Threads) g[e] = buf0[padw(e)];
+    for (uint32_t e = t; e < cnt * W; e += kT2Threads) g[e] = res[padw(e)];
   }
   __syncthreads();
 }
@@ -240,6 +261,7 @@ __global__ void __launch_bounds__(kT2Threads, BSORT_K4_MIN_CTAS) k_tile_sort2(co
   extern __shared__ __align__(128) uint64_t sm[];
   uint64_t* buf0 = sm;
   uint64_t* buf1 = sm + buf_words;
+  uint64_t* buf2 = sm + 2 * buf_words;
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t s_seg;
   __shared__ uint32_t s_first[kSegCache];
@@ -260,10 +282,10 @@ __global__ void __launch_bounds__(kT2Threads, BSORT_K4_MIN_CTAS) k_tile_sort2(co
     const Segment sg = segs[s_seg];
     __syncthreads();
     switch (width_of_len(sg.L)) {
-      case 1: sort_supertile<1, CL, G>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
-      case 2: sort_supertile<2, CL, G>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
-      case 4: sort_supertile<4, CL, G>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
-      default: sort_supertile<8, CL, G>(sg, st, r, keys, buf0, buf1, &bar, phase, eo, meta, wait_limit); break;
+      case 1: sort_supertile<1, CL, G>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
+      case 2: sort_supertile<2, CL, G>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
+      case 4: sort_supertile<4, CL, G>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
+      default: sort_supertile<8, CL, G>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
     }
   }
 }
@@ -274,7 +296,7 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
                           cudaStream_t st) {
   (void)max_width;
   const uint32_t buf_words = padded_words(2048u);
-  const size_t smem = (size_t)(CL > 1 ? 2 : 1) * buf_words * 8;
+  const size_t smem = (size_t)(CL > 1 ? 3 : 1) * buf_words * 8;
   static int attr_done[64];
   static int clusters_cached[64];
   cudaError_t e = once_per_device(attr_done, [&] {
