@@ -65,6 +65,7 @@ def parse_args(argv=None):
     p.add_argument("--batch-docs", type=int, default=None, help="use only the first D documents of batch_4096")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--tune", default=None, help="tune table text (bsort_config.tune_table); default: built-in")
     p.add_argument("--no-forms", action="store_true", help="skip the batched-form summary of the default run")
     p.add_argument("--prefix-bytes", type=int, default=None,
                    help="use only the first B bytes of the workload (profiling captures on smaller cases)")
@@ -359,7 +360,7 @@ def measure(args, quiet: bool = False):
     d_in = torch.from_numpy(host).to(dev)
     flush = None if batch else torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(dev)
-    ctx = bs.Context(profile=True, device=local_rank)
+    ctx = bs.Context(profile=True, device=local_rank, tune_table=args.tune)
     sampler = ClockSampler(local_rank).start()
 
     def step():

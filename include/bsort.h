@@ -69,6 +69,12 @@ typedef struct {
                                                 of 1, 2, 4 and 8 CTAs; each 2, 4 or 8
                               piped_min=k       merge passes with at least k tiles per resident
                                                 CTA use the pipelined merge (1..1000000)
+                              k4_runs=c         buckets too large for one cluster of 8 tiles
+                                                are sorted by K4 into runs of c tiles (clusters
+                                                of c CTAs: 1, 2, 4 or 8), which the merge
+                                                passes take up, when their merges are large
+                                                enough to be pipelined (see piped_min); else
+                                                into runs of 8 tiles
                               k4_streams=0|1    1 (default): the tile sorts of the smaller
                                                 classes run beside the largest on side
                                                 streams; 0: one after another on the call's

@@ -5,8 +5,10 @@ The tile sort (K4) handles a bucket with a thread-block cluster of 1, 2, 4 or
 tunes the odd-even/merge cutoff: how many lanes (2, 4 or 8) run odd-even
 transposition together before merge path takes over, i.e. runs of lanes x
 keys-per-thread keys leave the transposition stage.  For the merge passes (K5)
-it tunes the threshold, in tiles per resident CTA, above which a pass is
-pipelined (cut kernel, then double-buffered merge).
+it tunes the run length the tile sort leaves for them (clusters of 1, 2, 4 or 8
+CTAs for buckets larger than one cluster of 8 tiles) and the threshold, in
+tiles per resident CTA, above which a pass is pipelined (cut kernel, then
+double-buffered merge).
 
 Every candidate runs on the same seeded synthetic documents (the plain
 190 KB and 1.38 MB shapes, a 32 MiB slice of the 256 MiB generator and 256
@@ -32,6 +34,7 @@ import time
 CLUSTERS = (1, 2, 4, 8)
 LANES = (2, 4, 8)
 PIPED = (1, 2, 4, 8)
+RUNS = (8, 4, 2, 1)
 DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_table.txt")
 
 
@@ -106,10 +109,18 @@ def tune(reps: int = 5, log=print) -> str:
         span_of[lanes] = span / reps
         log(f"  lanes {lanes}: {span_of[lanes]:9.3f} ms per round (whole calls)")
     lanes = min(span_of, key=lambda k: (span_of[k], k != best))
-    # 3. the merge threshold
+    # 3. the runs the tile sort leaves for the merge passes (clusters of
+    #    k4_runs CTAs) for buckets larger than one cluster of 8 tiles
+    runs_of = {}
+    for r in RUNS:
+        _, span = _time(f"k4_lanes={lanes} k4_runs={r}", sets, reps)
+        runs_of[r] = span / reps
+        log(f"  runs of {r} tiles before the merge passes: {runs_of[r]:9.3f} ms per round (whole calls)")
+    runs = min(RUNS, key=lambda r: (runs_of[r], -r))
+    # 4. the merge threshold
     piped_of = {}
     for p in PIPED:
-        _, span = _time(f"k4_lanes={lanes} piped_min={p}", sets, reps)
+        _, span = _time(f"k4_lanes={lanes} k4_runs={runs} piped_min={p}", sets, reps)
         piped_of[p] = span / reps
         log(f"  merge threshold {p} tiles per CTA: {piped_of[p]:9.3f} ms per round (whole calls)")
     piped = min(PIPED, key=lambda p: (piped_of[p], p))
@@ -120,9 +131,12 @@ def tune(reps: int = 5, log=print) -> str:
     for cl in CLUSTERS:
         lines.append("#   clusters of %d: " % cl + "  ".join(f"{g} lanes {class_ms[(cl, g)]:.3f}" for g in LANES))
     lines.append("# whole calls, ms per round: " + "  ".join(f"lanes {k}: {v:.3f}" for k, v in span_of.items()))
+    lines.append("# runs before the merge passes, whole calls, ms per round: "
+                 + "  ".join(f"{r}: {v:.3f}" for r, v in runs_of.items()))
     lines.append("# merge threshold, whole calls, ms per round: "
                  + "  ".join(f"{p}: {v:.3f}" for p, v in piped_of.items()))
     lines.append(f"k4_lanes={lanes}")
+    lines.append(f"k4_runs={runs}")
     lines.append(f"piped_min={piped}")
     return "\n".join(lines) + "\n"
 

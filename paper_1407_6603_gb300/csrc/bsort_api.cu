@@ -49,9 +49,10 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Tuning chosen per bucket-size class (see bsort_config.tune_table).  The
 // built-in values are what the autotuner (autotune.py) picked on a GB300.
 struct Tune {
-  int k4_lanes[4] = {2, 2, 2, 2};  // clusters of 1, 2, 4, 8 CTAs
-  uint32_t piped_min = 4;
+  int k4_lanes[4] = {2, 2, 4, 2};  // clusters of 1, 2, 4, 8 CTAs
+  uint32_t piped_min = 1;
   int k4_streams = 1;  // 1: the tile sorts of the smaller classes run on side streams
+  int k4_runs = 1;     // cluster size (runs of that many tiles) for buckets that need pipelined merge passes
 };
 
 // Parses a tune table; false on an unknown key or a bad value.
@@ -92,6 +93,9 @@ bool parse_tune(const char* text, Tune& t) {
         if (nums[q] != 2 && nums[q] != 4 && nums[q] != 8) return false;
         t.k4_lanes[q] = (int)nums[q];
       }
+    } else if (key == "k4_runs") {
+      if (nums.size() != 1 || (nums[0] != 1 && nums[0] != 2 && nums[0] != 4 && nums[0] != 8)) return false;
+      t.k4_runs = (int)nums[0];
     } else if (key == "k4_streams") {
       if (nums.size() != 1 || nums[0] > 1) return false;
       t.k4_streams = (int)nums[0];
@@ -431,6 +435,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   std::vector<uint8_t>& group = c->groupv;
   group.clear();
   uint32_t group_n[kGroups] = {};
+  uint64_t big_tiles = 0;  // merge tiles of the buckets that need merge passes
   for (uint32_t d = 0; d < ndocs; ++d) {
     if (c->doc_status[d] != BSORT_OK) continue;
     const uint32_t* h = h_hist + (size_t)d * kHist;
@@ -464,10 +469,9 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
           gi = 6;
         } else if (n <= (uint32_t)kSuperCluster * T) {
           gi = 5;
-        } else {
-          sg.run0 = kSuperCluster * T;
-          sg.passes = merge_passes(n, sg.run0);
+        } else {  // needs merge passes: runs and passes are set below
           gi = (uint8_t)class_of_width(W);
+          big_tiles += (n + merge2_keys(W) - 1) / merge2_keys(W);
         }
         sg.final_buf = sg.passes & 1u;
         cand.push_back(sg);
@@ -479,26 +483,61 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     }
   }
   const uint32_t nseg = (uint32_t)cand.size();
-  // stable counting sort of the candidates by group
-  uint32_t gbeg[kGroups + 1] = {};
-  for (int g = 0; g < kGroups; ++g) gbeg[g + 1] = gbeg[g] + group_n[g];
+  // The buckets that need merge passes leave K4 as runs of k4_runs tiles
+  // when their merges are large enough to be pipelined (the passes then run
+  // at HBM speed, cheaper than more cluster levels), else as runs of 8 tiles
+  // (fewer passes, fewer launches).
+  const uint32_t piped_grid = (uint32_t)(c->sm_count * merge_piped_ctas_per_sm());
+  const int runs = big_tiles >= (uint64_t)c->tune.piped_min * piped_grid ? c->tune.k4_runs : kSuperCluster;
+  for (uint32_t i = 0; i < nseg; ++i)
+    if (group[i] < 4) {
+      Segment& sg = cand[i];
+      sg.run0 = (uint32_t)runs * tile2_keys(width_of_len(sg.L));
+      sg.passes = merge_passes(sg.n, sg.run0);
+      sg.final_buf = sg.passes & 1u;
+    }
+  // Table order: the groups that K4 finishes (clusters of 8, 4, 2, 1), with
+  // the groups that need merge passes (0..3, and the unused 4) placed just
+  // before the one whose cluster size makes their runs, so that every K4
+  // launch and every width's merge chain covers one contiguous range; then
+  // the warp sort and the wide keys.
+  int order[kGroups], n_ord = 0;
+  for (int gc : {5, 6, 7, 8}) {
+    if (kSuperCluster >> (gc - 5) == runs)
+      for (int g = 0; g < 5; ++g) order[n_ord++] = g;
+    order[n_ord++] = gc;
+  }
+  for (int g : {9, 10, 11}) order[n_ord++] = g;
+  int pos_of[kGroups];
+  for (int q = 0; q < kGroups; ++q) pos_of[order[q]] = q;
+  // stable counting sort of the candidates by table position
+  uint32_t pbeg[kGroups + 1] = {};
+  for (int q = 0; q < kGroups; ++q) pbeg[q + 1] = pbeg[q] + group_n[order[q]];
+  auto gb = [&](int g) { return pbeg[pos_of[g]]; };      // first segment of group g
+  auto ge = [&](int g) { return pbeg[pos_of[g] + 1]; };  // one past its last
   std::vector<Segment>& segs = c->segv2;
   segs.resize(nseg);
   {
     uint32_t at[kGroups];
-    for (int g = 0; g < kGroups; ++g) at[g] = gbeg[g];
-    for (uint32_t i = 0; i < nseg; ++i) segs[at[group[i]]++] = cand[i];
+    for (int q = 0; q < kGroups; ++q) at[q] = pbeg[q];
+    for (uint32_t i = 0; i < nseg; ++i) segs[at[pos_of[group[i]]]++] = cand[i];
   }
-  // K4 launches: cluster size and the groups each covers
+  // K4 launches: cluster size, its own group, and the table range it covers
+  // (the merge-pass groups too, for the cluster size that makes their runs)
   struct K4Launch {
     int cluster;
-    int g0, g1;  // groups [g0, g1)
+    int gc;
+    uint32_t sbeg = 0, send = 0;
     uint32_t supertiles = 0;
     int max_w = 1;
     double key_bytes = 0;
     double levels = 0;  // key-levels: each key times log2 of the sorted run it ends in
   };
-  K4Launch k4[4] = {{8, 0, 6}, {4, 6, 7}, {2, 7, 8}, {1, 8, 9}};
+  K4Launch k4[4] = {{8, 5}, {4, 6}, {2, 7}, {1, 8}};
+  for (K4Launch& l : k4) {
+    l.sbeg = l.cluster == runs ? gb(0) : gb(l.gc);
+    l.send = ge(l.gc);
+  }
   // bytes of a bucket's output: its letters and, if asked for, its offsets
   const uint64_t off_bytes = c->cfg.want_offsets ? 4 : 0;
   auto out_bytes = [&](const Segment& sg) { return (double)sg.n * (sg.L + off_bytes); };
@@ -509,8 +548,9 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   for (uint32_t i = 0; i < nseg; ++i) {
     Segment& sg = segs[i];
     const int W = width_of_len(sg.L);
-    int gi = 0;
-    while (i >= gbeg[gi + 1]) ++gi;
+    int q = 0;
+    while (i >= pbeg[q + 1]) ++q;
+    const int gi = order[q];
     sg.key_off = key_words;
     key_words += align_up((size_t)sg.n * W, 16);
     kb[gi] += 8ull * W * sg.n;
@@ -525,7 +565,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       mpasses[gi] = std::max(mpasses[gi], sg.passes);
     }
     for (K4Launch& l : k4)
-      if (gi >= l.g0 && gi < l.g1) {
+      if (i >= l.sbeg && i < l.send) {
         const uint32_t super = (uint32_t)l.cluster * tile2_keys(W);
         sg.stile0 = l.supertiles;
         l.supertiles += (sg.n + super - 1) / super;
@@ -595,7 +635,10 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   // before the merge passes
   // (with k4_streams=0 in the tune table every launch stays on the call's
   // stream, one after another: how the autotuner times each class alone)
-  const bool side = gbeg[10] > gbeg[6] && c->tune.k4_streams;
+  bool small_work = ge(9) > gb(9);  // the warp sort, or a K4 launch besides the clusters of 8
+  for (const K4Launch& l : k4)
+    if (l.cluster != kSuperCluster && l.supertiles) small_work = true;
+  const bool side = small_work && c->tune.k4_streams;
   if (side) CK(cudaEventRecord(c->fork_ev, st), "fork");
   int used = 0;
   cudaStream_t joined[bsort_ctx::kSide];
@@ -615,17 +658,17 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     Trace tr_(c, sx, kTileSort, l.key_bytes, l.levels);
     tr_.variant = (uint32_t)l.cluster;
     const int lanes = c->tune.k4_lanes[l.cluster == 1 ? 0 : l.cluster == 2 ? 1 : l.cluster == 4 ? 2 : 3];
-    CK(tr_.done(launch_tile_sort2(l.cluster, lanes, d_segs, gbeg[l.g0], gbeg[l.g1], l.supertiles, c->sm_count, l.max_w, kA,
+    CK(tr_.done(launch_tile_sort2(l.cluster, lanes, d_segs, l.sbeg, l.send, l.supertiles, c->sm_count, l.max_w, kA,
                                   eo, d_sticky, c->cfg.wait_limit, sx)),
        "K4 tile_sort");
   }
-  if (gbeg[10] > gbeg[9]) {
+  if (ge(9) > gb(9)) {
     cudaStream_t sx = side_stream();
     if (side) CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
     double levels = 0;
-    for (uint32_t i = gbeg[9]; i < gbeg[10]; ++i) levels += (double)segs[i].n * ceil_log2(segs[i].n);
+    for (uint32_t i = gb(9); i < ge(9); ++i) levels += (double)segs[i].n * ceil_log2(segs[i].n);
     Trace tr_(c, sx, kTileSort, (double)kb[9] + ob[9], levels);
-    CK(tr_.done(launch_warp_sort(d_segs, gbeg[9], gbeg[10], kA, eo, sx)), "K4 warp_sort");
+    CK(tr_.done(launch_warp_sort(d_segs, gb(9), ge(9), kA, eo, sx)), "K4 warp_sort");
   }
   for (int i = 0; i < used; ++i) {
     CK(cudaEventRecord(c->join_ev[i], joined[i]), "join");
@@ -635,12 +678,12 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     const uint32_t tiles = wtiles[g - 10];
     if (!tiles) continue;
     double levels = 0;
-    for (uint32_t k = gbeg[g]; k < gbeg[g + 1]; ++k)
+    for (uint32_t k = gb(g); k < ge(g); ++k)
       levels += (double)segs[k].n * ceil_log2(std::min<uint64_t>(segs[k].n, segs[k].run0));
     Trace tr_(c, st, kTileSort, 2.0 * kb[g], levels);
     tr_.variant = 1;
     CK(tr_.done(
-           launch_tile_sort(g == 10 ? 16 : 32, d_segs, gbeg[g], gbeg[g + 1], tiles, std::min(tiles, grid_cap), kA,
+           launch_tile_sort(g == 10 ? 16 : 32, d_segs, gb(g), ge(g), tiles, std::min(tiles, grid_cap), kA,
                             d_sticky, c->cfg.wait_limit, st)),
        "K4 tile_sort (wide keys)");
   }
@@ -650,7 +693,6 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   // load one tile while it merges another.  The widths' chains of passes are
   // independent: with more than one, each runs on a side stream of its own,
   // so that one chain's latency-bound launches overlap another's merges.
-  const uint32_t piped_grid = (uint32_t)(c->sm_count * merge_piped_ctas_per_sm());
   uint64_t job_at[4] = {}, jobs_total = 0;
   int chains = 0;
   for (int g = 0; g < 4; ++g) {
@@ -673,7 +715,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     }
     for (uint32_t p = 0; p < mpasses[g]; ++p) {
       double moved = 0;  // keys in, then keys out or, at a bucket's last pass, its words
-      for (uint32_t i = gbeg[g]; i < gbeg[g + 1]; ++i)
+      for (uint32_t i = gb(g); i < ge(g); ++i)
         if (segs[i].passes > p)
           moved += 8.0 * W * segs[i].n + (segs[i].passes == p + 1 ? out_bytes(segs[i]) : 8.0 * W * segs[i].n);
       const uint64_t* src = (p & 1) ? kB : kA;
@@ -683,7 +725,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
         {
           Trace tr_(c, sx, kMergeCut, 0.0);
           tr_.variant = (uint32_t)W;
-          CK(tr_.done(launch_merge_cut(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g], p, src, jobs, sx)), "K5 merge cut");
+          CK(tr_.done(launch_merge_cut(W, d_segs, gb(g), ge(g), mtiles[g], p, src, jobs, sx)), "K5 merge cut");
         }
         Trace tr_(c, sx, kMerge, moved);
         tr_.variant = (uint32_t)W;
@@ -691,7 +733,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       } else {
         Trace tr_(c, sx, kMerge, moved);
         tr_.variant = (uint32_t)W;
-        CK(tr_.done(launch_merge_pass2(W, d_segs, gbeg[g], gbeg[g + 1], mtiles[g],
+        CK(tr_.done(launch_merge_pass2(W, d_segs, gb(g), ge(g), mtiles[g],
                                        std::min<uint32_t>(mtiles[g], (uint32_t)c->sm_count * 8), p, src, dst, eo,
                                        sx)),
            "K5 merge_pass");
@@ -707,10 +749,10 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     const uint32_t tiles = wtiles[g - 10];
     for (uint32_t p = 0; p < wpasses[g - 10]; ++p) {
       double moved = 0;
-      for (uint32_t i = gbeg[g]; i < gbeg[g + 1]; ++i)
+      for (uint32_t i = gb(g); i < ge(g); ++i)
         if (segs[i].passes > p) moved += 16.0 * W * segs[i].n;
       LAUNCH(kMerge, moved,
-             launch_merge_pass(W, d_segs, gbeg[g], gbeg[g + 1], tiles, std::min(tiles, grid_cap), p, (p & 1) ? kB : kA,
+             launch_merge_pass(W, d_segs, gb(g), ge(g), tiles, std::min(tiles, grid_cap), p, (p & 1) ? kB : kA,
                                (p & 1) ? kA : kB, st),
              "K5 merge_pass (wide keys)");
     }
@@ -719,7 +761,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   // K6: the words of the wide keys (every other bucket was emitted by its sort)
   if (etile) {
     LAUNCH(kEmit, (double)kb[10] + kb[11] + ob[10] + ob[11],
-           launch_emit(d_segs, gbeg[10], gbeg[12], etile, std::min(etile, grid_cap), kA, kB, eo, st), "K6 emit");
+           launch_emit(d_segs, gb(10), ge(11), etile, std::min(etile, grid_cap), kA, kB, eo, st), "K6 emit");
   }
   return BSORT_OK;
 }

@@ -93,6 +93,8 @@ def test_config_default_has_builtin_tuning(libpath):
     "bogus=1",                 # unknown key
     "k4_lanes",                # no value
     "k4_lanes=4,,4,4",
+    "k4_runs=3",               # runs of 1, 2, 4 or 8 tiles
+    "k4_streams=2",
 ])
 def test_bad_tune_table_is_rejected_before_any_device_call(libpath, table):
     import paper_1407_6603_gb300 as bs
@@ -105,7 +107,7 @@ def test_bad_tune_table_is_rejected_before_any_device_call(libpath, table):
     assert e.value.status == bs.BSORT_E_INVAL
 
 
-@pytest.mark.parametrize("table", ["", "# only a comment\n", "k4_lanes=2,4,8,8; piped_min=3",
+@pytest.mark.parametrize("table", ["", "# only a comment\n", "k4_lanes=2,4,8,8; piped_min=3", "k4_runs=1 k4_streams=0",
                                    "k4_lanes=8,8,8,8\npiped_min=1000000  # forced off\n"])
 def test_good_tune_table_passes_the_parser(libpath, table):
     import torch

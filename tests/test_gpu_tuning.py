@@ -1,6 +1,7 @@
 """Every setting the autotuner can choose gives the oracle's result: the
-odd-even/merge cutoff of each tile-sort class (2, 4 or 8 lanes per group) and
-the pipelined-merge threshold (always on, never on)."""
+odd-even/merge cutoff of each tile-sort class (2, 4 or 8 lanes per group), the
+run length the tile sort leaves for the merge passes (clusters of 1, 2, 4, 8),
+the side streams and the pipelined-merge threshold (always on, never on)."""
 import numpy as np
 import pytest
 
@@ -15,7 +16,7 @@ def assert_same(got, exp, label=""):
     assert np.array_equal(got.stream, exp["stream"]), label
 
 TABLES = ["k4_lanes=2,2,2,2 piped_min=1", "k4_lanes=8,8,8,8 piped_min=1000000", "k4_lanes=2,8,4,2 piped_min=1",
-          "k4_lanes=8,4,2,8 piped_min=4"]
+          "k4_lanes=8,4,2,8 piped_min=4", "k4_runs=1 piped_min=1", "k4_runs=2 k4_streams=0", "k4_runs=4"]
 
 
 def threshold_doc(W):
