@@ -65,6 +65,7 @@ def parse_args(argv=None):
     p.add_argument("--batch-docs", type=int, default=None, help="use only the first D documents of batch_4096")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-sweep", action="store_true", help="only the oracle's thread sweep (Table 4 style), then exit")
     p.add_argument("--tune", default=None, help="tune table text (bsort_config.tune_table); default: built-in")
     p.add_argument("--no-forms", action="store_true", help="skip the batched-form summary of the default run")
     p.add_argument("--prefix-bytes", type=int, default=None,
@@ -213,6 +214,41 @@ def cpu_baseline(data, workload: str) -> dict:
             "sample": f"whole {workload} document ({data.size} B, {r['n_words']} words), {kind_s}, "
                       f"OpenMP over buckets on {cores} threads, {dt:.2f} s",
             "words_per_s": r["n_words"] / dt}
+
+
+def run_cpu_sweep(args) -> None:
+    """The paper's Table 4 measurement on this host: O1 (bubble sort per
+    length bucket, OpenMP over buckets) on the two paper-sized documents with
+    1, 2, 4, ... threads up to the core count; speedup S = T1 / Tp and
+    efficiency E = S / p.  Median of three runs for plain_190k, one for
+    plain_1m38 (whose single-thread run takes about a minute)."""
+    import oracle
+    import synth
+
+    cores = os.cpu_count() or 1
+    threads = []
+    p = 1
+    while p < cores:
+        threads.append(p)
+        p *= 2
+    threads.append(cores)
+    out = {"metric": "oracle thread sweep (Table 4 style)", "cores": cores, "documents": {}}
+    for wl, reps in (("plain_190k", 3), ("plain_1m38", 1)):
+        data = synth.plain(wl)
+        rows = []
+        for p in threads:
+            ts = []
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                oracle.bubble(data, nthreads=p)
+                ts.append(time.perf_counter() - t0)
+            rows.append({"threads": p, "seconds": statistics.median(ts)})
+        t1 = rows[0]["seconds"]
+        for r in rows:
+            r["speedup"] = t1 / r["seconds"]
+            r["efficiency"] = r["speedup"] / r["threads"]
+        out["documents"][wl] = rows
+    print(json.dumps(out), flush=True)
 
 
 def run_reference(args) -> None:
@@ -674,7 +710,9 @@ def run_serve(args) -> None:
 
 def main(argv=None) -> None:
     args = parse_args(argv)
-    if args.impl == "reference":
+    if args.cpu_sweep:
+        run_cpu_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "serve":
         run_serve(args)

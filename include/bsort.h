@@ -74,7 +74,9 @@ typedef struct {
                                                 of c CTAs: 1, 2, 4 or 8), which the merge
                                                 passes take up, when their merges are large
                                                 enough to be pipelined (see piped_min); else
-                                                into runs of 8 tiles
+                                                into runs of k4_runs_small tiles
+                              k4_runs_small=8|16  that run for the smaller merges (16: clusters
+                                                of 16 CTAs, beyond the portable cluster size)
                               k4_streams=0|1    1 (default): the tile sorts of the smaller
                                                 classes run beside the largest on side
                                                 streams; 0: one after another on the call's

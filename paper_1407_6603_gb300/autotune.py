@@ -35,6 +35,7 @@ CLUSTERS = (1, 2, 4, 8)
 LANES = (2, 4, 8)
 PIPED = (1, 2, 4, 8)
 RUNS = (8, 4, 2, 1)
+RUNS_SMALL = (8, 16)
 DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_table.txt")
 
 
@@ -117,10 +118,17 @@ def tune(reps: int = 5, log=print) -> str:
         runs_of[r] = span / reps
         log(f"  runs of {r} tiles before the merge passes: {runs_of[r]:9.3f} ms per round (whole calls)")
     runs = min(RUNS, key=lambda r: (runs_of[r], -r))
+    # 3b. the run length when the merges are too small to pipeline
+    small_of = {}
+    for r in RUNS_SMALL:
+        _, span = _time(f"k4_lanes={lanes} k4_runs={runs} k4_runs_small={r}", sets, reps)
+        small_of[r] = span / reps
+        log(f"  runs of {r} tiles before small merges: {small_of[r]:9.3f} ms per round (whole calls)")
+    runs_small = min(RUNS_SMALL, key=lambda r: (small_of[r], r))
     # 4. the merge threshold
     piped_of = {}
     for p in PIPED:
-        _, span = _time(f"k4_lanes={lanes} k4_runs={runs} piped_min={p}", sets, reps)
+        _, span = _time(f"k4_lanes={lanes} k4_runs={runs} k4_runs_small={runs_small} piped_min={p}", sets, reps)
         piped_of[p] = span / reps
         log(f"  merge threshold {p} tiles per CTA: {piped_of[p]:9.3f} ms per round (whole calls)")
     piped = min(PIPED, key=lambda p: (piped_of[p], p))
@@ -136,7 +144,10 @@ def tune(reps: int = 5, log=print) -> str:
     lines.append("# merge threshold, whole calls, ms per round: "
                  + "  ".join(f"{p}: {v:.3f}" for p, v in piped_of.items()))
     lines.append(f"k4_lanes={lanes}")
+    lines.append("# runs before small merges, whole calls, ms per round: "
+                 + "  ".join(f"{r}: {v:.3f}" for r, v in small_of.items()))
     lines.append(f"k4_runs={runs}")
+    lines.append(f"k4_runs_small={runs_small}")
     lines.append(f"piped_min={piped}")
     return "\n".join(lines) + "\n"
 

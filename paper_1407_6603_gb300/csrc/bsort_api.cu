@@ -53,6 +53,7 @@ struct Tune {
   uint32_t piped_min = 1;
   int k4_streams = 1;  // 1: the tile sorts of the smaller classes run on side streams
   int k4_runs = 1;     // cluster size (runs of that many tiles) for buckets that need pipelined merge passes
+  int k4_runs_small = 8;  // the same when their merges are too small to pipeline
 };
 
 // Parses a tune table; false on an unknown key or a bad value.
@@ -96,6 +97,9 @@ bool parse_tune(const char* text, Tune& t) {
     } else if (key == "k4_runs") {
       if (nums.size() != 1 || (nums[0] != 1 && nums[0] != 2 && nums[0] != 4 && nums[0] != 8)) return false;
       t.k4_runs = (int)nums[0];
+    } else if (key == "k4_runs_small") {
+      if (nums.size() != 1 || (nums[0] != 8 && nums[0] != 16)) return false;
+      t.k4_runs_small = (int)nums[0];
     } else if (key == "k4_streams") {
       if (nums.size() != 1 || nums[0] > 1) return false;
       t.k4_streams = (int)nums[0];
@@ -147,7 +151,7 @@ struct bsort_ctx {
   int device = 0;
   int sm_count = 0;
   cudaStream_t own_stream = nullptr;
-  static constexpr int kSide = 4;
+  static constexpr int kSide = 5;
   cudaStream_t side[kSide] = {};              // the smaller K4 launches run here, beside the clusters of 8
   cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
   cudaEvent_t counts_ev = nullptr;  // the counts of K1 reached the host
@@ -485,10 +489,11 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   const uint32_t nseg = (uint32_t)cand.size();
   // The buckets that need merge passes leave K4 as runs of k4_runs tiles
   // when their merges are large enough to be pipelined (the passes then run
-  // at HBM speed, cheaper than more cluster levels), else as runs of 8 tiles
-  // (fewer passes, fewer launches).
+  // at HBM speed, cheaper than more cluster levels), else as runs of
+  // k4_runs_small tiles (fewer passes, fewer launches).
   const uint32_t piped_grid = (uint32_t)(c->sm_count * merge_piped_ctas_per_sm());
-  const int runs = big_tiles >= (uint64_t)c->tune.piped_min * piped_grid ? c->tune.k4_runs : kSuperCluster;
+  const int runs =
+      big_tiles >= (uint64_t)c->tune.piped_min * piped_grid ? c->tune.k4_runs : c->tune.k4_runs_small;
   for (uint32_t i = 0; i < nseg; ++i)
     if (group[i] < 4) {
       Segment& sg = cand[i];
@@ -503,7 +508,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   // the warp sort and the wide keys.
   int order[kGroups], n_ord = 0;
   for (int gc : {5, 6, 7, 8}) {
-    if (kSuperCluster >> (gc - 5) == runs)
+    if (kSuperCluster >> (gc - 5) == runs || (runs > kSuperCluster && gc == 5))
       for (int g = 0; g < 5; ++g) order[n_ord++] = g;
     order[n_ord++] = gc;
   }
@@ -533,10 +538,15 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     double key_bytes = 0;
     double levels = 0;  // key-levels: each key times log2 of the sorted run it ends in
   };
-  K4Launch k4[4] = {{8, 5}, {4, 6}, {2, 7}, {1, 8}};
+  K4Launch k4[5] = {{8, 5}, {4, 6}, {2, 7}, {1, 8}, {16, -1}};  // the last: clusters of 16, runs only
   for (K4Launch& l : k4) {
-    l.sbeg = l.cluster == runs ? gb(0) : gb(l.gc);
-    l.send = ge(l.gc);
+    if (l.gc < 0) {
+      l.sbeg = runs == l.cluster ? gb(0) : 0u;
+      l.send = runs == l.cluster ? ge(4) : 0u;
+    } else {
+      l.sbeg = l.cluster == runs ? gb(0) : gb(l.gc);
+      l.send = ge(l.gc);
+    }
   }
   // bytes of a bucket's output: its letters and, if asked for, its offsets
   const uint64_t off_bytes = c->cfg.want_offsets ? 4 : 0;
@@ -657,7 +667,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     }
     Trace tr_(c, sx, kTileSort, l.key_bytes, l.levels);
     tr_.variant = (uint32_t)l.cluster;
-    const int lanes = c->tune.k4_lanes[l.cluster == 1 ? 0 : l.cluster == 2 ? 1 : l.cluster == 4 ? 2 : 3];
+    const int lanes = c->tune.k4_lanes[l.cluster == 1 ? 0 : l.cluster == 2 ? 1 : l.cluster == 4 ? 2 : 3];  // 16 as 8
     CK(tr_.done(launch_tile_sort2(l.cluster, lanes, d_segs, l.sbeg, l.send, l.supertiles, c->sm_count, l.max_w, kA,
                                   eo, d_sticky, c->cfg.wait_limit, sx)),
        "K4 tile_sort");

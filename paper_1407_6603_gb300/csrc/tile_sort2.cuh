@@ -303,6 +303,8 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
     cudaError_t r = cudaFuncSetAttribute(k_tile_sort2<CL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (r == cudaSuccess)  // shared memory, not L1, limits how many CTAs fit
       r = cudaFuncSetAttribute(k_tile_sort2<CL, G>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (r == cudaSuccess && CL > 8)  // clusters of 16 are beyond the portable 8
+      r = cudaFuncSetAttribute(k_tile_sort2<CL, G>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return r;
   });
   if (e != cudaSuccess) return e;
@@ -345,6 +347,7 @@ cudaError_t tile_sort2_lanes(int cluster, const Segment* segs, uint32_t sbeg, ui
     case 2: return tile_sort2_cl<2, G>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
     case 4: return tile_sort2_cl<4, G>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
     case 8: return tile_sort2_cl<8, G>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 16: return tile_sort2_cl<16, G>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -27,7 +27,7 @@ def test_profile_and_timeline(bsort_gpu, synth_mod):
         assert 0.0 <= s <= e, name
         assert 0 <= st <= 4
         if name == "tile_sort":
-            assert var in (0, 1, 2, 4, 8)  # CTAs per cluster, 0 for the warp sort
+            assert var in (0, 1, 2, 4, 8, 16)  # CTAs per cluster, 0 for the warp sort
         if name in ("merge_pass", "merge_cut"):
             assert var in (1, 2, 4, 8, 16, 32)  # key width
     for name in {r[0] for r in tl}:

@@ -16,7 +16,8 @@ def assert_same(got, exp, label=""):
     assert np.array_equal(got.stream, exp["stream"]), label
 
 TABLES = ["k4_lanes=2,2,2,2 piped_min=1", "k4_lanes=8,8,8,8 piped_min=1000000", "k4_lanes=2,8,4,2 piped_min=1",
-          "k4_lanes=8,4,2,8 piped_min=4", "k4_runs=1 piped_min=1", "k4_runs=2 k4_streams=0", "k4_runs=4"]
+          "k4_lanes=8,4,2,8 piped_min=4", "k4_runs=1 piped_min=1", "k4_runs=2 k4_streams=0", "k4_runs=4", "k4_runs_small=16",
+          "k4_runs_small=16 k4_streams=0 k4_lanes=8,8,8,8"]
 
 
 def threshold_doc(W):
@@ -54,6 +55,6 @@ def test_tuning_applies_to_launches(bsort_gpu):
             r = c.text(data)
             assert r.n_words == n
             tl = c.trace_read()
-        assert {v[5] for v in tl if v[0] == "tile_sort"} <= {0, 1, 2, 4, 8}
+        assert {v[5] for v in tl if v[0] == "tile_sort"} <= {0, 1, 2, 4, 8, 16}
         cuts[table] = sum(1 for v in tl if v[0] == "merge_cut")
     assert cuts["piped_min=1"] > 0 and cuts["piped_min=1000000"] == 0
