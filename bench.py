@@ -561,6 +561,7 @@ def measure(args, quiet: bool = False):
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_batch(docs) if batch else cpu_baseline(host, args.workload)
     step_sorted = sorted(step_ms)
+    path_min = nbytes + s_bytes + 4 * (n_words + len(docs)) + 8 * 256 * len(docs)
     d2h = 4 * (n_words + len(docs)) + s_bytes + 1536 * len(docs) + 32
     wl = args.workload + (f" (first {nbytes} B)" if args.prefix_bytes else "")
     if batch and args.batch_docs:
@@ -582,6 +583,11 @@ def measure(args, quiet: bool = False):
         "p99_ms": step_sorted[min(len(step_sorted) - 1, int(round(0.99 * (len(step_sorted) - 1))))],
         "roofline": roofline,
         "roofline_hbm": roofline_hbm,
+        # the whole step against the least any implementation must move: read
+        # the input, write the sorted letters, the offsets and the counts
+        "path_roofline": {"bound": "hbm", "min_bytes_per_step": path_min,
+                          "achieved": path_min / (statistics.mean(step_ms) / 1e3) / 1e9, "peak": peak,
+                          "unit": "GB/s", "frac": path_min / (statistics.mean(step_ms) / 1e3) / 1e9 / peak},
         "kernels": kernels,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_agg["mb_per_s"], "unit": "MB/s", "h2d_bytes_per_step": nbytes,

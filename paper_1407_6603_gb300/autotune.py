@@ -18,7 +18,7 @@ events and tags tile-sort launches with their cluster size.  Each class is
 first timed alone (k4_streams=0 puts every tile sort on the call's stream),
 then the per-class choice is checked against uniform ones on whole calls with
 the classes side by side, as they run in production; the merge threshold is
-judged on whole calls too.  The result is a tune table
+chosen on whole calls too.  The result is a tune table
 (bsort_config.tune_table); the library's built-in tuning is the one this
 program chose on a GB300 (tune_table.txt beside it):
 

@@ -219,6 +219,26 @@ __device__ __forceinline__ void emit_tile(const Segment& sg, uint32_t k0, uint32
                 cnt, key_word);
 }
 
+// The last index d in [0, n) with key(d) <= x, for keys ascending in d and
+// key(0) <= x, found by one warp (all 32 lanes call it): every round probes 32
+// evenly spaced indexes and keeps the gap after the last one that qualifies,
+// so about log32(n) rounds of loads instead of log2(n) one after another.
+template <class K>
+__device__ __forceinline__ uint32_t warp_last_le(K key, uint32_t n, uint32_t x) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t lo = 0, hi = n;  // the answer is in [lo, hi)
+  while (hi - lo > 1) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t p = lo + lane * step;
+    const bool ok = p < hi && key(p) <= x;
+    const uint32_t m = __ballot_sync(0xffffffffu, ok);
+    const uint32_t h = 31u - __clz(m);  // lane 0 always qualifies
+    lo = lo + h * step;
+    hi = min(lo + step, hi);
+  }
+  return lo;
+}
+
 // Field selector: which first-item number a kernel searches by.
 enum SegField { kByTile0, kByStile0, kByEtile0 };
 template <SegField F>

@@ -20,18 +20,6 @@
 namespace bsort {
 namespace {
 
-__device__ __forceinline__ uint32_t doc_of_item(const uint32_t* doc_item0, uint32_t ndocs, uint32_t it) {
-  uint32_t lo = 0, hi = ndocs - 1;  // last document with doc_item0 <= it
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) >> 1;
-    if (doc_item0[mid] <= it)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
 constexpr int kWordsPerThread = kWordBlock / kWordThreads;
 // Bytes of letters a CTA stages in shared memory (1024 words of up to 15
 // letters on average); longer ranges are read from global memory.
@@ -59,7 +47,10 @@ __global__ void __launch_bounds__(kWordThreads) k_scatter(
   const int t = threadIdx.x;
   for (uint32_t it = blockIdx.x; it < items; it += gridDim.x) {
     for (int i = t; i < kHist; i += kWordThreads) cnt[i] = 0;
-    if (t == 0) s_doc = doc_of_item(doc_item0, ndocs, it);
+    if (t < 32) {  // warp 0 finds the item's document
+      const uint32_t d0 = ndocs > 1 ? warp_last_le([&](uint32_t i) { return doc_item0[i]; }, ndocs, it) : 0u;
+      if (t == 0) s_doc = d0;
+    }
     __syncthreads();
     const uint32_t d = s_doc;
     const uint32_t w0 = doc_wbase[d] + (it - doc_item0[d]) * kWordBlock;

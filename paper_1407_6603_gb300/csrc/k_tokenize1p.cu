@@ -103,19 +103,6 @@ __device__ __forceinline__ void st_acc(TokAcc* p, const TokAcc& v) {
   __stcg(q + 4, v.ldoc);
 }
 
-__device__ __forceinline__ uint32_t doc_of_chunk(const DocDesc* docs, uint32_t ndocs, uint32_t c) {
-  uint32_t lo = 0, hi = ndocs - 1;  // last document whose chunk0 <= c
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) >> 1;
-    if (docs[mid].chunk0 <= c)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  while (lo + 1 < ndocs && (docs[lo].nchunks == 0 || c >= docs[lo].chunk0 + docs[lo].nchunks)) ++lo;
-  return lo;
-}
-
 // Adds one word length to a document's histogram (bin 0 counts words longer
 // than l_cap, which make the document fail).
 __device__ __forceinline__ void count_length(uint32_t L, uint32_t doc, uint32_t my_doc, uint32_t l_cap,
@@ -145,9 +132,21 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
   __shared__ uint32_t s_wlast[kTokThreads / 32];
   const int t = threadIdx.x;
   for (int i = t; i < kHist; i += kTokThreads) h_local[i] = 0;
-  if (t == 0) {
-    s_c = atomicAdd(&s->ticket, 1u);
-    s_doc = (s_c < nchunks) ? (ndocs == 1 ? 0u : doc_of_chunk(docs, ndocs, s_c)) : 0u;
+  if (t < 32) {  // warp 0 takes the ticket and finds the chunk's document
+    uint32_t c0 = 0;
+    if (t == 0) c0 = atomicAdd(&s->ticket, 1u);
+    c0 = __shfl_sync(kFull, c0, 0);
+    uint32_t d0 = 0;
+    if (c0 < nchunks && ndocs > 1) {
+      d0 = warp_last_le([&](uint32_t i) { return docs[i].chunk0; }, ndocs, c0);
+      // empty documents share their chunk0 with the next one: step past them
+      if (t == 0)
+        while (d0 + 1 < ndocs && (docs[d0].nchunks == 0 || c0 >= docs[d0].chunk0 + docs[d0].nchunks)) ++d0;
+    }
+    if (t == 0) {
+      s_c = c0;
+      s_doc = d0;
+    }
   }
   __syncthreads();
   const uint32_t c = s_c;
