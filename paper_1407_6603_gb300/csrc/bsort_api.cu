@@ -168,9 +168,8 @@ struct bsort_ctx {
   // results of the last run (host view)
   MetaLayout ml;
   uint32_t ndocs = 0;
-  std::vector<Segment> segv, segv2;
+  std::vector<Segment> segv;
   std::vector<uint8_t> groupv;
-  std::vector<uint32_t> lookupv;
   std::vector<uint32_t> doc_status;
 
   // tracing
@@ -422,16 +421,16 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   }
 
   // ---- bucket layout: one segment per (document, length) ----
-  // Groups, in table order (T = one K4 tile of the bucket's key width):
-  //   0..3  W = 1, 2, 4, 8 and more than 8T keys: K4 in clusters of 8, then
-  //         K5 merge passes (one launch per pass and width); group 4 unused
+  // Groups (T = one K4 tile of the bucket's key width; table order below):
+  //   0..3  W = 1, 2, 4, 8 and more than 8T keys: K4 into runs of k4_runs or
+  //         k4_runs_small tiles, then K5 merge passes (one launch per pass
+  //         and width); group 4 unused
   //   5     (4T, 8T] keys: K4 in clusters of 8        6   (2T, 4T]: clusters of 4
   //   7     (T, 2T]: clusters of 2                      8   (32 KPT, T]: single CTAs
   //   9     at most 32 lanes x KPT keys: one warp each
   //   10,11 keys of 16 / 32 words (65..128 / 129..255 letters): the narrow-tile
   //         kernels of k_sort.cu
   constexpr int kGroups = 12;
-  c->lookupv.assign((size_t)ndocs * kHist, kNoSegment);
   for (uint32_t d = 0; d < ndocs; ++d)
     if (h_hist[(size_t)d * kHist] != 0) c->doc_status[d] = BSORT_E_WORD_TOO_LONG;
   std::vector<Segment>& cand = c->segv;
@@ -520,8 +519,18 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   for (int q = 0; q < kGroups; ++q) pbeg[q + 1] = pbeg[q] + group_n[order[q]];
   auto gb = [&](int g) { return pbeg[pos_of[g]]; };      // first segment of group g
   auto ge = [&](int g) { return pbeg[pos_of[g] + 1]; };  // one past its last
-  std::vector<Segment>& segs = c->segv2;
-  segs.resize(nseg);
+  // the layout is built in place in the page-locked upload buffer: segments,
+  // the (document, length) -> segment lookup and the zeroed slot cursors of
+  // K3, which go to the device in one copy
+  const size_t seg_bytes = align_up(sizeof(Segment) * std::max<size_t>(nseg, 1), 256);
+  const size_t lookup_bytes = align_up(4ull * ndocs * kHist, 256);
+  const size_t cursor_bytes = align_up(4ull * std::max<uint32_t>(nseg, 1), 256);
+  const size_t plan_bytes = seg_bytes + lookup_bytes + cursor_bytes;
+  GROW_HOST(c->h_plan, plan_bytes, "layout");
+  Segment* const segs = hptr<Segment>(c->h_plan);
+  uint32_t* const lookup = hptr<uint32_t>(c->h_plan, seg_bytes);
+  std::memset(lookup, 0xFF, 4ull * ndocs * kHist);  // kNoSegment
+  std::memset(hptr<char>(c->h_plan, seg_bytes + lookup_bytes), 0, cursor_bytes);
   {
     uint32_t at[kGroups];
     for (int q = 0; q < kGroups; ++q) at[q] = pbeg[q];
@@ -589,20 +598,10 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       wtiles[gi - 10] += (sg.n + sg.run0 - 1) / sg.run0;
       wpasses[gi - 10] = std::max(wpasses[gi - 10], sg.passes);
     }
-    c->lookupv[(size_t)sg.doc * kHist + sg.L] = i;
+    lookup[(size_t)sg.doc * kHist + sg.L] = i;
   }
 
   // ---- upload the layout, size the key and output buffers ----
-  // segments, the (document, length) -> segment lookup and the zeroed slot
-  // cursors of K3 go to the device in one copy
-  const size_t seg_bytes = align_up(sizeof(Segment) * std::max<size_t>(nseg, 1), 256);
-  const size_t lookup_bytes = align_up(4ull * ndocs * kHist, 256);
-  const size_t cursor_bytes = align_up(4ull * std::max<uint32_t>(nseg, 1), 256);
-  const size_t plan_bytes = seg_bytes + lookup_bytes + cursor_bytes;
-  GROW_HOST(c->h_plan, plan_bytes, "layout");
-  if (nseg) std::memcpy(c->h_plan.p, segs.data(), sizeof(Segment) * nseg);
-  std::memcpy(hptr<char>(c->h_plan, seg_bytes), c->lookupv.data(), 4ull * ndocs * kHist);
-  std::memset(hptr<char>(c->h_plan, seg_bytes + lookup_bytes), 0, cursor_bytes);
   GROW(c->plan, plan_bytes, "layout");
   GROW(c->keysA, 8 * std::max<uint64_t>(key_words, 16), "keys");
   GROW(c->keysB, 8 * std::max<uint64_t>(key_words, 16), "keys");
