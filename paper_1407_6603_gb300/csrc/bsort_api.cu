@@ -708,7 +708,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     if (mpasses[g]) ++chains;
     if (mtiles[g] >= c->tune.piped_min * piped_grid) {
       job_at[g] = jobs_total;
-      jobs_total += mtiles[g];
+      jobs_total += mtiles[g] + 1;  // and the end sentinel
     }
   }
   if (jobs_total) GROW(c->jobs, sizeof(TileJob) * jobs_total, "merge jobs");

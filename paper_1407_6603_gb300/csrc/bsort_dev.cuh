@@ -110,20 +110,24 @@ struct Segment {
 };
 
 // One output tile of a pipelined merge pass (K5), as the cut kernel leaves it:
-// where the tile's slices of the two runs start, how many keys each gives,
-// and where its output goes.
+// where the tile's slices of the two runs start and where run A ends, how
+// many keys it outputs, and where they go.  The tile takes run A's keys up to
+// the next tile's a_src (or a_end, whichever comes first) and the rest of its
+// outputs from run B.
 struct TileJob {
-  uint64_t a_src;   // word offset in the source key buffer of the tile's slice of run A
+  uint64_t a_src;   // word offset in the source key buffer of the tile's first key of run A
   uint64_t b_src;   // the same for run B
+  uint64_t a_end;   // end of run A (its words up to, not including, this offset)
   uint64_t dst;     // word offset in the destination key buffer of the tile's first output
-  uint32_t na, nb;  // keys taken from A and from B; both 0: nothing to do
+  uint32_t cnt;     // outputs of the tile; 0: nothing to do
   uint32_t L;       // 0: the merged keys go to dst; else this pass finishes the bucket
                     // and its words (of L letters) are emitted:
   uint32_t stream;  //   stream byte offset of the tile's first word
   uint32_t word;    //   offsets[] index of that word
   uint32_t rel;     //   its offset within its document
+  uint32_t pad[3];
 };
-static_assert(sizeof(TileJob) == 48, "TileJob is three 16-byte copies");
+static_assert(sizeof(TileJob) == 64, "TileJob is four 16-byte copies");
 
 // K4 v2 / K5 v2 geometry (keys of at most 16 u64 words).
 constexpr int kSuperCluster = 8;    // CTAs per K4 cluster
@@ -271,6 +275,15 @@ __device__ __forceinline__ uint32_t seg_find(const Segment* segs, uint32_t sbeg,
       hi = mid - 1;
   }
   return sbeg + lo;
+}
+// seg_find by one warp (all 32 lanes call it): from the shared-memory cache
+// when the launch's segments fit it, else by 32-way rounds over the table in
+// global memory (a few dependent loads instead of one per halving).
+template <SegField F>
+__device__ __forceinline__ uint32_t seg_find_warp(const Segment* segs, uint32_t sbeg, uint32_t send,
+                                                  const uint32_t* cache, bool cached, uint32_t it) {
+  if (cached) return seg_find<F>(segs, sbeg, send, cache, true, it);
+  return sbeg + warp_last_le([&](uint32_t i) { return seg_first_item<F>(segs[sbeg + i]); }, send - sbeg, it);
 }
 #endif
 

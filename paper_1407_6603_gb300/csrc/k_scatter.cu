@@ -129,7 +129,10 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const Segment* __restrict
   __shared__ uint32_t s_first[kSegCache];
   const bool cached = seg_cache_fill<kByEtile0>(segs, sbeg, send, s_first);
   for (uint32_t it = blockIdx.x; it < tiles; it += gridDim.x) {
-    if (threadIdx.x == 0) s_seg = seg_find<kByEtile0>(segs, sbeg, send, s_first, cached, it);
+    if (threadIdx.x < 32) {
+      const uint32_t v = seg_find_warp<kByEtile0>(segs, sbeg, send, s_first, cached, it);
+      if (threadIdx.x == 0) s_seg = v;
+    }
     __syncthreads();
     const Segment sg = segs[s_seg];
     __syncthreads();

@@ -202,7 +202,10 @@ __global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_pass2(c
   const uint32_t nchunk = (tiles + chunk - 1) / chunk;
   for (uint32_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x)
     for (uint32_t it = ch * chunk; it < min(tiles, ch * chunk + chunk); ++it) {
-      if (threadIdx.x == 0) s_seg = seg_find<kByTile0>(segs, sbeg, send, s_first, cached, it);
+      if (threadIdx.x < 32) {
+        const uint32_t v = seg_find_warp<kByTile0>(segs, sbeg, send, s_first, cached, it);
+        if (threadIdx.x == 0) s_seg = v;
+      }
       __syncthreads();
       const uint32_t si = s_seg;
       const Segment sg = segs[si];
@@ -213,9 +216,10 @@ __global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_pass2(c
 }
 
 // ------------------------------------------------- pipelined K5 ----
-// The cut kernel: one warp per output tile of the pass.  Its two half-warps
-// find, by a 16-way merge-path search each, where the tile's first and its
-// last-plus-one outputs cut the two runs; lane 0 writes the tile's job.
+// The cut kernel: one warp per output tile of the pass finds, by a 32-way
+// merge-path search, where the tile's first output cuts the two runs (its end
+// is the next tile's start), and lane 0 writes the tile's job.  Entry `tiles`
+// is a sentinel whose run-A start lies past every run.
 template <int W>
 __global__ void __launch_bounds__(256) k_merge_cut(const Segment* __restrict__ segs, uint32_t sbeg, uint32_t send,
                                                    uint32_t tiles, uint32_t pass, const uint64_t* __restrict__ src,
@@ -224,46 +228,46 @@ __global__ void __launch_bounds__(256) k_merge_cut(const Segment* __restrict__ s
   constexpr uint32_t T = kM2Threads * KPT;
   __shared__ uint32_t s_first[kSegCache];
   const bool cached = seg_cache_fill<kByTile0>(segs, sbeg, send, s_first);
-  const int lane = threadIdx.x & 31, half = lane >> 4, h = lane & 15;
+  const uint32_t lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * (blockDim.x / 32);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    TileJob end{};
+    end.a_src = ~0ull;
+    jobs[tiles] = end;
+  }
   for (uint32_t it = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < tiles; it += warps) {
-    const uint32_t si = seg_find<kByTile0>(segs, sbeg, send, s_first, cached, it);
+    const uint32_t si = seg_find_warp<kByTile0>(segs, sbeg, send, s_first, cached, it);
     const Segment& sg = segs[si];
     TileJob job{};
     const uint32_t passes = sg.passes;
-    if (passes > pass) {  // else the bucket is one run already: nothing to do
+    const uint64_t out0 = (uint64_t)(it - sg.tile0) * T;
+    job.a_src = sg.key_off + out0 * W;  // (a bucket already in one run: monotone, no outputs)
+    if (passes > pass) {
       const uint64_t n = sg.n, R = (uint64_t)sg.run0 << pass;
-      const uint64_t out0 = (uint64_t)(it - sg.tile0) * T;
       const uint64_t ps = out0 / (2 * R) * (2 * R);
       const uint32_t la = (uint32_t)min(R, n - ps);
       const uint32_t lb = n - ps > R ? (uint32_t)min(R, n - ps - R) : 0u;
-      const uint32_t d0 = (uint32_t)(out0 - ps);
-      const uint32_t d1 = d0 + min(T, la + lb - d0);
+      const uint32_t d = (uint32_t)(out0 - ps);
       const uint64_t* A = src + sg.key_off + ps * W;
       const uint64_t* B = A + (size_t)la * W;
-      const uint32_t d = half ? d1 : d0;
       uint32_t lo = d > lb ? d - lb : 0u, hi = d < la ? d : la;
-      for (;;) {
-        const bool more = hi > lo;
-        if (!__any_sync(kFull, more)) break;
+      while (hi > lo) {  // uniform across the warp
         const uint32_t span = hi - lo;
-        const uint32_t step = span <= 16u ? 1u : (span + 15u) / 16u;
-        const uint32_t m = lo + (uint32_t)h * step;
+        const uint32_t step = span <= 32u ? 1u : (span + 31u) / 32u;
+        const uint32_t m = lo + lane * step;
         bool f = false;  // A[m] goes before the diagonal's B key: the cut is past m
-        if (more && m < hi) f = !klt(kload<W>(B + (size_t)(d - 1 - m) * W), kload<W>(A + (size_t)m * W));
-        const uint32_t nf = __popc((__ballot_sync(kFull, f) >> (16 * half)) & 0xffffu);
-        if (more) {  // the cut lies after the last probe that says so, up to the next probe
-          const uint32_t nhi = lo + nf * step < hi ? lo + nf * step : hi;
-          lo = nf == 0 ? lo : lo + (nf - 1) * step + 1;
-          hi = nhi;
-        }
+        if (m < hi) f = !klt(kload<W>(B + (size_t)(d - 1 - m) * W), kload<W>(A + (size_t)m * W));
+        const uint32_t nf = __popc(__ballot_sync(kFull, f));
+        // the cut lies after the last probe that says so, up to the next probe
+        const uint32_t nhi = lo + nf * step < hi ? lo + nf * step : hi;
+        lo = nf == 0 ? lo : lo + (nf - 1) * step + 1;
+        hi = nhi;
       }
-      const uint32_t a0 = __shfl_sync(kFull, lo, 0), a1 = __shfl_sync(kFull, lo, 16);
-      job.a_src = sg.key_off + (ps + a0) * W;
-      job.b_src = sg.key_off + (ps + la + (d0 - a0)) * W;
+      job.a_src = sg.key_off + (ps + lo) * W;
+      job.b_src = sg.key_off + (ps + la + (d - lo)) * W;
+      job.a_end = sg.key_off + (ps + la) * W;
       job.dst = sg.key_off + out0 * W;
-      job.na = a1 - a0;
-      job.nb = (d1 - a1) - (d0 - a0);
+      job.cnt = min(T, la + lb - d);
       if (pass + 1 == passes) {
         job.L = sg.L;
         job.stream = sg.stream_off + (uint32_t)out0 * sg.L;
@@ -288,18 +292,26 @@ __global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_piped(c
   constexpr uint32_t TW = kM2Threads * KPT * W;
   extern __shared__ __align__(128) uint64_t sm[];  // two tile buffers, padded layout
   __shared__ __align__(16) TileJob s_job[3];
+  __shared__ __align__(8) uint64_t s_next[3];  // the next tile's a_src
   const uint32_t bw = padded_words(TW);
   const int t = threadIdx.x;
   const uint32_t G = gridDim.x;
   auto fetch_job = [&](uint32_t k) {  // the CTA's k-th job into ring slot k % 3
     const uint32_t it = blockIdx.x + k * G;
-    if (it < tiles && t < 3)
+    if (it < tiles && t < 4)
       cp_async16(reinterpret_cast<uint4*>(&s_job[k % 3]) + t, reinterpret_cast<const uint4*>(jobs + it) + t);
+    if (it < tiles && t == 4) cp_async8(&s_next[k % 3], &jobs[it + 1].a_src);
+  };
+  // keys of the job's tile taken from run A
+  auto na_of = [&](uint32_t k) {
+    const TileJob& j = s_job[k % 3];
+    const uint64_t a1 = s_next[k % 3] < j.a_end ? s_next[k % 3] : j.a_end;
+    return (uint32_t)((a1 - j.a_src) / W);
   };
   auto fetch_data = [&](uint32_t k) {  // its slices into buffer k & 1: A's keys, then B's
     if (blockIdx.x + k * G >= tiles) return;
     const TileJob& j = s_job[k % 3];
-    const uint32_t wa = j.na * W, tot = (j.na + j.nb) * W;
+    const uint32_t wa = j.cnt ? na_of(k) * W : 0u, tot = j.cnt * W;
     uint64_t* buf = sm + (k & 1) * bw;
     for (uint32_t e = t; e < tot; e += kM2Threads) cp_async8(buf + padw(e), src + (e < wa ? j.a_src + e : j.b_src + (e - wa)));
   };
@@ -317,8 +329,9 @@ __global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_piped(c
     fetch_job(k + 2);
     cp_async_commit();
     const TileJob& j = s_job[k % 3];
-    const uint32_t na = j.na, nb = j.nb, cnt = na + nb;
+    const uint32_t cnt = j.cnt;
     if (cnt == 0) continue;
+    const uint32_t na = na_of(k), nb = cnt - na;
     uint64_t* buf = sm + (k & 1) * bw;
     Key<W> kk[KPT];
     const uint32_t pos = t * KPT;

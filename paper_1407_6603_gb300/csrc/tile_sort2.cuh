@@ -277,7 +277,10 @@ __global__ void __launch_bounds__(kT2Threads, BSORT_K4_MIN_CTAS) k_tile_sort2(co
   __syncthreads();
   uint32_t phase = 0;
   for (uint32_t st = cid; st < nst; st += ncl) {  // uniform across the cluster
-    if (t == 0) s_seg = seg_find<kByStile0>(segs, sbeg, send, s_first, cached, st);
+    if (t < 32) {
+      const uint32_t v = seg_find_warp<kByStile0>(segs, sbeg, send, s_first, cached, st);
+      if (t == 0) s_seg = v;
+    }
     __syncthreads();
     const Segment sg = segs[s_seg];
     __syncthreads();
