@@ -524,7 +524,8 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   // K3, which go to the device in one copy
   const size_t seg_bytes = align_up(sizeof(Segment) * std::max<size_t>(nseg, 1), 256);
   const size_t lookup_bytes = align_up(4ull * ndocs * kHist, 256);
-  const size_t cursor_bytes = align_up(4ull * std::max<uint32_t>(nseg, 1), 256);
+  // (after the cursors: the grid-barrier counters of the merge chains)
+  const size_t cursor_bytes = align_up(4ull * (std::max<uint32_t>(nseg, 1) + 4), 256);
   const size_t plan_bytes = seg_bytes + lookup_bytes + cursor_bytes;
   GROW_HOST(c->h_plan, plan_bytes, "layout");
   Segment* const segs = hptr<Segment>(c->h_plan);
@@ -612,6 +613,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   Segment* const segs_dev = dptr<Segment>(c->plan);
   uint32_t* const lookup_dev = dptr<uint32_t>(c->plan, seg_bytes);
   uint32_t* const cursor_dev = dptr<uint32_t>(c->plan, seg_bytes + lookup_bytes);
+  uint32_t* const barrier_dev = cursor_dev + std::max<uint32_t>(nseg, 1);  // one per key width
 
   if (gap_a) {  // the round trip ends where the layout copy is enqueued
     cudaEvent_t gap_b = next_event(c);
@@ -722,31 +724,37 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       sx = c->side[g];
       CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
     }
-    for (uint32_t p = 0; p < mpasses[g]; ++p) {
-      double moved = 0;  // keys in, then keys out or, at a bucket's last pass, its words
+    auto moved_in = [&](uint32_t p) {  // keys in, then keys out or, at a bucket's last pass, its words
+      double moved = 0;
       for (uint32_t i = gb(g); i < ge(g); ++i)
         if (segs[i].passes > p)
           moved += 8.0 * W * segs[i].n + (segs[i].passes == p + 1 ? out_bytes(segs[i]) : 8.0 * W * segs[i].n);
-      const uint64_t* src = (p & 1) ? kB : kA;
-      uint64_t* dst = (p & 1) ? kA : kB;
-      if (mtiles[g] >= c->tune.piped_min * piped_grid) {
+      return moved;
+    };
+    if (mtiles[g] >= c->tune.piped_min * piped_grid) {
+      for (uint32_t p = 0; p < mpasses[g]; ++p) {
+        const uint64_t* src = (p & 1) ? kB : kA;
+        uint64_t* dst = (p & 1) ? kA : kB;
         TileJob* jobs = dptr<TileJob>(c->jobs) + job_at[g];
         {
           Trace tr_(c, sx, kMergeCut, 0.0);
           tr_.variant = (uint32_t)W;
           CK(tr_.done(launch_merge_cut(W, d_segs, gb(g), ge(g), mtiles[g], p, src, jobs, sx)), "K5 merge cut");
         }
-        Trace tr_(c, sx, kMerge, moved);
+        Trace tr_(c, sx, kMerge, moved_in(p));
         tr_.variant = (uint32_t)W;
         CK(tr_.done(launch_merge_piped(W, jobs, mtiles[g], piped_grid, src, dst, eo, sx)), "K5 merge_pass");
-      } else {
-        Trace tr_(c, sx, kMerge, moved);
-        tr_.variant = (uint32_t)W;
-        CK(tr_.done(launch_merge_pass2(W, d_segs, gb(g), ge(g), mtiles[g],
-                                       std::min<uint32_t>(mtiles[g], (uint32_t)c->sm_count * 8), p, src, dst, eo,
-                                       sx)),
-           "K5 merge_pass");
       }
+    } else {
+      // small passes: all of them in one launch, grid barriers between them
+      double moved = 0;
+      for (uint32_t p = 0; p < mpasses[g]; ++p) moved += moved_in(p);
+      Trace tr_(c, sx, kMerge, moved);
+      tr_.variant = (uint32_t)W;
+      CK(tr_.done(launch_merge_pass2(W, d_segs, gb(g), ge(g), mtiles[g],
+                                     std::min<uint32_t>(mtiles[g], (uint32_t)c->sm_count * 8), 0, mpasses[g], kA,
+                                     kB, eo, barrier_dev + g, d_sticky, c->cfg.wait_limit, sx)),
+         "K5 merge_pass");
     }
     if (chains > 1) {
       CK(cudaEventRecord(c->join_ev[nj], sx), "join");

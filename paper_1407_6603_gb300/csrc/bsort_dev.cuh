@@ -341,9 +341,12 @@ cudaError_t launch_tile_sort2_g4(int cluster, const Segment* segs, uint32_t sbeg
 cudaError_t launch_tile_sort2_g8(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                                  int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
                                  uint64_t wait_limit, cudaStream_t st);
+// Merge passes pass0 .. pass0 + npass - 1 (keys between kA and kB, pass p
+// reading kA when p is even); npass > 1 makes one cooperative launch whose
+// passes are separated by grid barriers counted on *barrier (zeroed).
 cudaError_t launch_merge_pass2(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
-                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, EmitOut eo,
-                               cudaStream_t st);
+                               uint32_t grid, uint32_t pass0, uint32_t npass, uint64_t* kA, uint64_t* kB, EmitOut eo,
+                               uint32_t* barrier, Meta* meta, uint64_t wait_limit, cudaStream_t st);
 // Pipelined K5 for passes with many tiles: the cut kernel finds every tile's
 // slices (one warp per tile), then the merge kernel streams the tiles through
 // two shared-memory buffers, loading one while it merges the other.

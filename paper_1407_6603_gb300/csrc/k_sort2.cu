@@ -95,7 +95,7 @@ struct SplitCarry {
 // the padded layout; each thread merges its KPT outputs into registers.
 template <int W>
 __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t pass,
-                           const uint64_t* __restrict__ src, uint64_t* __restrict__ dst, uint64_t* sm,
+                           const uint64_t* src, uint64_t* dst, uint64_t* sm,
                            SplitCarry& carry, const EmitOut& eo) {
   constexpr int KPT = W >= 8 ? 1 : 8 / W;
   constexpr uint32_t T = kM2Threads * KPT;
@@ -185,34 +185,68 @@ __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t
   __syncthreads();
 }
 
-// One merge pass over the buckets [sbeg, send) of key width W.
+// Grid-wide barrier of a cooperative launch (every CTA resident): CTA
+// arrivals counted on `counter`, generation `gen` complete when the count
+// reaches (gen + 1) * gridDim.x.  The wait is bounded: when it runs out the
+// call is marked timed out and the CTA goes on.
+__device__ __forceinline__ void grid_barrier(uint32_t* counter, uint32_t gen, Meta* meta, uint64_t wait_limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(counter, 1u);
+    const uint32_t target = (gen + 1) * gridDim.x;
+    uint64_t polls = 0;
+    for (;;) {
+      uint32_t v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+      if (v >= target) break;
+      if (++polls >= wait_limit) {
+        atomicAdd(&meta->err_timeout, 1u);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();  // the other CTAs' writes of the pass are seen from here on
+  }
+  __syncthreads();
+}
+
+// Merge passes pass0 .. pass0 + npass - 1 over the buckets [sbeg, send) of
+// key width W, the keys moving between kA and kB (pass p reads kA when p is
+// even).  With npass > 1 the launch is cooperative and the passes are
+// separated by grid barriers, one launch for all of them.
 template <int W>
-__global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_pass2(const Segment* __restrict__ segs, uint32_t sbeg,
-                                                            uint32_t send, uint32_t tiles, uint32_t pass,
-                                                            uint32_t chunk, const uint64_t* __restrict__ src,
-                                                            uint64_t* __restrict__ dst, EmitOut eo) {
+__global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_pass2(
+    const Segment* __restrict__ segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t pass0, uint32_t npass,
+    uint32_t chunk, uint64_t* kA, uint64_t* kB, EmitOut eo, uint32_t* barrier, Meta* meta, uint64_t wait_limit) {
   extern __shared__ __align__(128) uint64_t sm[];
   __shared__ uint32_t s_seg;
   __shared__ uint32_t s_first[kSegCache];
   const bool cached = seg_cache_fill<kByTile0>(segs, sbeg, send, s_first);
-  // chunks of `chunk` consecutive tiles, dealt round-robin: within a chunk a
-  // tile's start split is the previous tile's end split; with few tiles the
-  // host asks for chunks of one so that no CTA serialises several
-  SplitCarry carry{~0u, ~0u, 0u, ~0ull};
   const uint32_t nchunk = (tiles + chunk - 1) / chunk;
-  for (uint32_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x)
-    for (uint32_t it = ch * chunk; it < min(tiles, ch * chunk + chunk); ++it) {
-      if (threadIdx.x < 32) {
-        const uint32_t v = seg_find_warp<kByTile0>(segs, sbeg, send, s_first, cached, it);
-        if (threadIdx.x == 0) s_seg = v;
+  for (uint32_t q = 0; q < npass; ++q) {
+    const uint32_t pass = pass0 + q;
+    const uint64_t* src = (pass & 1) ? kB : kA;
+    uint64_t* dst = (pass & 1) ? kA : kB;
+    if (q > 0) grid_barrier(barrier, q - 1, meta, wait_limit);
+    // chunks of `chunk` consecutive tiles, dealt round-robin: within a chunk a
+    // tile's start split is the previous tile's end split; with few tiles the
+    // host asks for chunks of one so that no CTA serialises several
+    SplitCarry carry{~0u, ~0u, 0u, ~0ull};
+    for (uint32_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x)
+      for (uint32_t it = ch * chunk; it < min(tiles, ch * chunk + chunk); ++it) {
+        if (threadIdx.x < 32) {
+          const uint32_t v = seg_find_warp<kByTile0>(segs, sbeg, send, s_first, cached, it);
+          if (threadIdx.x == 0) s_seg = v;
+        }
+        __syncthreads();
+        const uint32_t si = s_seg;
+        const Segment sg = segs[si];
+        __syncthreads();
+        if (sg.passes <= pass) continue;  // this bucket is already one run
+        merge_tile<W>(sg, si, it, pass, src, dst, sm, carry, eo);
       }
-      __syncthreads();
-      const uint32_t si = s_seg;
-      const Segment sg = segs[si];
-      __syncthreads();
-      if (sg.passes <= pass) continue;  // this bucket is already one run
-      merge_tile<W>(sg, si, it, pass, src, dst, sm, carry, eo);
-    }
+  }
 }
 
 // ------------------------------------------------- pipelined K5 ----
@@ -360,22 +394,45 @@ __global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_piped(c
 
 template <int W>
 cudaError_t merge_pass2_w(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,
-                          uint32_t pass, const uint64_t* src, uint64_t* dst, const EmitOut& eo, cudaStream_t st) {
+                          uint32_t pass0, uint32_t npass, uint64_t* kA, uint64_t* kB, const EmitOut& eo,
+                          uint32_t* barrier, Meta* meta, uint64_t wait_limit, cudaStream_t st) {
   constexpr uint32_t words = kM2Threads * (W >= 8 ? 1 : 8 / W) * W;
   const size_t smem = (size_t)padded_words(words) * 8;
   // (the default carveout stays: the merge-path probes live in L1)
   static int attr_done[64];
+  static int resident[64];  // CTAs per SM, for the cooperative form
   cudaError_t e = once_per_device(attr_done, [&] {
-    return smem > 48 * 1024
-               ? cudaFuncSetAttribute(k_merge_pass2<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-               : cudaSuccess;
+    cudaError_t r = smem > 48 * 1024
+                        ? cudaFuncSetAttribute(k_merge_pass2<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                        : cudaSuccess;
+    int dev = 0, per_sm = 0;
+    if (r == cudaSuccess) r = cudaGetDevice(&dev);
+    if (r == cudaSuccess) r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_merge_pass2<W>, kM2Threads, smem);
+    if (r == cudaSuccess && dev >= 0 && dev < 64) resident[dev] = per_sm;
+    return r;
   });
   if (e != cudaSuccess) return e;
   const uint32_t chunk = tiles >= 4u * grid ? 4u : 1u;
   const uint32_t nchunk = (tiles + chunk - 1) / chunk;
-  k_merge_pass2<W><<<nchunk < grid ? nchunk : grid, kM2Threads, smem, st>>>(segs, sbeg, send, tiles, pass, chunk,
-                                                                            src, dst, eo);
-  return cudaGetLastError();
+  uint32_t g = nchunk < grid ? nchunk : grid;
+  if (npass <= 1) {
+    k_merge_pass2<W><<<g, kM2Threads, smem, st>>>(segs, sbeg, send, tiles, pass0, 1u, chunk, kA, kB, eo, barrier, meta,
+                                                 wait_limit);
+    return cudaGetLastError();
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return cudaErrorUnknown;
+  // at most a quarter of what fits on the device: the chains of the four key
+  // widths may each run one of these grids at the same time, and all of them
+  // must be resident together
+  const uint32_t cap = (uint32_t)(resident[dev >= 0 && dev < 64 ? dev : 0] * sms) / 4;
+  if (cap == 0) return cudaErrorCooperativeLaunchTooLarge;
+  if (g > cap) g = cap;
+  void* args[] = {&segs, &sbeg, &send, &tiles, &pass0, &npass, const_cast<uint32_t*>(&chunk), &kA, &kB,
+                  const_cast<EmitOut*>(&eo), &barrier, &meta, &wait_limit};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(k_merge_pass2<W>), dim3(g), dim3(kM2Threads), args, smem,
+                                     st);
 }
 
 }  // namespace
@@ -446,14 +503,14 @@ cudaError_t launch_merge_piped(int W, const TileJob* jobs, uint32_t tiles, uint3
 }
 
 cudaError_t launch_merge_pass2(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
-                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, EmitOut eo,
-                               cudaStream_t st) {
+                               uint32_t grid, uint32_t pass0, uint32_t npass, uint64_t* kA, uint64_t* kB, EmitOut eo,
+                               uint32_t* barrier, Meta* meta, uint64_t wait_limit, cudaStream_t st) {
   if (tiles == 0 || grid == 0) return cudaSuccess;
   switch (W) {
-    case 1: return merge_pass2_w<1>(segs, sbeg, send, tiles, grid, pass, src, dst, eo, st);
-    case 2: return merge_pass2_w<2>(segs, sbeg, send, tiles, grid, pass, src, dst, eo, st);
-    case 4: return merge_pass2_w<4>(segs, sbeg, send, tiles, grid, pass, src, dst, eo, st);
-    case 8: return merge_pass2_w<8>(segs, sbeg, send, tiles, grid, pass, src, dst, eo, st);
+    case 1: return merge_pass2_w<1>(segs, sbeg, send, tiles, grid, pass0, npass, kA, kB, eo, barrier, meta, wait_limit, st);
+    case 2: return merge_pass2_w<2>(segs, sbeg, send, tiles, grid, pass0, npass, kA, kB, eo, barrier, meta, wait_limit, st);
+    case 4: return merge_pass2_w<4>(segs, sbeg, send, tiles, grid, pass0, npass, kA, kB, eo, barrier, meta, wait_limit, st);
+    case 8: return merge_pass2_w<8>(segs, sbeg, send, tiles, grid, pass0, npass, kA, kB, eo, barrier, meta, wait_limit, st);
     default: return cudaErrorInvalidValue;
   }
 }

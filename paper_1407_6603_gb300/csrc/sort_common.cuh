@@ -245,8 +245,8 @@ __device__ uint32_t coop_split_fn(FA keyA, uint32_t la, FB keyB, uint32_t lb, ui
 }
 
 template <int W, int NTH>
-__device__ __forceinline__ uint32_t coop_split(const uint64_t* __restrict__ A, uint32_t la,
-                                               const uint64_t* __restrict__ B, uint32_t lb, uint32_t d) {
+__device__ __forceinline__ uint32_t coop_split(const uint64_t* A, uint32_t la, const uint64_t* B, uint32_t lb,
+                                               uint32_t d) {
   return coop_split_fn<W, NTH>([&](uint32_t i) { return kload<W>(A + (size_t)i * W); }, la,
                                [&](uint32_t i) { return kload<W>(B + (size_t)i * W); }, lb, d);
 }
