@@ -244,6 +244,26 @@ __device__ uint32_t coop_split_fn(FA keyA, uint32_t la, FB keyB, uint32_t lb, ui
   return lo;
 }
 
+// The merge-path search by one warp (all 32 lanes call it): 32 probes per
+// round, ballots instead of CTA barriers.  keyA / keyB as in coop_split_fn.
+template <int W, class FA, class FB>
+__device__ __forceinline__ uint32_t warp_split_fn(FA keyA, uint32_t la, FB keyB, uint32_t lb, uint32_t d) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t lo = d > lb ? d - lb : 0u, hi = d < la ? d : la;
+  while (hi > lo) {
+    const uint32_t span = hi - lo;
+    const uint32_t step = span <= 32u ? 1u : (span + 31u) / 32u;
+    const uint32_t m = lo + lane * step;
+    bool f = false;
+    if (m < hi) f = !klt(keyB(d - 1 - m), keyA(m));
+    const uint32_t nf = __popc(__ballot_sync(kFull, f));
+    const uint32_t nhi = lo + nf * step < hi ? lo + nf * step : hi;
+    lo = nf == 0 ? lo : lo + (nf - 1) * step + 1;
+    hi = nhi;
+  }
+  return lo;
+}
+
 template <int W, int NTH>
 __device__ __forceinline__ uint32_t coop_split(const uint64_t* A, uint32_t la, const uint64_t* B, uint32_t lb,
                                                uint32_t d) {

@@ -185,8 +185,15 @@ __device__ uint64_t* cluster_merge(uint64_t* buf0, uint64_t* buf1, uint64_t* buf
     const uint32_t d0 = pos0 - pb;
     auto keyA = [&](uint32_t i) { return key_at(pb + i); };
     auto keyB = [&](uint32_t i) { return key_at(pb + R + i); };
-    const uint32_t a0 = coop_split_fn<W, kT2Threads>(keyA, R, keyB, R, d0);
-    const uint32_t a1 = coop_split_fn<W, kT2Threads>(keyA, R, keyB, R, d0 + T);
+    // the two cuts of this CTA's output tile, one warp each, side by side
+    __shared__ uint32_t s_cut[2];
+    const uint32_t wid = threadIdx.x >> 5;
+    if (wid < 2) {
+      const uint32_t v = warp_split_fn<W>(keyA, R, keyB, R, d0 + wid * T);
+      if ((threadIdx.x & 31) == 0) s_cut[wid] = v;
+    }
+    __syncthreads();
+    const uint32_t a0 = s_cut[0], a1 = s_cut[1];
     const uint32_t na = a1 - a0, b0 = d0 - a0, nb = T - na;
     // copy the two slices into buf1 (keys [0, na) from A, [na, T) from B)
     for (uint32_t e = t; e < T * W; e += kT2Threads) {
