@@ -137,10 +137,20 @@ __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t
     }
     return;
   }
-  const uint32_t a0 = (carry.seg == si && carry.ps == ps && carry.d1 == d0)
-                          ? carry.a1
-                          : coop_split<W, kM2Threads>(A, la, B, lb, d0);
-  const uint32_t a1 = coop_split<W, kM2Threads>(A, la, B, lb, d1);
+  // the tile's two cuts, one warp each side by side (the first is the
+  // previous tile's second when the CTA just merged that tile)
+  __shared__ uint32_t s_cut[2];
+  const bool have0 = carry.seg == si && carry.ps == ps && carry.d1 == d0;
+  const uint32_t wid = threadIdx.x >> 5;
+  if (wid < 2 && !(wid == 0 && have0)) {
+    auto kA_ = [&](uint32_t i) { return kload<W>(A + (size_t)i * W); };
+    auto kB_ = [&](uint32_t i) { return kload<W>(B + (size_t)i * W); };
+    const uint32_t v = warp_split_fn<W>(kA_, la, kB_, lb, wid ? d1 : d0);
+    if ((threadIdx.x & 31) == 0) s_cut[wid] = v;
+  }
+  __syncthreads();
+  const uint32_t a0 = have0 ? carry.a1 : s_cut[0];
+  const uint32_t a1 = s_cut[1];
   carry = SplitCarry{si, d1, a1, ps};
   const uint32_t na = a1 - a0, nb = (d1 - a1) - (d0 - a0);
   const uint64_t* gA = A + (size_t)a0 * W;
