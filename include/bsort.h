@@ -67,6 +67,10 @@ typedef struct {
                                                 lanes x keys-per-thread keys leave odd-even
                                                 transposition) for buckets sorted by clusters
                                                 of 1, 2, 4 and 8 CTAs; each 2, 4 or 8
+                              k4_threads=a,b,c,d  threads per tile-sort CTA (256 or 512; 512
+                                                takes effect for launches whose keys are at
+                                                most 4 words) for the same classes: keys per
+                                                thread 2048 / (threads x key words)
                               piped_min=k       merge passes with at least k tiles per resident
                                                 CTA use the pipelined merge (1..1000000)
                               k4_runs=c         buckets too large for one cluster of 8 tiles

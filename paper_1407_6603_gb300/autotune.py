@@ -4,7 +4,8 @@ The tile sort (K4) handles a bucket with a thread-block cluster of 1, 2, 4 or
 8 CTAs depending on its size (one size class per cluster size).  Per class it
 tunes the odd-even/merge cutoff: how many lanes (2, 4 or 8) run odd-even
 transposition together before merge path takes over, i.e. runs of lanes x
-keys-per-thread keys leave the transposition stage.  For the merge passes (K5)
+keys-per-thread keys leave the transposition stage; and the keys per thread
+(CTAs of 256 or 512 threads on the same 2048-word tile).  For the merge passes (K5)
 it tunes the run length the tile sort leaves for them (clusters of 1, 2, 4 or 8
 CTAs for buckets larger than one cluster of 8 tiles) and the threshold, in
 tiles per resident CTA, above which a pass is pipelined (cut kernel, then
@@ -36,6 +37,7 @@ LANES = (2, 4, 8)
 PIPED = (1, 2, 4, 8)
 RUNS = (8, 4, 2, 1)
 RUNS_SMALL = (8, 16)
+THREADS = ("256,256,256,256", "512,512,512,256", "512,512,512,512")
 DEFAULT_OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_table.txt")
 
 
@@ -110,25 +112,34 @@ def tune(reps: int = 5, log=print) -> str:
         span_of[lanes] = span / reps
         log(f"  lanes {lanes}: {span_of[lanes]:9.3f} ms per round (whole calls)")
     lanes = min(span_of, key=lambda k: (span_of[k], k != best))
+    # 2b. keys per thread: tile-sort CTAs of 256 threads (8 / W keys each) or
+    #     512 (4 / W), per class, on whole calls
+    threads_of = {}
+    for th in THREADS:
+        _, span = _time(f"k4_lanes={lanes} k4_threads={th}", sets, reps)
+        threads_of[th] = span / reps
+        log(f"  tile-sort CTA sizes {th}: {threads_of[th]:9.3f} ms per round (whole calls)")
+    threads = min(threads_of, key=lambda k: (threads_of[k], k != THREADS[0]))
     # 3. the runs the tile sort leaves for the merge passes (clusters of
     #    k4_runs CTAs) for buckets larger than one cluster of 8 tiles
     runs_of = {}
     for r in RUNS:
-        _, span = _time(f"k4_lanes={lanes} k4_runs={r}", sets, reps)
+        _, span = _time(f"k4_lanes={lanes} k4_threads={threads} k4_runs={r}", sets, reps)
         runs_of[r] = span / reps
         log(f"  runs of {r} tiles before the merge passes: {runs_of[r]:9.3f} ms per round (whole calls)")
     runs = min(RUNS, key=lambda r: (runs_of[r], -r))
     # 3b. the run length when the merges are too small to pipeline
     small_of = {}
     for r in RUNS_SMALL:
-        _, span = _time(f"k4_lanes={lanes} k4_runs={runs} k4_runs_small={r}", sets, reps)
+        _, span = _time(f"k4_lanes={lanes} k4_threads={threads} k4_runs={runs} k4_runs_small={r}", sets, reps)
         small_of[r] = span / reps
         log(f"  runs of {r} tiles before small merges: {small_of[r]:9.3f} ms per round (whole calls)")
     runs_small = min(RUNS_SMALL, key=lambda r: (small_of[r], r))
     # 4. the merge threshold
     piped_of = {}
     for p in PIPED:
-        _, span = _time(f"k4_lanes={lanes} k4_runs={runs} k4_runs_small={runs_small} piped_min={p}", sets, reps)
+        _, span = _time(f"k4_lanes={lanes} k4_threads={threads} k4_runs={runs} k4_runs_small={runs_small} "
+                        f"piped_min={p}", sets, reps)
         piped_of[p] = span / reps
         log(f"  merge threshold {p} tiles per CTA: {piped_of[p]:9.3f} ms per round (whole calls)")
     piped = min(PIPED, key=lambda p: (piped_of[p], p))
@@ -143,7 +154,10 @@ def tune(reps: int = 5, log=print) -> str:
                  + "  ".join(f"{r}: {v:.3f}" for r, v in runs_of.items()))
     lines.append("# merge threshold, whole calls, ms per round: "
                  + "  ".join(f"{p}: {v:.3f}" for p, v in piped_of.items()))
+    lines.append("# tile-sort CTA sizes, whole calls, ms per round: "
+                 + "  ".join(f"{k}: {v:.3f}" for k, v in threads_of.items()))
     lines.append(f"k4_lanes={lanes}")
+    lines.append(f"k4_threads={threads}")
     lines.append("# runs before small merges, whole calls, ms per round: "
                  + "  ".join(f"{r}: {v:.3f}" for r, v in small_of.items()))
     lines.append(f"k4_runs={runs}")

@@ -50,6 +50,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // built-in values are what the autotuner (autotune.py) picked on a GB300.
 struct Tune {
   int k4_lanes[4] = {2, 2, 4, 2};  // clusters of 1, 2, 4, 8 CTAs
+  int k4_threads[4] = {256, 256, 256, 256};  // CTA size for the same classes (512: keys of up to 4 words)
   uint32_t piped_min = 1;
   int k4_streams = 1;  // 1: the tile sorts of the smaller classes run on side streams
   int k4_runs = 1;     // cluster size (runs of that many tiles) for buckets that need pipelined merge passes
@@ -103,6 +104,12 @@ bool parse_tune(const char* text, Tune& t) {
     } else if (key == "k4_streams") {
       if (nums.size() != 1 || nums[0] > 1) return false;
       t.k4_streams = (int)nums[0];
+    } else if (key == "k4_threads") {
+      if (nums.size() != 4) return false;
+      for (int q = 0; q < 4; ++q) {
+        if (nums[q] != 256 && nums[q] != 512) return false;
+        t.k4_threads[q] = (int)nums[q];
+      }
     } else if (key == "piped_min") {
       if (nums.size() != 1 || nums[0] < 1 || nums[0] > 1000000) return false;
       t.piped_min = (uint32_t)nums[0];
@@ -668,8 +675,8 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     }
     Trace tr_(c, sx, kTileSort, l.key_bytes, l.levels);
     tr_.variant = (uint32_t)l.cluster;
-    const int lanes = c->tune.k4_lanes[l.cluster == 1 ? 0 : l.cluster == 2 ? 1 : l.cluster == 4 ? 2 : 3];  // 16 as 8
-    CK(tr_.done(launch_tile_sort2(l.cluster, lanes, d_segs, l.sbeg, l.send, l.supertiles, c->sm_count, l.max_w, kA,
+    const int cls = l.cluster == 1 ? 0 : l.cluster == 2 ? 1 : l.cluster == 4 ? 2 : 3;  // 16 as 8
+    CK(tr_.done(launch_tile_sort2(l.cluster, c->tune.k4_lanes[cls], c->tune.k4_threads[cls], d_segs, l.sbeg, l.send, l.supertiles, c->sm_count, l.max_w, kA,
                                   eo, d_sticky, c->cfg.wait_limit, sx)),
        "K4 tile_sort");
   }

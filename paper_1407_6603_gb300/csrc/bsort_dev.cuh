@@ -327,18 +327,19 @@ cudaError_t launch_merge_pass(int W, const Segment* segs, uint32_t sbeg, uint32_
                               uint32_t grid, uint32_t pass, const uint64_t* src, uint64_t* dst, cudaStream_t st);
 cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, uint64_t* keys, EmitOut eo,
                              cudaStream_t st);
-// K4 with clusters of `cluster` CTAs and `lanes` (2, 4 or 8) lanes per
+// K4 with clusters of `cluster` CTAs of `threads` (256, or 512 when no key
+// of the launch is wider than 4 words) and `lanes` (2, 4 or 8) lanes per
 // odd-even transposition group.
-cudaError_t launch_tile_sort2(int cluster, int lanes, const Segment* segs, uint32_t sbeg, uint32_t send,
+cudaError_t launch_tile_sort2(int cluster, int lanes, int threads, const Segment* segs, uint32_t sbeg, uint32_t send,
                               uint32_t supertiles, int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
                               uint64_t wait_limit, cudaStream_t st);
-cudaError_t launch_tile_sort2_g2(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
+cudaError_t launch_tile_sort2_g2(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                                  int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
                                  uint64_t wait_limit, cudaStream_t st);
-cudaError_t launch_tile_sort2_g4(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
+cudaError_t launch_tile_sort2_g4(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                                  int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
                                  uint64_t wait_limit, cudaStream_t st);
-cudaError_t launch_tile_sort2_g8(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
+cudaError_t launch_tile_sort2_g8(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                                  int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
                                  uint64_t wait_limit, cudaStream_t st);
 // Merge passes pass0 .. pass0 + npass - 1 (keys between kA and kB, pass p

@@ -7,7 +7,7 @@
 // the paper's method, the sort of each length bucket into ASCII order
 // (Section II; Section III step 4).
 //
-// K4 (k_tile_sort2<CL, G>) sorts "supertiles".  One CTA of 256 threads holds
+// K4 (k_tile_sort2<CL, G, NTH>) sorts "supertiles".  One CTA of 256 threads holds
 // a tile of 2048 u64 words (2048 / W keys) in shared memory, staged by a TMA
 // bulk copy, and sorts it with the bubble sort's compare-exchange in its
 // parallel form, odd-even transposition:
@@ -34,7 +34,6 @@ namespace cg = cooperative_groups;
 namespace bsort {
 namespace {
 
-constexpr int kT2Threads = 256;
 // CTAs per SM that K4's register budget aims for (a build-time tuning
 // constant).  The lanes per odd-even transposition group, G (the odd-even /
 // merge cutoff: runs of G * KPT keys leave the transposition stage, merges
@@ -48,9 +47,11 @@ template <int W>
 __host__ __device__ constexpr int kpt2() {
   return W >= 8 ? 1 : 8 / W;
 }
-template <int W>
-__host__ __device__ constexpr uint32_t tile_words2() {
-  return (uint32_t)kT2Threads * kpt2<W>() * W;  // 2048 u64 words, 4096 for W = 16
+// Keys per thread when NTH threads share a tile of 2048 u64 words (0: the
+// tile is too small for them, keys of W words take NTH / 256 x more).
+template <int W, int NTH>
+__host__ __device__ constexpr int kptn() {
+  return (int)(2048u / (uint32_t)(NTH * W));
 }
 
 constexpr int kM2Threads = 256;
@@ -118,16 +119,16 @@ __device__ __forceinline__ void merge_run_buf(const uint64_t* buf, uint32_t offA
 
 // Sorts the tile staged (unpadded, by TMA) in buf; the sorted tile is left in
 // buf in the padded layout.
-template <int W, int G>
+template <int W, int G, int NTH>
 __device__ void cta_sort(uint64_t* buf) {
-  constexpr int KPT = kpt2<W>();
-  constexpr uint32_t T = kT2Threads * KPT;
+  constexpr int KPT = kptn<W, NTH>();
+  constexpr uint32_t T = NTH * KPT;
   const int t = threadIdx.x;
   Key<W> k[KPT];
   // The tile is unsorted, so any assignment of keys to threads will do:
   // take them striped, which reads consecutive words across the warp.
 #pragma unroll
-  for (int i = 0; i < KPT; ++i) k[i] = kload<W>(buf + (size_t)(t + i * kT2Threads) * W);
+  for (int i = 0; i < KPT; ++i) k[i] = kload<W>(buf + (size_t)(t + i * NTH) * W);
   oets_registers<W, KPT>(k);
   oets_lanes<W, KPT, G>(k);
 #pragma unroll 1
@@ -166,10 +167,10 @@ __device__ void cta_sort(uint64_t* buf) {
 // alternate between buf0 and buf2, so one cluster barrier per level suffices:
 // a level overwrites the buffer its peers read two levels back.  buf1 takes
 // the slices this CTA merges.
-template <int W, int CL>
+template <int W, int CL, int NTH>
 __device__ uint64_t* cluster_merge(uint64_t* buf0, uint64_t* buf1, uint64_t* buf2, uint32_t r) {
-  constexpr int KPT = kpt2<W>();
-  constexpr uint32_t T = kT2Threads * KPT;
+  constexpr int KPT = kptn<W, NTH>();
+  constexpr uint32_t T = NTH * KPT;
   cg::cluster_group cluster = cg::this_cluster();
   const int t = threadIdx.x;
   uint64_t* cur = buf0;  // this level's input tile (every CTA uses the same buffer)
@@ -196,7 +197,7 @@ __device__ uint64_t* cluster_merge(uint64_t* buf0, uint64_t* buf1, uint64_t* buf
     const uint32_t a0 = s_cut[0], a1 = s_cut[1];
     const uint32_t na = a1 - a0, b0 = d0 - a0, nb = T - na;
     // copy the two slices into buf1 (keys [0, na) from A, [na, T) from B)
-    for (uint32_t e = t; e < T * W; e += kT2Threads) {
+    for (uint32_t e = t; e < T * W; e += NTH) {
       const uint32_t kk = e / W, j = e % W;
       const uint32_t src = kk < na ? pb + a0 + kk : pb + R + b0 + (kk - na);
       buf1[padw(e)] = cluster.map_shared_rank(pkey<W>(cur, src % T), src / T)[j];
@@ -218,12 +219,12 @@ __device__ uint64_t* cluster_merge(uint64_t* buf0, uint64_t* buf1, uint64_t* buf
   return cur;
 }
 
-template <int W, int CL, int G>
+template <int W, int CL, int G, int NTH>
 __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint64_t* keys, uint64_t* buf0,
                                uint64_t* buf1, uint64_t* buf2, uint64_t* bar, uint32_t& phase, const EmitOut& eo,
                                Meta* meta, uint64_t wait_limit) {
-  constexpr int KPT = kpt2<W>();
-  constexpr uint32_t T = kT2Threads * KPT;
+  constexpr int KPT = kptn<W, NTH>();
+  constexpr uint32_t T = NTH * KPT;
   constexpr uint32_t TW = T * W;
   const int t = threadIdx.x;
   const uint64_t j0 = (uint64_t)(st - sg.stile0) * CL * T + (uint64_t)r * T;
@@ -236,7 +237,7 @@ __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint6
     mbar_arrive_expect_tx(bar, tma_bytes);
     if (tma_bytes) tma_load_1d(buf0, g, tma_bytes, bar);
   }
-  for (uint32_t e = tma_bytes / 8 + t; e < TW; e += kT2Threads)
+  for (uint32_t e = tma_bytes / 8 + t; e < TW; e += NTH)
     buf0[e] = e < cnt * W ? g[e] : ~0ull;  // odd tail word, then +inf padding
   const bool ok = mbar_wait_bounded(bar, phase, wait_limit);
   phase ^= 1u;
@@ -249,19 +250,19 @@ __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint6
     }
     __syncthreads();
   }
-  cta_sort<W, G>(buf0);
+  cta_sort<W, G, NTH>(buf0);
   const uint64_t* res = buf0;
-  if constexpr (CL > 1) res = cluster_merge<W, CL>(buf0, buf1, buf2, r);
+  if constexpr (CL > 1) res = cluster_merge<W, CL, NTH>(buf0, buf1, buf2, r);
   if (sg.passes == 0) {  // the bucket is sorted: its words go straight out
-    emit_tile<kT2Threads>(sg, (uint32_t)j0, cnt, [&](uint32_t j, uint32_t q) { return res[padw(j * W + q)]; }, eo);
+    emit_tile<NTH>(sg, (uint32_t)j0, cnt, [&](uint32_t j, uint32_t q) { return res[padw(j * W + q)]; }, eo);
   } else {  // a run of CL tiles for K5
-    for (uint32_t e = t; e < cnt * W; e += kT2Threads) g[e] = res[padw(e)];
+    for (uint32_t e = t; e < cnt * W; e += NTH) g[e] = res[padw(e)];
   }
   __syncthreads();
 }
 
-template <int CL, int G>
-__global__ void __launch_bounds__(kT2Threads, BSORT_K4_MIN_CTAS) k_tile_sort2(const Segment* __restrict__ segs, uint32_t sbeg,
+template <int CL, int G, int NTH>
+__global__ void __launch_bounds__(NTH, BSORT_K4_MIN_CTAS * 256 / NTH) k_tile_sort2(const Segment* __restrict__ segs, uint32_t sbeg,
                                                            uint32_t send, uint32_t nst, uint32_t buf_words,
                                                            uint64_t* keys, EmitOut eo, Meta* meta,
                                                            uint64_t wait_limit) {
@@ -292,15 +293,21 @@ __global__ void __launch_bounds__(kT2Threads, BSORT_K4_MIN_CTAS) k_tile_sort2(co
     const Segment sg = segs[s_seg];
     __syncthreads();
     switch (width_of_len(sg.L)) {
-      case 1: sort_supertile<1, CL, G>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
-      case 2: sort_supertile<2, CL, G>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
-      case 4: sort_supertile<4, CL, G>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
-      default: sort_supertile<8, CL, G>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
+      case 1: sort_supertile<1, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
+      case 2: sort_supertile<2, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
+      case 4:
+        if constexpr (kptn<4, NTH>() >= 1)
+          sort_supertile<4, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit);
+        break;
+      default:  // (launches with 8-word keys use 256 threads)
+        if constexpr (kptn<8, NTH>() >= 1)
+          sort_supertile<8, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit);
+        break;
     }
   }
 }
 
-template <int CL, int G>
+template <int CL, int G, int NTH>
 cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t nst, int max_grid,
                           int max_width, uint64_t* keys, const EmitOut& eo, Meta* meta, uint64_t wait_limit,
                           cudaStream_t st) {
@@ -310,16 +317,16 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
   static int attr_done[64];
   static int clusters_cached[64];
   cudaError_t e = once_per_device(attr_done, [&] {
-    cudaError_t r = cudaFuncSetAttribute(k_tile_sort2<CL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t r = cudaFuncSetAttribute(k_tile_sort2<CL, G, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (r == cudaSuccess)  // shared memory, not L1, limits how many CTAs fit
-      r = cudaFuncSetAttribute(k_tile_sort2<CL, G>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      r = cudaFuncSetAttribute(k_tile_sort2<CL, G, NTH>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (r == cudaSuccess && CL > 8)  // clusters of 16 are beyond the portable 8
-      r = cudaFuncSetAttribute(k_tile_sort2<CL, G>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      r = cudaFuncSetAttribute(k_tile_sort2<CL, G, NTH>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return r;
   });
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.blockDim = dim3(kT2Threads, 1, 1);
+  cfg.blockDim = dim3(NTH, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -334,7 +341,7 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
   int clusters = (dev >= 0 && dev < 64) ? clusters_cached[dev] : 0;
   if (clusters <= 0) {
     cfg.gridDim = dim3(CL, 1, 1);
-    e = cudaOccupancyMaxActiveClusters(&clusters, k_tile_sort2<CL, G>, &cfg);
+    e = cudaOccupancyMaxActiveClusters(&clusters, k_tile_sort2<CL, G, NTH>, &cfg);
     if (e != cudaSuccess || clusters <= 0) {
       cudaGetLastError();
       clusters = max(1, max_grid / CL);
@@ -343,23 +350,34 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
   }
   const uint32_t ncl = nst < (uint32_t)clusters * 2u ? nst : (uint32_t)clusters * 2u;
   cfg.gridDim = dim3(ncl * CL, 1, 1);
-  return cudaLaunchKernelEx(&cfg, k_tile_sort2<CL, G>, segs, sbeg, send, nst, buf_words, keys, eo, meta, wait_limit);
+  return cudaLaunchKernelEx(&cfg, k_tile_sort2<CL, G, NTH>, segs, sbeg, send, nst, buf_words, keys, eo, meta, wait_limit);
 }
 
-// All cluster sizes for one lane count G (each K4 translation unit
-// instantiates one G).
-template <int G>
-cudaError_t tile_sort2_lanes(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
-                             int max_grid, int max_width, uint64_t* keys, const EmitOut& eo, Meta* meta,
-                             uint64_t wait_limit, cudaStream_t st) {
+// All cluster sizes and CTA sizes for one lane count G (each K4 translation
+// unit instantiates one G).
+template <int G, int NTH>
+cudaError_t tile_sort2_cls(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
+                           int max_grid, int max_width, uint64_t* keys, const EmitOut& eo, Meta* meta,
+                           uint64_t wait_limit, cudaStream_t st) {
   switch (cluster) {
-    case 1: return tile_sort2_cl<1, G>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 2: return tile_sort2_cl<2, G>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 4: return tile_sort2_cl<4, G>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 8: return tile_sort2_cl<8, G>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 16: return tile_sort2_cl<16, G>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 1: return tile_sort2_cl<1, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 2: return tile_sort2_cl<2, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 4: return tile_sort2_cl<4, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 8: return tile_sort2_cl<8, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 16: return tile_sort2_cl<16, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <int G>
+cudaError_t tile_sort2_lanes(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send,
+                             uint32_t supertiles, int max_grid, int max_width, uint64_t* keys, const EmitOut& eo,
+                             Meta* meta, uint64_t wait_limit, cudaStream_t st) {
+  if (threads == 512 && max_width <= 4)
+    return tile_sort2_cls<G, 512>(cluster, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta,
+                                  wait_limit, st);
+  return tile_sort2_cls<G, 256>(cluster, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta,
+                                wait_limit, st);
 }
 
 }  // namespace

@@ -96,6 +96,7 @@ def test_config_default_has_builtin_tuning(libpath):
     "k4_runs=3",               # runs of 1, 2, 4 or 8 tiles
     "k4_streams=2",
     "k4_runs_small=4",         # 8 or 16
+    "k4_threads=128,256,256,256",  # 256 or 512
 ])
 def test_bad_tune_table_is_rejected_before_any_device_call(libpath, table):
     import paper_1407_6603_gb300 as bs
