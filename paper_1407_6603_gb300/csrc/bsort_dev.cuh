@@ -5,7 +5,7 @@
 //                     stripped letter stream S, the S offset of every word
 //                     start, the per-document length histograms and bases
 //   -- host reads the histograms and lays out one segment per (doc, length)
-//   K3  scatter       per 1024-word block: each word packed into a big-endian
+//   K3  scatter       per 2048-word block: each word packed into a big-endian
 //                     key of W u64 words, written to its segment
 //   K4  tile_sort     per tile: odd-even transposition sort, then merges
 //                     through distributed shared memory inside a cluster
@@ -23,7 +23,7 @@ constexpr int kMaxLen = 255;                // longest word the key layout holds
 constexpr int kTokThreads = 256;            // K1 CTA size
 constexpr int kTokSeg = 64;                 // bytes per K1 thread
 constexpr int kChunk = kTokThreads * kTokSeg;  // bytes per K1 chunk (16 KiB)
-constexpr int kWordBlock = 1024;            // words per K3 work item
+constexpr int kWordBlock = 2048;            // words per K3 work item
 constexpr int kWordThreads = 256;
 constexpr int kSortThreads = 256;           // K4/K5/K6 CTA size
 constexpr int kNumClasses = 6;              // key widths W = 1, 2, 4, 8, 16, 32 u64 words

@@ -5,7 +5,7 @@
 // 3-D char array, one plane per length (Section III "Approach Second"); here
 // each (document, length) bucket is a contiguous array of packed keys, W u64
 // words per key, big-endian so that integer order is ASCII order.  A CTA
-// takes 1024 words of one document, ranks them per length in shared memory
+// takes 2048 words of one document, ranks them per length in shared memory
 // and reserves each length's slots with one atomic per length, so the slots
 // of a bucket come out in no fixed order (the sort that follows makes the
 // result unique anyway).
@@ -21,9 +21,9 @@ namespace bsort {
 namespace {
 
 constexpr int kWordsPerThread = kWordBlock / kWordThreads;
-// Bytes of letters a CTA stages in shared memory (1024 words of up to 15
+// Bytes of letters a CTA stages in shared memory (2048 words of up to 16
 // letters on average); longer ranges are read from global memory.
-constexpr uint32_t kLetterStage = 16384;
+constexpr uint32_t kLetterStage = 32768;
 
 __global__ void __launch_bounds__(kWordThreads) k_scatter(
     const uint32_t* __restrict__ starts, const uint8_t* __restrict__ letters, const uint32_t* __restrict__ doc_wbase,

@@ -14,7 +14,7 @@
 // (carried through the scan as "last start, and its document"), so it emits
 // the length of the previous word; the last word of all is emitted by the
 // CTA that finishes last.  That CTA also derives each document's word and
-// letter bases from the chunk prefixes and the prefix of 1024-word blocks.
+// letter bases from the chunk prefixes and the prefix of 2048-word blocks.
 #include <cstddef>
 
 #include "bsort_dev.cuh"
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
     doc_lbase[d] = b.letters;
   }
   __syncthreads();
-  // prefix over documents of their 1024-word blocks (work items of K3)
+  // prefix over documents of their 2048-word blocks (work items of K3)
   __shared__ uint32_t warp_sum[kTokThreads / 32];
   __shared__ uint32_t s_run;
   if (t == 0) s_run = 0;
