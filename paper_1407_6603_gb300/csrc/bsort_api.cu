@@ -124,13 +124,14 @@ bool parse_tune(const char* text, Tune& t) {
 // The meta region: what K1 leaves for the host (read back in one copy of
 // `total` bytes), then K1's look-back scratch; one memset clears both.
 struct MetaLayout {
-  size_t meta = 0, wbase = 0, lbase = 0, item0 = 0, hist = 0, total = 0, scratch = 0, cleared = 0;
+  size_t meta = 0, wbase = 0, lbase = 0, item0 = 0, maxlen = 0, hist = 0, total = 0, scratch = 0, cleared = 0;
   void set(uint32_t ndocs, uint32_t chunks) {
     meta = 0;
     wbase = meta + align_up(sizeof(Meta), 128);
     lbase = wbase + align_up((ndocs + 1) * 4ull, 128);
     item0 = lbase + align_up((ndocs + 1) * 4ull, 128);
-    hist = item0 + align_up((ndocs + 1) * 4ull, 128);
+    maxlen = item0 + align_up((ndocs + 1) * 4ull, 128);
+    hist = maxlen + align_up(ndocs * 4ull, 128);
     total = hist + (size_t)ndocs * kHist * 4;
     scratch = align_up(total, 256);
     cleared = scratch + tokenize1p_scratch_bytes(chunks);
@@ -394,7 +395,8 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   // counts come back; they are added to its tag below.
   LAUNCH(kTokenize, 0,
          launch_tokenize1p(d_in, d_docs, ndocs, (uint32_t)chunks, dptr<uint8_t>(c->meta, ml.scratch),
-                           dptr<uint8_t>(c->letters), dptr<uint32_t>(c->starts), d_hist, d_wbase, d_lbase, d_item0,
+                           dptr<uint8_t>(c->letters), dptr<uint32_t>(c->starts), d_hist,
+                           dptr<uint32_t>(c->meta, ml.maxlen), d_wbase, d_lbase, d_item0,
                            d_meta, d_sticky, c->cfg.l_cap, c->cfg.wait_limit, st),
          "K1 tokenize");
   CK(cudaMemcpyAsync(c->h_meta.p, c->meta.p, ml.total, cudaMemcpyDeviceToHost, st), "read counts");
@@ -411,6 +413,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   const uint32_t* h_wbase = hptr<uint32_t>(c->h_meta, ml.wbase);
   const uint32_t* h_lbase = hptr<uint32_t>(c->h_meta, ml.lbase);
   const uint32_t* h_hist = hptr<uint32_t>(c->h_meta, ml.hist);
+  const uint32_t* h_maxlen = hptr<uint32_t>(c->h_meta, ml.maxlen);
   if (hs->err_timeout) {
     CK(cudaMemsetAsync(d_sticky, 0, sizeof(Meta), st), "clear timeout flag");
     return fail(c, BSORT_E_TIMEOUT, "a bounded device wait ran out in an earlier call on this context");
@@ -450,7 +453,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     if (c->doc_status[d] != BSORT_OK) continue;
     const uint32_t* h = h_hist + (size_t)d * kHist;
     uint32_t word_before = h_wbase[d] + d, byte_before = h_lbase[d];
-    for (uint32_t L = 1; L < (uint32_t)kHist; ++L) {
+    for (uint32_t L = 1, Lmax = std::min(h_maxlen[d], (uint32_t)kHist - 1); L <= Lmax; ++L) {
       const uint32_t n = h[L];
       if (n) {
         Segment sg{};
@@ -794,11 +797,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
 void fill_scalars(const bsort_ctx* c, uint32_t d, bsort_result* r) {
   const uint32_t* h_wbase = hptr<uint32_t>(c->h_meta, c->ml.wbase);
   const uint32_t* h_lbase = hptr<uint32_t>(c->h_meta, c->ml.lbase);
-  const uint32_t* h = hptr<uint32_t>(c->h_meta, c->ml.hist) + (size_t)d * kHist;
-  uint32_t max_len = 0;
-  for (uint32_t L = 1; L < (uint32_t)kHist; ++L)
-    if (h[L]) max_len = L;
-  r->max_len = max_len;
+  r->max_len = hptr<uint32_t>(c->h_meta, c->ml.maxlen)[d];
   r->n_words = h_wbase[d + 1] - h_wbase[d];
   r->stream_bytes = h_lbase[d + 1] - h_lbase[d];
   r->status = c->doc_status[d];

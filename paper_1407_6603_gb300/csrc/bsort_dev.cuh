@@ -315,7 +315,7 @@ inline cudaError_t once_per_device(int (&done)[64], F set) {
 size_t tokenize1p_scratch_bytes(uint32_t nchunks);
 cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
                               uint8_t* scratch, uint8_t* letters, uint32_t* starts, uint32_t* hist,
-                              uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
+                              uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
                               Meta* sticky, uint32_t l_cap, uint64_t wait_limit, cudaStream_t st);
 cudaError_t launch_scatter(const uint32_t* starts, const uint8_t* letters, const uint32_t* doc_wbase,
                            const uint32_t* doc_lbase, const uint32_t* doc_item0, uint32_t ndocs, uint32_t items,

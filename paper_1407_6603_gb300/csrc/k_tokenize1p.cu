@@ -103,25 +103,24 @@ __device__ __forceinline__ void st_acc(TokAcc* p, const TokAcc& v) {
   __stcg(q + 4, v.ldoc);
 }
 
-// Adds one word length to a document's histogram (bin 0 counts words longer
-// than l_cap, which make the document fail).
-__device__ __forceinline__ void count_length(uint32_t L, uint32_t doc, uint32_t my_doc, uint32_t l_cap,
-                                             uint32_t* h_local, uint32_t* hist, Meta* meta) {
+// Adds the last word of the input to its document's histogram (bin 0 counts
+// words longer than l_cap, which make the document fail) and to the
+// document's longest length.
+__device__ __forceinline__ void count_last_word(uint32_t L, uint32_t doc, uint32_t l_cap, uint32_t* hist,
+                                                uint32_t* doc_maxlen, Meta* meta) {
   uint32_t bin = L;
   if (L > l_cap || L > (uint32_t)kMaxLen) {
     bin = 0;
     atomicAdd(&meta->err_long, 1u);
   }
-  if (doc == my_doc)
-    atomicAdd(&h_local[bin], 1u);
-  else
-    atomicAdd(&hist[(size_t)doc * kHist + bin], 1u);
+  atomicAdd(&hist[(size_t)doc * kHist + bin], 1u);
+  if (bin) atomicMax(&doc_maxlen[doc], bin);
 }
 
 __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
     const uint8_t* __restrict__ in, const DocDesc* __restrict__ docs, uint32_t ndocs, uint32_t nchunks,
     uint8_t* scratch, uint8_t* __restrict__ letters_out, uint32_t* __restrict__ starts, uint32_t* hist,
-    uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta, Meta* sticky, uint32_t l_cap,
+    uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta, Meta* sticky, uint32_t l_cap,
     uint64_t wait_limit) {
   K1Scratch* s = reinterpret_cast<K1Scratch*>(scratch);
   __shared__ uint4 buf[kChunk / 16 + 1];  // the chunk, then its letters (with up to 15 bytes of lead)
@@ -322,14 +321,21 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
         bin = 0;
         atomicAdd(&meta->err_long, 1u);
       }
-      if (pdoc != d)
-        atomicAdd(&hist[(size_t)pdoc * kHist + bin], 1u);  // a word of an earlier document
-      else
+      if (pdoc != d) {  // a word of an earlier document
+        atomicAdd(&hist[(size_t)pdoc * kHist + bin], 1u);
+        if (bin) atomicMax(&doc_maxlen[pdoc], bin);
+      } else {
         atomicAdd(&h_local[bin], 1u);
+      }
     }
     __syncthreads();
-    for (int i = t; i < kHist; i += kTokThreads)
-      if (h_local[i]) atomicAdd(&hist[(size_t)d * kHist + i], h_local[i]);
+    // the histogram and the document's longest length so far (one atomic
+    // per warp that holds a non-empty bin)
+    static_assert(kHist == kTokThreads, "one bin per thread");
+    const uint32_t hv = h_local[t];
+    if (hv) atomicAdd(&hist[(size_t)d * kHist + t], hv);
+    const uint32_t mx = __reduce_max_sync(kFull, hv && t ? (uint32_t)t : 0u);
+    if ((t & 31) == 0 && mx) atomicMax(&doc_maxlen[d], mx);
   }
   // the CTA that finishes last derives the totals and the document bases
   __syncthreads();
@@ -346,7 +352,7 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
     meta->n_total = all.words;
     meta->s_total = all.letters;
     starts[all.words] = all.letters;  // the last word ends at the end of S
-    if (all.fl & kHas) count_length(all.letters - all.last, all.ldoc, ~0u, l_cap, h_local, hist, meta);
+    if (all.fl & kHas) count_last_word(all.letters - all.last, all.ldoc, l_cap, hist, doc_maxlen, meta);
     doc_wbase[ndocs] = all.words;
     doc_lbase[ndocs] = all.letters;
   }
@@ -395,7 +401,7 @@ size_t tokenize1p_scratch_bytes(uint32_t nchunks) {
 
 cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
                               uint8_t* scratch, uint8_t* letters, uint32_t* starts, uint32_t* hist,
-                              uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
+                              uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
                               Meta* sticky, uint32_t l_cap, uint64_t wait_limit, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   const size_t smem = (size_t)(kChunk / 2) * sizeof(uint32_t);
@@ -405,7 +411,7 @@ cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t n
   });
   if (e != cudaSuccess) return e;
   k_tokenize1p<<<nchunks ? nchunks : 1u, kTokThreads, smem, st>>>(in, docs, ndocs, nchunks, scratch, letters, starts,
-                                                              hist, doc_wbase, doc_lbase, doc_item0, meta, sticky,
+                                                              hist, doc_maxlen, doc_wbase, doc_lbase, doc_item0, meta, sticky,
                                                               l_cap, wait_limit);
   return cudaGetLastError();
 }
