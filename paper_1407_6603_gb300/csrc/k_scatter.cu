@@ -8,7 +8,8 @@
 // takes 2048 words of one document, ranks them per length in shared memory
 // and reserves each length's slots with one atomic per length, so the slots
 // of a bucket come out in no fixed order (the sort that follows makes the
-// result unique anyway).
+// result unique anyway).  It then packs the words in (length, rank) order,
+// so that neighbouring lanes write neighbouring slots of one bucket.
 //
 // The sort kernels write each bucket's words as soon as its keys are final
 // (emit_tile in bsort_dev.cuh); K3 also writes the per-length counts and each
@@ -21,9 +22,42 @@ namespace bsort {
 namespace {
 
 constexpr int kWordsPerThread = kWordBlock / kWordThreads;
-// Bytes of letters a CTA stages in shared memory (2048 words of up to 16
-// letters on average); longer ranges are read from global memory.
-constexpr uint32_t kLetterStage = 32768;
+// Bytes of letters a CTA stages in shared memory (2048 words of up to 14
+// letters on average); longer ranges are read from global memory.  With it a
+// CTA holds about 45 KB of shared memory, so five fit on an SM.
+constexpr uint32_t kLetterStage = 28672;
+
+// Packs one word into its key.  Key word q of a word that starts at S offset
+// s0 holds its letters 8q..8q+7, first letter in the most significant byte.
+// With the letters read as aligned 32-bit words u[] (u[0] at S offset
+// `base`), bytes p..p+3 (p = s0 + 8q) lie in u[k], u[k+1] for
+// k = (p - base) / 4, and one byte_perm takes them from there already
+// reversed (selector nibbles s+3, s+2, s+1, s for s = p % 4).  Bytes past
+// the word's last letter are cleared; key words past it are zero.  Reads
+// reach at most 11 bytes past the word's last letter.
+__device__ __forceinline__ void pack_word(const uint32_t* __restrict__ u, uint32_t base, uint32_t s0, uint32_t L,
+                                          uint64_t* __restrict__ out) {
+  const int W = width_of_len(L);
+  const uint32_t sel = 0x0123u + (s0 & 3u) * 0x1111u;
+  const uint32_t* src = u + ((s0 - base) >> 2);
+  uint32_t a = src[0];
+  for (int q = 0; q < W; ++q) {
+    uint64_t v = 0;
+    const uint32_t b0 = (uint32_t)q * 8;
+    if (b0 < L) {
+      const uint32_t b = src[2 * q + 1], c = src[2 * q + 2];
+      uint32_t hi = __byte_perm(a, b, sel), lo = __byte_perm(b, c, sel);
+      a = c;
+      const uint32_t valid = L - b0;
+      if (valid < 8) {
+        hi &= ~0u << (8 * (4 - min(valid, 4u)));
+        lo = valid > 4 ? lo & (~0u << (8 * (8 - valid))) : 0u;
+      }
+      v = ((uint64_t)hi << 32) | lo;
+    }
+    out[q] = v;
+  }
+}
 
 __global__ void __launch_bounds__(kWordThreads) k_scatter(
     const uint32_t* __restrict__ starts, const uint8_t* __restrict__ letters, const uint32_t* __restrict__ doc_wbase,
@@ -42,6 +76,8 @@ __global__ void __launch_bounds__(kWordThreads) k_scatter(
   __shared__ uint64_t s_out[kHist];  // word offset in `keys` of the CTA's first slot of each length
   __shared__ uint32_t s_lookup[kHist];
   __shared__ uint32_t s_st[kWordBlock + 1];
+  __shared__ uint16_t s_idx[kWordBlock];  // the item's words (index in the item) by (length, rank)
+  __shared__ uint32_t s_wtot[kWordThreads / 32];
   __shared__ __align__(16) uint64_t s_let[kLetterStage / 8 + 2];
   __shared__ uint32_t s_doc;
   const int t = threadIdx.x;
@@ -81,41 +117,50 @@ __global__ void __launch_bounds__(kWordThreads) k_scatter(
       if (L) rank[k] = atomicAdd(&cnt[L], 1u);
     }
     __syncthreads();
-    // one thread per length reserves the CTA's slots in the bucket
-    for (int L = t; L < kHist; L += kWordThreads)
-      if (cnt[L]) {
-        const uint32_t si = s_lookup[L];
-        s_out[L] = segs[si].key_off + (uint64_t)atomicAdd(&cursor[si], cnt[L]) * width_of_len(L);
-      }
-    if (staged) cp_async_wait_all();
+    // thread t owns length t: it reserves the CTA's slots in the bucket of
+    // that length and takes part in the exclusive prefix over lengths of the
+    // CTA's counts, which orders the CTA's words by (length, rank)
+    static_assert(kHist == kWordThreads, "one length per thread");
+    const uint32_t c = cnt[t];
+    if (c) {
+      const uint32_t si = s_lookup[t];
+      s_out[t] = segs[si].key_off + (uint64_t)atomicAdd(&cursor[si], c) * width_of_len(t);
+    }
+    uint32_t inc = c;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+      if ((t & 31) >= off) inc += v;
+    }
+    if ((t & 31) == 31) s_wtot[t >> 5] = inc;
+    __syncthreads();
+    uint32_t before = 0, nv = 0;
+#pragma unroll
+    for (int w = 0; w < kWordThreads / 32; ++w) {
+      const uint32_t x = s_wtot[w];
+      before += w < (t >> 5) ? x : 0u;
+      nv += x;
+    }
+    cnt[t] = before + inc - c;  // now: the CTA's words of shorter lengths
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kWordsPerThread; ++k) {
-      const uint32_t L = len[k];
-      if (L == 0) continue;
-      const uint32_t s0 = s_st[t + k * kWordThreads];
-      const int W = width_of_len(L);
-      uint64_t* out = keys + s_out[L] + (size_t)rank[k] * W;
-      // the letters as aligned 8-byte loads, shifted into place, byte-swapped
-      // to big-endian and cut at L
-      const uint32_t sh = s0 & 7u;
-      const uint64_t* src =
-          staged ? s_let + ((s0 - l0) >> 3) : reinterpret_cast<const uint64_t*>(letters + (s0 & ~7u));
-      uint64_t x0 = src[0];
-      for (int q = 0; q < W; ++q) {
-        uint64_t v = 0;
-        const uint32_t b0 = (uint32_t)q * 8;
-        if (b0 < L) {
-          const uint64_t x1 = src[q + 1];
-          const uint64_t le = sh ? (x0 >> (8 * sh)) | (x1 << (64 - 8 * sh)) : x0;
-          x0 = x1;
-          v = ((uint64_t)__byte_perm((uint32_t)le, 0, 0x0123) << 32) | __byte_perm((uint32_t)(le >> 32), 0, 0x0123);
-          const uint32_t valid = L - b0;
-          if (valid < 8) v &= ~0ull << (8 * (8 - valid));
-        }
-        out[q] = v;
+    for (int k = 0; k < kWordsPerThread; ++k)
+      if (len[k]) s_idx[cnt[len[k]] + rank[k]] = (uint16_t)(t + k * kWordThreads);
+    if (staged) cp_async_wait_all();
+    __syncthreads();
+    // the keys in (length, rank) order: neighbouring lanes write neighbouring
+    // slots of one bucket, and mostly keys of one width
+    auto pack_sorted = [&](const uint32_t* u, uint32_t base) {
+      for (uint32_t j = t; j < nv; j += kWordThreads) {
+        const uint32_t i = s_idx[j];
+        const uint32_t s0 = s_st[i], L = s_st[i + 1] - s0;
+        pack_word(u, base, s0, L, keys + s_out[L] + (size_t)(j - cnt[L]) * width_of_len(L));
       }
-    }
+    };
+    if (staged)
+      pack_sorted(reinterpret_cast<const uint32_t*>(s_let), l0);
+    else
+      pack_sorted(reinterpret_cast<const uint32_t*>(letters), 0u);
     __syncthreads();
   }
 }

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kTokThreads) k_strip_onepass(const uint8_t* __
         }
       }
     }
-    buf[g] = v;
+    buf[chunk_slot(g)] = v;
   }
   __syncthreads();
   uint32_t w[16];

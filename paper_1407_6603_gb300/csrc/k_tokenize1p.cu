@@ -117,20 +117,31 @@ __device__ __forceinline__ void count_last_word(uint32_t L, uint32_t doc, uint32
   if (bin) atomicMax(&doc_maxlen[doc], bin);
 }
 
-__global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
+// Resident CTAs per SM the register budget is sized for (48 registers a
+// thread at 5; the shared memory of a CTA, about 34 KB, allows six).  A CTA
+// spends much of its time waiting at barriers (for warp 0's look-back), so
+// more resident CTAs hide more of it: on a GB300, 5 beat 4 by about 7% on
+// large inputs, and 6 (40 registers) lost on small ones.
+#ifndef BSORT_K1_MIN_CTAS
+#define BSORT_K1_MIN_CTAS 5
+#endif
+
+__global__ void __launch_bounds__(kTokThreads, BSORT_K1_MIN_CTAS) k_tokenize1p(
     const uint8_t* __restrict__ in, const DocDesc* __restrict__ docs, uint32_t ndocs, uint32_t nchunks,
     uint8_t* scratch, uint8_t* __restrict__ letters_out, uint32_t* __restrict__ starts, uint32_t* hist,
     uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta, Meta* sticky, uint32_t l_cap,
     uint64_t wait_limit) {
   K1Scratch* s = reinterpret_cast<K1Scratch*>(scratch);
   __shared__ uint4 buf[kChunk / 16 + 1];  // the chunk, then its letters (with up to 15 bytes of lead)
-  extern __shared__ uint32_t s_starts[];   // up to kChunk / 2 word starts
+  extern __shared__ uint16_t s_starts[];   // up to kChunk / 2 word starts, as letter offsets in the chunk
   __shared__ uint32_t h_local[kHist];
   __shared__ uint32_t s_c, s_doc, s_last;
   __shared__ TokAcc s_prefix;
   __shared__ uint32_t s_wlast[kTokThreads / 32];
+  __shared__ uint32_t s_sel[16];
   const int t = threadIdx.x;
   for (int i = t; i < kHist; i += kTokThreads) h_local[i] = 0;
+  compact_table_fill(s_sel);
   if (t < 32) {  // warp 0 takes the ticket and finds the chunk's document
     uint32_t c0 = 0;
     if (t == 0) c0 = atomicAdd(&s->ticket, 1u);
@@ -172,7 +183,7 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
           }
         }
       }
-      buf[g] = v;
+      buf[chunk_slot(g)] = v;
     }
     __syncthreads();
     uint32_t w[16];
@@ -275,7 +286,6 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
     const uint32_t fe = pk_flags(ex);
     const bool cin_ws = (cin.fl & kEv) && (cin.fl & kWs);
     const bool ws_before = doc_start || ((fe & kEv) ? (fe & kWs) != 0 : cin_ws);
-    const uint32_t pre_letters = cin.letters + pk_letters(ex);
     // word starts of this chunk, staged in order (they are contiguous in
     // `starts`); the chunk's first letter counts before this thread when the
     // predecessors end in whitespace
@@ -285,12 +295,12 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
       const int b = __ffsll(starts_m) - 1;
       starts_m &= starts_m - 1;
       const uint64_t below = b ? (lm & (~0ull >> (64 - b))) : 0ull;
-      s_starts[wpos++] = pre_letters + __popcll(below);
+      s_starts[wpos++] = (uint16_t)(pk_letters(ex) + __popcll(below));
     }
     // letters, staged so that stage[k] lands at global byte (cin.letters & ~15) + k
     const uint32_t lead = cin.letters & 15u;
     uint8_t* const stage = reinterpret_cast<uint8_t*>(buf);
-    stage_letters(w, lm, stage, lead + pk_letters(ex));
+    stage_letters(w, lm, stage, lead + pk_letters(ex), s_sel);
     __syncthreads();
     // letters out: bytes up to the first 16-byte boundary, 16-byte stores, bytes after the last
     {
@@ -310,11 +320,11 @@ __global__ void __launch_bounds__(kTokThreads) k_tokenize1p(
     // this chunk's starts: its own, plus its first letter when the carry
     // (ending in whitespace) makes that a start
     const uint32_t nw = acc_combine(cin, total).words - cin.words;
-    for (uint32_t i = t; i < nw; i += kTokThreads) starts[cin.words + i] = s_starts[i];
+    for (uint32_t i = t; i < nw; i += kTokThreads) starts[cin.words + i] = cin.letters + s_starts[i];
     const bool carry_word = (cin.fl & kHas) != 0;
     for (uint32_t i = t; i < nw; i += kTokThreads) {
       if (i == 0 && !carry_word) continue;
-      const uint32_t L = s_starts[i] - (i > 0 ? s_starts[i - 1] : cin.last);
+      const uint32_t L = i > 0 ? (uint32_t)s_starts[i] - s_starts[i - 1] : cin.letters + s_starts[0] - cin.last;
       const uint32_t pdoc = i > 0 ? d : cin.ldoc;
       uint32_t bin = L;
       if (L > l_cap || L > (uint32_t)kMaxLen) {
@@ -404,7 +414,7 @@ cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t n
                               uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
                               Meta* sticky, uint32_t l_cap, uint64_t wait_limit, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
-  const size_t smem = (size_t)(kChunk / 2) * sizeof(uint32_t);
+  const size_t smem = (size_t)(kChunk / 2) * sizeof(uint16_t);
   static int attr_done[64];
   e = once_per_device(attr_done, [&] {
     return cudaFuncSetAttribute(k_tokenize1p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -2,7 +2,7 @@
 // kernels of k_tokenize1p.cu (the main path) and k_strip_noalloc.cu.
 //
 // Each thread owns 64 consecutive bytes.  It classifies them four at a time
-// with byte-SIMD compares into two 64-bit masks (letters, whitespace), and
+// (swar.h) into two 64-bit masks (letters, whitespace), and
 // finds the word starts among its letters with one addition: adding
 // (whitespace << 1) to the mask of transparent bytes (neither letter nor
 // whitespace) carries each whitespace bit across the transparent run after it
@@ -12,31 +12,24 @@
 #pragma once
 
 #include "bsort_dev.cuh"
+#include "swar.h"
 
 namespace bsort {
 namespace {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
-__device__ __forceinline__ uint32_t pack4(uint32_t bytemask) {
-  // bytes 0x00/0xFF -> 4 bits, bit i = byte i
-  return (((bytemask & 0x01010101u) * 0x01020408u) >> 24) & 0xFu;
-}
-
 // Letter and whitespace bit masks of 64 bytes held as 16 little-endian words.
 __device__ __forceinline__ void classify64(const uint32_t (&w)[16], uint64_t& letters, uint64_t& spaces) {
-  uint64_t lm = 0, sm = 0;
+  uint32_t l[2] = {0, 0}, sp[2] = {0, 0};
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
-    const uint32_t x = w[i];
-    const uint32_t lower = x | 0x20202020u;
-    const uint32_t is_letter = __vcmpltu4(__vsub4(lower, 0x61616161u), 0x1a1a1a1au);
-    const uint32_t is_space = __vcmpeq4(x, 0x20202020u) | __vcmpltu4(__vsub4(x, 0x09090909u), 0x05050505u);
-    lm |= (uint64_t)pack4(is_letter) << (4 * i);
-    sm |= (uint64_t)pack4(is_space) << (4 * i);
+    const uint32_t c = class_nibbles(w[i]);
+    l[i >> 3] |= (c & 0xFu) << (4 * (i & 7));
+    sp[i >> 3] |= (c >> 4) << (4 * (i & 7));
   }
-  letters = lm;
-  spaces = sm;
+  letters = ((uint64_t)l[1] << 32) | l[0];
+  spaces = ((uint64_t)sp[1] << 32) | sp[0];
 }
 
 // Letters whose previous letter-or-space byte is a space.  `ws_before` says
@@ -160,53 +153,70 @@ __device__ uint32_t block_exclusive_pk(uint32_t v, uint32_t* total) {
   return ex;
 }
 
-// byte_perm selector that moves the bytes of a 4-bit mask, in order, to the
-// low end of a word and fills the rest with zero bytes: nibble k of entry m
-// is the position of the k-th set bit of m (4 = a zero byte).  Sixteen
-// 16-bit entries, four to a 64-bit constant.
-__device__ __forceinline__ uint32_t compact_sel(uint32_t m4) {
-  const uint64_t t01 = (m4 & 4u) ? 0x4210442144204442ull : 0x4410444144404444ull;
-  const uint64_t t23 = (m4 & 4u) ? 0x3210432143204432ull : 0x4310443144304443ull;
-  const uint64_t t = (m4 & 8u) ? t23 : t01;
-  return (uint32_t)(t >> (16 * (m4 & 3u))) & 0xFFFFu;
+// byte_perm selectors that move the bytes of a 4-bit mask, in order, to the
+// low end of a word and fill the rest with zero bytes: nibble k of entry m is
+// the position of the k-th set bit of m (4 selects a zero byte).  Threads
+// 0..15 each fill one entry of a CTA's table.
+__device__ __forceinline__ void compact_table_fill(uint32_t* tab) {
+  const uint32_t m = threadIdx.x;
+  if (m < 16) {
+    uint32_t sel = 0x4444u, k = 0;
+    for (uint32_t b = 0; b < 4; ++b)
+      if ((m >> b) & 1u) {
+        sel = (sel & ~(0xFu << (4 * k))) | (b << (4 * k));
+        ++k;
+      }
+    tab[m] = sel;
+  }
 }
 
 // Writes the letters of the thread's 64 bytes (w, letter mask lm), in order,
 // to stage[pos...]: whole aligned 32-bit words where all four bytes are the
-// thread's, single bytes at the two ends (which neighbours share).
-__device__ __forceinline__ void stage_letters(const uint32_t (&w)[16], uint64_t lm, uint8_t* stage, uint32_t pos) {
+// thread's, single bytes at the two ends (which neighbours share).  Pending
+// bytes (at most seven) are held in two 32-bit words, the first at byte 0 of
+// `lo`, behind the `skew` bytes that precede pos in its word.
+__device__ __forceinline__ void stage_letters(const uint32_t (&w)[16], uint64_t lm, uint8_t* stage, uint32_t pos,
+                                              const uint32_t* sel_tab) {
   uint32_t* stage32 = reinterpret_cast<uint32_t*>(stage);
   const uint32_t skew = pos & 3u;
-  uint64_t acc = 0;      // pending bytes, the first at byte 0 (skew junk bytes first)
-  uint32_t na = skew;    // pending byte count
+  uint32_t lo = 0, hi = 0;
+  uint32_t na = skew;  // pending byte count, below 4 at the top of each step
   uint32_t wi = pos >> 2;
   bool first = true;
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    const uint32_t m4 = (uint32_t)(lm >> (4 * j)) & 0xFu;
-    const uint32_t c = __byte_perm(w[j], 0u, compact_sel(m4));
-    acc |= (uint64_t)c << (8 * na);
+    const uint32_t m4 = ((j < 8 ? (uint32_t)lm : (uint32_t)(lm >> 32)) >> (4 * (j & 7))) & 0xFu;
+    const uint32_t c = __byte_perm(w[j], 0u, sel_tab[m4]);
+    const uint32_t sh = 8 * na;
+    hi = __funnelshift_l(c, 0u, sh);  // the bytes of c that pass byte 3
+    lo |= c << sh;
     na += __popc(m4);
     if (na >= 4) {
-      const uint32_t word = (uint32_t)acc;
       if (first && skew) {
-        for (uint32_t b = skew; b < 4; ++b) stage[4 * wi + b] = (uint8_t)(word >> (8 * b));
+        for (uint32_t b = skew; b < 4; ++b) stage[4 * wi + b] = (uint8_t)(lo >> (8 * b));
       } else {
-        stage32[wi] = word;
+        stage32[wi] = lo;
       }
       first = false;
       ++wi;
-      acc >>= 32;
+      lo = hi;
+      hi = 0;
       na -= 4;
     }
   }
-  for (uint32_t b = first ? skew : 0u; b < na; ++b) stage[4 * wi + b] = (uint8_t)(acc >> (8 * b));
+  for (uint32_t b = first ? skew : 0u; b < na; ++b) stage[4 * wi + b] = (uint8_t)(lo >> (8 * b));
 }
+
+// Shared-memory slot of the chunk's 16-byte granule g.  The chunk is loaded
+// with granule g in thread g % 256's hands and read back four consecutive
+// granules per thread; XOR-ing the low three bits with bits 2..4 spreads
+// both access patterns over all eight 16-byte bank groups (no conflicts).
+__device__ __forceinline__ uint32_t chunk_slot(uint32_t g) { return g ^ ((g >> 2) & 7u); }
 
 __device__ __forceinline__ void thread_words(const uint4* buf, uint32_t (&w)[16]) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const uint4 v = buf[threadIdx.x * 4 + i];
+    const uint4 v = buf[chunk_slot(threadIdx.x * 4 + i)];
     w[4 * i + 0] = v.x;
     w[4 * i + 1] = v.y;
     w[4 * i + 2] = v.z;
