@@ -170,7 +170,7 @@ struct bsort_ctx {
 
   DevBuf sticky;  // a Meta kept across calls: err_timeout of bounded device waits
   HostBuf h_sticky;
-  DevBuf in, docs, meta, starts, letters, plan, keysA, keysB, counts, offsets, stream, jobs;
+  DevBuf in, docs, meta, starts, letters, plan, keysA, keysB, counts, offsets, stream, jobs, samples;
   HostBuf h_in, h_docs, h_meta, h_plan, h_counts, h_offsets, h_stream;
 
   // results of the last run (host view)
@@ -571,7 +571,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   // bytes of a bucket's output: its letters and, if asked for, its offsets
   const uint64_t off_bytes = c->cfg.want_offsets ? 4 : 0;
   auto out_bytes = [&](const Segment& sg) { return (double)sg.n * (sg.L + off_bytes); };
-  uint64_t key_words = 0, kb[kGroups] = {};
+  uint64_t key_words = 0, smp_words = 0, kb[kGroups] = {};
   double ob[kGroups] = {};
   uint32_t etile = 0, wtiles[2] = {0, 0}, wpasses[2] = {0, 0};
   uint32_t mtiles[4] = {}, mpasses[4] = {};
@@ -590,6 +590,9 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       etile += (sg.n + tile_of_width(W) - 1) / tile_of_width(W);
     }
     if (gi < 4) {
+      // merge samples: one key in 32 (read by the pipelined merges' cuts)
+      sg.smp_off = (uint32_t)smp_words;
+      smp_words += (uint64_t)(sg.n + 31) / 32 * W;
       sg.tile0 = mtiles[gi];
       mtiles[gi] += (sg.n + merge2_keys(W) - 1) / merge2_keys(W);
       mpasses[gi] = std::max(mpasses[gi], sg.passes);
@@ -616,6 +619,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   GROW(c->plan, plan_bytes, "layout");
   GROW(c->keysA, 8 * std::max<uint64_t>(key_words, 16), "keys");
   GROW(c->keysB, 8 * std::max<uint64_t>(key_words, 16), "keys");
+  GROW(c->samples, 8 * std::max<uint64_t>(smp_words, 16), "merge samples");
   GROW(c->counts, 8ull * ndocs * kHist, "counts");
   GROW(c->offsets, 4ull * ((uint64_t)n_total + ndocs), "offsets");
   GROW(c->stream, (size_t)s_total + 16, "stream");
@@ -746,14 +750,15 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
         const uint64_t* src = (p & 1) ? kB : kA;
         uint64_t* dst = (p & 1) ? kA : kB;
         TileJob* jobs = dptr<TileJob>(c->jobs) + job_at[g];
+        uint64_t* smp = dptr<uint64_t>(c->samples);
         {
           Trace tr_(c, sx, kMergeCut, 0.0);
           tr_.variant = (uint32_t)W;
-          CK(tr_.done(launch_merge_cut(W, d_segs, gb(g), ge(g), mtiles[g], p, src, jobs, sx)), "K5 merge cut");
+          CK(tr_.done(launch_merge_cut(W, d_segs, gb(g), ge(g), mtiles[g], p, src, smp, jobs, sx)), "K5 merge cut");
         }
         Trace tr_(c, sx, kMerge, moved_in(p));
         tr_.variant = (uint32_t)W;
-        CK(tr_.done(launch_merge_piped(W, jobs, mtiles[g], piped_grid, src, dst, eo, sx)), "K5 merge_pass");
+        CK(tr_.done(launch_merge_piped(W, jobs, mtiles[g], piped_grid, src, dst, smp, eo, sx)), "K5 merge_pass");
       }
     } else {
       // small passes: all of them in one launch, grid barriers between them
@@ -920,7 +925,7 @@ void bsort_destroy(bsort_ctx* c) {
   bsort_serve_shutdown(c);
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
-  for (DevBuf* b : {&c->sticky, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream, &c->jobs})
+  for (DevBuf* b : {&c->sticky, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream, &c->jobs, &c->samples})
     if (b->p) cudaFree(b->p);
   for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets, &c->h_stream})
     if (b->p) cudaFreeHost(b->p);

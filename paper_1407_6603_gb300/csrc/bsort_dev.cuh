@@ -106,7 +106,8 @@ struct Segment {
   uint32_t final_buf;   // 0: sorted keys end in buffer A, 1: in buffer B
   uint32_t passes;      // merge passes the bucket needs after K4
   uint32_t run0;        // length of the sorted runs K4 leaves
-  uint32_t pad[2];
+  uint32_t smp_off;     // pipelined merges: first u64 word of the bucket's merge samples
+  uint32_t pad;
 };
 
 // One output tile of a pipelined merge pass (K5), as the cut kernel leaves it:
@@ -125,8 +126,12 @@ struct TileJob {
   uint32_t stream;  //   stream byte offset of the tile's first word
   uint32_t word;    //   offsets[] index of that word
   uint32_t rel;     //   its offset within its document
-  uint32_t pad[3];
+  uint32_t smp;     // kNoSamples, or the word offset in the sample buffer of the slot of
+                    // the tile's first 32 outputs: the merge stores its output at
+  uint32_t smp_phase;  // tile positions = smp_phase (mod 32) there, one slot per 32
+  uint32_t pad;
 };
+constexpr uint32_t kNoSamples = 0xFFFFFFFFu;
 static_assert(sizeof(TileJob) == 64, "TileJob is four 16-byte copies");
 
 // K4 v2 / K5 v2 geometry (keys of at most 16 u64 words).
@@ -350,11 +355,13 @@ cudaError_t launch_merge_pass2(int W, const Segment* segs, uint32_t sbeg, uint32
                                uint32_t* barrier, Meta* meta, uint64_t wait_limit, cudaStream_t st);
 // Pipelined K5 for passes with many tiles: the cut kernel finds every tile's
 // slices (one warp per tile), then the merge kernel streams the tiles through
-// two shared-memory buffers, loading one while it merges the other.
+// two shared-memory buffers, loading one while it merges the other.  Each
+// merge pass but a bucket's last also stores one key in 32 of its output in
+// `samples` (Segment::smp_off), and the next pass's cut searches those first.
 cudaError_t launch_merge_cut(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t pass,
-                             const uint64_t* src, TileJob* jobs, cudaStream_t st);
+                             const uint64_t* src, const uint64_t* samples, TileJob* jobs, cudaStream_t st);
 cudaError_t launch_merge_piped(int W, const TileJob* jobs, uint32_t tiles, uint32_t grid, const uint64_t* src,
-                               uint64_t* dst, EmitOut eo, cudaStream_t st);
+                               uint64_t* dst, uint64_t* samples, EmitOut eo, cudaStream_t st);
 // CTAs per SM of the pipelined merge kernel.
 int merge_piped_ctas_per_sm();
 cudaError_t launch_emit(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,

@@ -267,6 +267,7 @@ __global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_pass2(
 template <int W>
 __global__ void __launch_bounds__(256) k_merge_cut(const Segment* __restrict__ segs, uint32_t sbeg, uint32_t send,
                                                    uint32_t tiles, uint32_t pass, const uint64_t* __restrict__ src,
+                                                   const uint64_t* __restrict__ samples,
                                                    TileJob* __restrict__ jobs) {
   constexpr int KPT = W >= 8 ? 1 : 8 / W;
   constexpr uint32_t T = kM2Threads * KPT;
@@ -279,10 +280,27 @@ __global__ void __launch_bounds__(256) k_merge_cut(const Segment* __restrict__ s
     end.a_src = ~0ull;
     jobs[tiles] = end;
   }
+  // 32-way search for the first m in [lo, hi) where the monotone predicate
+  // f (true, then false) is false; hi if none.  Uniform across the warp.
+  auto first_false = [&](uint32_t lo, uint32_t hi, auto f) {
+    while (hi > lo) {
+      const uint32_t span = hi - lo;
+      const uint32_t step = span <= 32u ? 1u : (span + 31u) / 32u;
+      const uint32_t m = lo + lane * step;
+      const bool t = m < hi && f(m);
+      const uint32_t nt = __popc(__ballot_sync(kFull, t));
+      // the answer lies after the last probe that holds, up to the next probe
+      const uint32_t nhi = lo + nt * step < hi ? lo + nt * step : hi;
+      lo = nt == 0 ? lo : lo + (nt - 1) * step + 1;
+      hi = nhi;
+    }
+    return lo;
+  };
   for (uint32_t it = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; it < tiles; it += warps) {
     const uint32_t si = seg_find_warp<kByTile0>(segs, sbeg, send, s_first, cached, it);
     const Segment& sg = segs[si];
     TileJob job{};
+    job.smp = kNoSamples;
     const uint32_t passes = sg.passes;
     const uint64_t out0 = (uint64_t)(it - sg.tile0) * T;
     job.a_src = sg.key_off + out0 * W;  // (a bucket already in one run: monotone, no outputs)
@@ -294,19 +312,25 @@ __global__ void __launch_bounds__(256) k_merge_cut(const Segment* __restrict__ s
       const uint32_t d = (uint32_t)(out0 - ps);
       const uint64_t* A = src + sg.key_off + ps * W;
       const uint64_t* B = A + (size_t)la * W;
+      // the cut: the first m where A[m] goes after the diagonal's B key
+      // B[d-1-m] (A's keys first among equals)
       uint32_t lo = d > lb ? d - lb : 0u, hi = d < la ? d : la;
-      while (hi > lo) {  // uniform across the warp
-        const uint32_t span = hi - lo;
-        const uint32_t step = span <= 32u ? 1u : (span + 31u) / 32u;
-        const uint32_t m = lo + lane * step;
-        bool f = false;  // A[m] goes before the diagonal's B key: the cut is past m
-        if (m < hi) f = !klt(kload<W>(B + (size_t)(d - 1 - m) * W), kload<W>(A + (size_t)m * W));
-        const uint32_t nf = __popc(__ballot_sync(kFull, f));
-        // the cut lies after the last probe that says so, up to the next probe
-        const uint32_t nhi = lo + nf * step < hi ? lo + nf * step : hi;
-        lo = nf == 0 ? lo : lo + (nf - 1) * step + 1;
-        hi = nhi;
+      if (pass > 0 && hi > lo) {
+        // The previous pass stored this pass's A keys at positions 31 (mod 32)
+        // and B keys at positions 0 (mod 32) (run starts and d are multiples
+        // of 32), so the probes m = 32i + 31 read A[m] and B[d-1-m] = B[d - 32(i+1)]
+        // from the sample buffer.  They pin the cut to 32 positions.
+        const uint64_t* sA = samples + sg.smp_off + (ps / 32) * W;
+        const uint64_t* sB = samples + sg.smp_off + ((ps + la + d) / 32 - 1) * W;
+        const uint32_t i_f = first_false(lo / 32, hi / 32, [&](uint32_t i) {
+          return !klt(kload<W>(sB - (size_t)i * W), kload<W>(sA + (size_t)i * W));
+        });
+        lo = max(lo, 32 * i_f);
+        hi = min(hi, 32 * i_f + 31);
       }
+      lo = first_false(lo, hi, [&](uint32_t m) {
+        return !klt(kload<W>(B + (size_t)(d - 1 - m) * W), kload<W>(A + (size_t)m * W));
+      });
       job.a_src = sg.key_off + (ps + lo) * W;
       job.b_src = sg.key_off + (ps + la + (d - lo)) * W;
       job.a_end = sg.key_off + (ps + la) * W;
@@ -317,6 +341,12 @@ __global__ void __launch_bounds__(256) k_merge_cut(const Segment* __restrict__ s
         job.stream = sg.stream_off + (uint32_t)out0 * sg.L;
         job.word = sg.out_word + (uint32_t)out0;
         job.rel = job.stream - sg.doc_stream0;
+      } else {
+        // samples for the next pass's cut: the tile lies in one run of that
+        // pass (its runs are 2R long, a multiple of T); A runs sample their
+        // positions 31 (mod 32), B runs their positions 0 (mod 32)
+        job.smp = sg.smp_off + (uint32_t)(out0 / 32) * W;
+        job.smp_phase = (out0 / (2 * R)) % 2 == 0 ? 31u : 0u;
       }
     }
     if (lane == 0) jobs[it] = job;
@@ -331,7 +361,8 @@ template <int W>
 __global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_piped(const TileJob* __restrict__ jobs,
                                                                               uint32_t tiles,
                                                                               const uint64_t* __restrict__ src,
-                                                                              uint64_t* __restrict__ dst, EmitOut eo) {
+                                                                              uint64_t* __restrict__ dst,
+                                                                              uint64_t* __restrict__ samples, EmitOut eo) {
   constexpr int KPT = W >= 8 ? 1 : 8 / W;
   constexpr uint32_t TW = kM2Threads * KPT * W;
   extern __shared__ __align__(128) uint64_t sm[];  // two tile buffers, padded layout
@@ -384,6 +415,12 @@ __global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_piped(c
       auto sB = [&](uint32_t i) { return kload<W>(pkey<W>(buf, na + i)); };
       const uint32_t a = mp_split_f<W>(sA, na, sB, nb, pos);
       merge_run_buf<W, KPT>(buf, 0, na, na, nb, a, pos - a, kk);
+      if (j.smp != kNoSamples) {  // one output in 32 for the next pass's cut
+#pragma unroll
+        for (int s = 0; s < KPT; ++s)
+          if ((pos + s) % 32 == j.smp_phase && pos + s < cnt)
+            kstore<W>(samples + j.smp + (size_t)((pos + s) / 32) * W, kk[s]);
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -471,14 +508,14 @@ cudaError_t launch_tile_sort2(int cluster, int lanes, int threads, const Segment
 int merge_piped_ctas_per_sm() { return BSORT_K5_MIN_CTAS; }
 
 cudaError_t launch_merge_cut(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t pass,
-                             const uint64_t* src, TileJob* jobs, cudaStream_t st) {
+                             const uint64_t* src, const uint64_t* samples, TileJob* jobs, cudaStream_t st) {
   if (tiles == 0) return cudaSuccess;
   const uint32_t grid = (tiles + 7) / 8;
   switch (W) {
-    case 1: k_merge_cut<1><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, jobs); break;
-    case 2: k_merge_cut<2><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, jobs); break;
-    case 4: k_merge_cut<4><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, jobs); break;
-    case 8: k_merge_cut<8><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, jobs); break;
+    case 1: k_merge_cut<1><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, samples, jobs); break;
+    case 2: k_merge_cut<2><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, samples, jobs); break;
+    case 4: k_merge_cut<4><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, samples, jobs); break;
+    case 8: k_merge_cut<8><<<grid, 256, 0, st>>>(segs, sbeg, send, tiles, pass, src, samples, jobs); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -486,7 +523,7 @@ cudaError_t launch_merge_cut(int W, const Segment* segs, uint32_t sbeg, uint32_t
 
 template <int W>
 cudaError_t merge_piped_w(const TileJob* jobs, uint32_t tiles, uint32_t grid, const uint64_t* src, uint64_t* dst,
-                          const EmitOut& eo, cudaStream_t st) {
+                          uint64_t* samples, const EmitOut& eo, cudaStream_t st) {
   constexpr uint32_t words = kM2Threads * (W >= 8 ? 1 : 8 / W) * W;
   const size_t smem = 2 * (size_t)padded_words(words) * 8;
   static int attr_done[64];
@@ -496,18 +533,18 @@ cudaError_t merge_piped_w(const TileJob* jobs, uint32_t tiles, uint32_t grid, co
                : cudaSuccess;
   });
   if (e != cudaSuccess) return e;
-  k_merge_piped<W><<<grid < tiles ? grid : tiles, kM2Threads, smem, st>>>(jobs, tiles, src, dst, eo);
+  k_merge_piped<W><<<grid < tiles ? grid : tiles, kM2Threads, smem, st>>>(jobs, tiles, src, dst, samples, eo);
   return cudaGetLastError();
 }
 
 cudaError_t launch_merge_piped(int W, const TileJob* jobs, uint32_t tiles, uint32_t grid, const uint64_t* src,
-                               uint64_t* dst, EmitOut eo, cudaStream_t st) {
+                               uint64_t* dst, uint64_t* samples, EmitOut eo, cudaStream_t st) {
   if (tiles == 0 || grid == 0) return cudaSuccess;
   switch (W) {
-    case 1: return merge_piped_w<1>(jobs, tiles, grid, src, dst, eo, st);
-    case 2: return merge_piped_w<2>(jobs, tiles, grid, src, dst, eo, st);
-    case 4: return merge_piped_w<4>(jobs, tiles, grid, src, dst, eo, st);
-    case 8: return merge_piped_w<8>(jobs, tiles, grid, src, dst, eo, st);
+    case 1: return merge_piped_w<1>(jobs, tiles, grid, src, dst, samples, eo, st);
+    case 2: return merge_piped_w<2>(jobs, tiles, grid, src, dst, samples, eo, st);
+    case 4: return merge_piped_w<4>(jobs, tiles, grid, src, dst, samples, eo, st);
+    case 8: return merge_piped_w<8>(jobs, tiles, grid, src, dst, samples, eo, st);
     default: return cudaErrorInvalidValue;
   }
 }
