@@ -172,6 +172,8 @@ struct bsort_ctx {
   HostBuf h_sticky;
   DevBuf in, docs, meta, starts, letters, plan, keysA, keysB, counts, offsets, stream, jobs, samples;
   HostBuf h_in, h_docs, h_meta, h_plan, h_counts, h_offsets, h_stream;
+  HostBuf h_flag;     // K1 raises it once its copy of a small meta region is in h_meta
+  uint32_t seq = 0;   // the value it raises it to: one per call
 
   // results of the last run (host view)
   MetaLayout ml;
@@ -340,6 +342,24 @@ bool host_pinned(const void* p, size_t len) {
 
 // Waits for an event by polling it (the call's one mid-path wait is short,
 // and a poll answers sooner than a blocking wait); after 200 us it blocks.
+// Waits until K1 has raised *flag to seq (its copy of the meta region is in
+// host memory by then).  Every 64 polls it also asks whether the stream has
+// passed `ev` (recorded after K1): a launch that failed or ended without
+// raising the flag is then reported instead of waited on.
+cudaError_t flag_wait(const uint32_t* flag, uint32_t seq, cudaEvent_t ev) {
+  for (uint32_t n = 1;; ++n) {
+    if (__atomic_load_n(flag, __ATOMIC_ACQUIRE) == seq) return cudaSuccess;
+    if ((n & 63u) == 0) {
+      const cudaError_t e = cudaEventQuery(ev);
+      if (e == cudaErrorNotReady) continue;
+      if (e != cudaSuccess) return e;
+      // the stream is past K1: the flag is up, or the kernel did not raise it
+      if (__atomic_load_n(flag, __ATOMIC_ACQUIRE) == seq) return cudaSuccess;
+      return cudaErrorLaunchFailure;
+    }
+  }
+}
+
 cudaError_t spin_wait(cudaEvent_t ev) {
   const auto t0 = std::chrono::steady_clock::now();
   for (;;) {
@@ -387,6 +407,26 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   uint32_t* d_item0 = dptr<uint32_t>(c->meta, ml.item0);
   uint32_t* d_hist = dptr<uint32_t>(c->meta, ml.hist);
 
+  // A small meta region (up to 64 KB: about 60 documents) reaches the host
+  // from K1's last CTA directly, without a copy of its own.
+  // (Page-locked host memory is mapped at the same address on the device
+  // with unified addressing; where it is not mapped the copy path is taken.)
+  bool meta_direct = ml.total <= 65536;
+  HostMeta hmeta{nullptr, 0, nullptr, 0};
+  if (meta_direct) {
+    GROW_HOST(c->h_flag, 64, "flag");
+    void* dm = nullptr;
+    void* df = nullptr;
+    if (cudaHostGetDevicePointer(&dm, c->h_meta.p, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer(&df, c->h_flag.p, 0) != cudaSuccess) {
+      cudaGetLastError();
+      meta_direct = false;
+    } else {
+      if (++c->seq == 0) ++c->seq;  // 0: the flag's value before any call
+      __atomic_store_n(hptr<uint32_t>(c->h_flag), 0u, __ATOMIC_RELEASE);
+      hmeta = HostMeta{static_cast<uint4*>(dm), (uint32_t)(ml.total / 16), static_cast<uint32_t*>(df), c->seq};
+    }
+  }
   CK(cudaMemcpyAsync(c->docs.p, hd, sizeof(DocDesc) * ndocs, cudaMemcpyHostToDevice, st), "copy document table");
   CK(cudaMemsetAsync(c->meta.p, 0, ml.cleared, st), "clear meta");
   const DocDesc* d_docs = dptr<DocDesc>(c->docs);
@@ -397,16 +437,19 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
          launch_tokenize1p(d_in, d_docs, ndocs, (uint32_t)chunks, dptr<uint8_t>(c->meta, ml.scratch),
                            dptr<uint8_t>(c->letters), dptr<uint32_t>(c->starts), d_hist,
                            dptr<uint32_t>(c->meta, ml.maxlen), d_wbase, d_lbase, d_item0,
-                           d_meta, d_sticky, c->cfg.l_cap, c->cfg.wait_limit, st),
+                           d_meta, d_sticky, c->cfg.l_cap, c->cfg.wait_limit, hmeta, st),
          "K1 tokenize");
-  CK(cudaMemcpyAsync(c->h_meta.p, c->meta.p, ml.total, cudaMemcpyDeviceToHost, st), "read counts");
+  if (!meta_direct) CK(cudaMemcpyAsync(c->h_meta.p, c->meta.p, ml.total, cudaMemcpyDeviceToHost, st), "read counts");
   cudaEvent_t gap_a = nullptr;
   if (c->cfg.profile) {
     gap_a = next_event(c);
     if (gap_a) cudaEventRecord(gap_a, st);
   }
   CK(cudaEventRecord(c->counts_ev, st), "counts event");
-  CK(spin_wait(c->counts_ev), "wait for counts");
+  if (meta_direct)
+    CK(flag_wait(hptr<uint32_t>(c->h_flag), hmeta.seq, c->counts_ev), "wait for counts");
+  else
+    CK(spin_wait(c->counts_ev), "wait for counts");
 
   const Meta* hm = hptr<Meta>(c->h_meta, ml.meta);
   const Meta* hs = hm;  // K1 copies the context's sticky timeout count into meta
@@ -927,7 +970,7 @@ void bsort_destroy(bsort_ctx* c) {
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
   for (DevBuf* b : {&c->sticky, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream, &c->jobs, &c->samples})
     if (b->p) cudaFree(b->p);
-  for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets, &c->h_stream})
+  for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets, &c->h_stream, &c->h_flag})
     if (b->p) cudaFreeHost(b->p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);

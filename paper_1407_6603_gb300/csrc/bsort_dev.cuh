@@ -318,10 +318,20 @@ inline cudaError_t once_per_device(int (&done)[64], F set) {
 // before the launch, and meta's histograms too; the caller clears both with
 // one memset.
 size_t tokenize1p_scratch_bytes(uint32_t nchunks);
+// Where K1's last CTA leaves a copy of the meta region for the host: `n16`
+// 16-byte words to page-locked host memory at `dst`, then `seq` in *flag
+// (after a system-scope fence).  dst == nullptr: no copy (the host reads the
+// region with a copy of its own).
+struct HostMeta {
+  uint4* dst;
+  uint32_t n16;
+  uint32_t* flag;
+  uint32_t seq;
+};
 cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
                               uint8_t* scratch, uint8_t* letters, uint32_t* starts, uint32_t* hist,
                               uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
-                              Meta* sticky, uint32_t l_cap, uint64_t wait_limit, cudaStream_t st);
+                              Meta* sticky, uint32_t l_cap, uint64_t wait_limit, HostMeta hm, cudaStream_t st);
 cudaError_t launch_scatter(const uint32_t* starts, const uint8_t* letters, const uint32_t* doc_wbase,
                            const uint32_t* doc_lbase, const uint32_t* doc_item0, uint32_t ndocs, uint32_t items,
                            uint32_t grid, const uint32_t* seg_lookup, const Segment* segs, uint32_t* cursor,

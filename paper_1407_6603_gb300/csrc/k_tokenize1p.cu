@@ -129,8 +129,8 @@ __device__ __forceinline__ void count_last_word(uint32_t L, uint32_t doc, uint32
 __global__ void __launch_bounds__(kTokThreads, BSORT_K1_MIN_CTAS) k_tokenize1p(
     const uint8_t* __restrict__ in, const DocDesc* __restrict__ docs, uint32_t ndocs, uint32_t nchunks,
     uint8_t* scratch, uint8_t* __restrict__ letters_out, uint32_t* __restrict__ starts, uint32_t* hist,
-    uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta, Meta* sticky, uint32_t l_cap,
-    uint64_t wait_limit) {
+    uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta, Meta* sticky,
+    uint32_t l_cap, uint64_t wait_limit, HostMeta hm) {
   K1Scratch* s = reinterpret_cast<K1Scratch*>(scratch);
   __shared__ uint4 buf[kChunk / 16 + 1];  // the chunk, then its letters (with up to 15 bytes of lead)
   extern __shared__ uint16_t s_starts[];   // up to kChunk / 2 word starts, as letter offsets in the chunk
@@ -401,6 +401,16 @@ __global__ void __launch_bounds__(kTokThreads, BSORT_K1_MIN_CTAS) k_tokenize1p(
     doc_item0[ndocs] = s_run;
     meta->items_total = s_run;
   }
+  if (hm.dst) {
+    // the whole meta region (this CTA's writes and the other CTAs' counts,
+    // all in L2 by now) to the host, then the flag the host waits on
+    __syncthreads();
+    const uint4* src = reinterpret_cast<const uint4*>(meta);
+    for (uint32_t i = t; i < hm.n16; i += kTokThreads) hm.dst[i] = __ldcg(src + i);
+    __threadfence_system();
+    __syncthreads();
+    if (t == 0) asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(hm.flag), "r"(hm.seq) : "memory");
+  }
 }
 
 }  // namespace
@@ -412,7 +422,7 @@ size_t tokenize1p_scratch_bytes(uint32_t nchunks) {
 cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
                               uint8_t* scratch, uint8_t* letters, uint32_t* starts, uint32_t* hist,
                               uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
-                              Meta* sticky, uint32_t l_cap, uint64_t wait_limit, cudaStream_t st) {
+                              Meta* sticky, uint32_t l_cap, uint64_t wait_limit, HostMeta hm, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   const size_t smem = (size_t)(kChunk / 2) * sizeof(uint16_t);
   static int attr_done[64];
@@ -422,7 +432,7 @@ cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t n
   if (e != cudaSuccess) return e;
   k_tokenize1p<<<nchunks ? nchunks : 1u, kTokThreads, smem, st>>>(in, docs, ndocs, nchunks, scratch, letters, starts,
                                                               hist, doc_maxlen, doc_wbase, doc_lbase, doc_item0, meta, sticky,
-                                                              l_cap, wait_limit);
+                                                              l_cap, wait_limit, hm);
   return cudaGetLastError();
 }
 
