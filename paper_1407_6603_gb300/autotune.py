@@ -14,7 +14,10 @@ double-buffered merge).
 Every candidate runs on the same seeded synthetic documents (the plain
 190 KB and 1.38 MB shapes, a 32 MiB slice of the 256 MiB generator and 256
 documents of the batch generator), resident on the current GPU, through the
-library's device entry points.  The library traces each launch with CUDA
+library's device entry points.  The two choices that only large inputs meet
+(the run length before pipelined merges, and the threshold that pipelines
+them) are timed on the whole 256 MiB document and the 4096-document batch as
+well.  The library traces each launch with CUDA
 events and tags tile-sort launches with their cluster size.  Each class is
 first timed alone (k4_streams=0 puts every tile sort on the call's stream),
 then the per-class choice is checked against uniform ones on whole calls with
@@ -48,9 +51,10 @@ def _documents():
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import synth
 
-    big = synth.plain("plain_256m")[: 32 << 20]
+    big = synth.plain("plain_256m")
     return [("plain_190k", [synth.plain("plain_190k")]), ("plain_1m38", [synth.plain("plain_1m38")]),
-            ("plain_256m[:32MiB]", [np.ascontiguousarray(big)]), ("batch_256", synth.batch(256))]
+            ("plain_256m[:32MiB]", [np.ascontiguousarray(big[: 32 << 20])]), ("batch_256", synth.batch(256))], \
+           [("plain_256m", [big]), ("batch_4096", synth.batch(4096))]
 
 
 def _time(table: str, sets, reps: int) -> tuple[dict, float]:
@@ -94,7 +98,7 @@ def _time(table: str, sets, reps: int) -> tuple[dict, float]:
 def tune(reps: int = 5, log=print) -> str:
     import torch
 
-    sets = _documents()
+    sets, large = _documents()
     # 1. each class timed alone (its tile sorts on the call's stream, one
     #    launch after another), for every lane count
     class_ms = {}
@@ -124,7 +128,7 @@ def tune(reps: int = 5, log=print) -> str:
     #    k4_runs CTAs) for buckets larger than one cluster of 8 tiles
     runs_of = {}
     for r in RUNS:
-        _, span = _time(f"k4_lanes={lanes} k4_threads={threads} k4_runs={r}", sets, reps)
+        _, span = _time(f"k4_lanes={lanes} k4_threads={threads} k4_runs={r}", sets + large, reps)
         runs_of[r] = span / reps
         log(f"  runs of {r} tiles before the merge passes: {runs_of[r]:9.3f} ms per round (whole calls)")
     runs = min(RUNS, key=lambda r: (runs_of[r], -r))
@@ -139,13 +143,13 @@ def tune(reps: int = 5, log=print) -> str:
     piped_of = {}
     for p in PIPED:
         _, span = _time(f"k4_lanes={lanes} k4_threads={threads} k4_runs={runs} k4_runs_small={runs_small} "
-                        f"piped_min={p}", sets, reps)
+                        f"piped_min={p}", sets + large, reps)
         piped_of[p] = span / reps
         log(f"  merge threshold {p} tiles per CTA: {piped_of[p]:9.3f} ms per round (whole calls)")
     piped = min(PIPED, key=lambda p: (piped_of[p], p))
     gpu = torch.cuda.get_device_name()
     lines = [f"# tuned on {gpu}, {time.strftime('%Y-%m-%d')}, {reps} rounds over "
-             + ", ".join(n for n, _ in sets),
+             + ", ".join(n for n, _ in sets) + " (run length and merge threshold: also " + ", ".join(n for n, _ in large) + ")",
              "# tile sort per class alone (clusters of 1, 2, 4, 8 CTAs), ms per round:"]
     for cl in CLUSTERS:
         lines.append("#   clusters of %d: " % cl + "  ".join(f"{g} lanes {class_ms[(cl, g)]:.3f}" for g in LANES))
