@@ -49,12 +49,12 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Tuning chosen per bucket-size class (see bsort_config.tune_table).  The
 // built-in values are what the autotuner (autotune.py) picked on a GB300.
 struct Tune {
-  int k4_lanes[4] = {2, 2, 4, 2};  // clusters of 1, 2, 4, 8 CTAs
+  int k4_lanes[4] = {2, 2, 2, 2};  // clusters of 1, 2, 4, 8 CTAs
   int k4_threads[4] = {256, 256, 256, 256};  // CTA size for the same classes (512: keys of up to 4 words)
   uint32_t piped_min = 1;
   int k4_streams = 1;  // 1: the tile sorts of the smaller classes run on side streams
-  int k4_runs = 1;     // cluster size (runs of that many tiles) for buckets that need pipelined merge passes
-  int k4_runs_small = 8;  // the same when their merges are too small to pipeline
+  int k4_runs = 2;     // cluster size (runs of that many tiles) for buckets that need pipelined merge passes
+  int k4_runs_small = 16;  // the same when their merges are too small to pipeline
 };
 
 // Parses a tune table; false on an unknown key or a bad value.
