@@ -159,8 +159,9 @@ struct bsort_ctx {
   int device = 0;
   int sm_count = 0;
   cudaStream_t own_stream = nullptr;
-  static constexpr int kSide = 5;
-  cudaStream_t side[kSide] = {};              // the smaller K4 launches run here, beside the clusters of 8
+  static constexpr int kSide = 9;
+  static constexpr int kChainSide = 5;        // side[5 + class]: the merge chains of the four key widths
+  cudaStream_t side[kSide] = {};              // side[0..4]: the K4 launches after the first, and the warp sort
   cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
   cudaEvent_t counts_ev = nullptr;  // the counts of K1 reached the host
   std::string err;
@@ -698,14 +699,22 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
                           items, grid, lookup_dev, d_segs, cursor_dev, kA, d_hist, dptr<uint64_t>(c->counts), eo, st),
            "K3 scatter");
   }
-  // K4: the clusters of 8 on the call's stream; the smaller kernels, which
-  // sort other buckets, each on a side stream at the same time, joined back
-  // before the merge passes
-  // (with k4_streams=0 in the tune table every launch stays on the call's
-  // stream, one after another: how the autotuner times each class alone)
-  bool small_work = ge(9) > gb(9);  // the warp sort, or a K4 launch besides the clusters of 8
-  for (const K4Launch& l : k4)
-    if (l.cluster != kSuperCluster && l.supertiles) small_work = true;
+  // K4: the launch that makes the merge passes' runs first, on the call's
+  // stream, so that the merges (which wait for it alone) start as early as
+  // they can; then the other launches, largest first, each on a side stream
+  // at the same time (they sort other buckets), joined back at the end of
+  // the call.  (With k4_streams=0 in the tune table every launch stays on the
+  // call's stream, one after another: how the autotuner times each class
+  // alone.)
+  int k4_order[5], n4 = 0;
+  for (int i = 0; i < 5; ++i)
+    if (k4[i].supertiles) k4_order[n4++] = i;
+  std::stable_sort(k4_order, k4_order + n4, [&](int a, int b) {
+    const bool ra = k4[a].cluster == runs, rb = k4[b].cluster == runs;
+    if (ra != rb) return ra;
+    return k4[a].levels > k4[b].levels;
+  });
+  const bool small_work = ge(9) > gb(9) || n4 > 1;  // the warp sort, or more than one K4 launch
   const bool side = small_work && c->tune.k4_streams;
   if (side) CK(cudaEventRecord(c->fork_ev, st), "fork");
   int used = 0;
@@ -716,10 +725,10 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     joined[used++] = sx;
     return sx;
   };
-  for (const K4Launch& l : k4) {
-    if (!l.supertiles) continue;
+  for (int q = 0; q < n4; ++q) {
+    const K4Launch& l = k4[k4_order[q]];
     cudaStream_t sx = st;
-    if (l.cluster != kSuperCluster && side) {
+    if (q > 0 && side) {
       sx = side_stream();
       CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
     }
@@ -737,10 +746,6 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     for (uint32_t i = gb(9); i < ge(9); ++i) levels += (double)segs[i].n * ceil_log2(segs[i].n);
     Trace tr_(c, sx, kTileSort, (double)kb[9] + ob[9], levels);
     CK(tr_.done(launch_warp_sort(d_segs, gb(9), ge(9), kA, eo, sx)), "K4 warp_sort");
-  }
-  for (int i = 0; i < used; ++i) {
-    CK(cudaEventRecord(c->join_ev[i], joined[i]), "join");
-    CK(cudaStreamWaitEvent(st, c->join_ev[i], 0), "join");
   }
   for (int g = 10; g < 12; ++g) {
     const uint32_t tiles = wtiles[g - 10];
@@ -778,7 +783,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     const int W = width_of_class(g);
     cudaStream_t sx = st;
     if (chains > 1) {
-      sx = c->side[g];
+      sx = c->side[bsort_ctx::kChainSide + g];
       CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
     }
     auto moved_in = [&](uint32_t p) {  // keys in, then keys out or, at a bucket's last pass, its words
@@ -815,7 +820,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
          "K5 merge_pass");
     }
     if (chains > 1) {
-      CK(cudaEventRecord(c->join_ev[nj], sx), "join");
+      CK(cudaEventRecord(c->join_ev[bsort_ctx::kChainSide + nj], sx), "join");
       ++nj;
     }
   }
@@ -832,7 +837,12 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
              "K5 merge_pass (wide keys)");
     }
   }
-  for (int i = 0; i < nj; ++i) CK(cudaStreamWaitEvent(st, c->join_ev[i], 0), "join");
+  for (int i = 0; i < nj; ++i) CK(cudaStreamWaitEvent(st, c->join_ev[bsort_ctx::kChainSide + i], 0), "join");
+  // the tile sorts on side streams
+  for (int i = 0; i < used; ++i) {
+    CK(cudaEventRecord(c->join_ev[i], joined[i]), "join");
+    CK(cudaStreamWaitEvent(st, c->join_ev[i], 0), "join");
+  }
   // K6: the words of the wide keys (every other bucket was emitted by its sort)
   if (etile) {
     LAUNCH(kEmit, (double)kb[10] + kb[11] + ob[10] + ob[11],
