@@ -32,10 +32,14 @@ constexpr uint64_t kDefaultWaitLimit = 1ull << 26;
 
 // Key width class of a word of L letters: W = next power of two >= ceil(L/8).
 __host__ __device__ inline int width_of_len(uint32_t L) {
+  // next_pow2(ceil(L / 8)), 1 for L <= 8: without a loop
   const uint32_t k = (L + 7) >> 3;
-  int w = 1;
-  while ((uint32_t)w < k) w <<= 1;
-  return w;
+  if (k <= 1) return 1;
+#ifdef __CUDA_ARCH__
+  return 1 << (32 - __clz(k - 1));
+#else
+  return 1 << (32 - __builtin_clz(k - 1));
+#endif
 }
 __host__ __device__ inline int class_of_width(int W) {
   return W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : W == 16 ? 4 : 5;

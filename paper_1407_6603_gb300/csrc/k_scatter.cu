@@ -37,10 +37,17 @@ constexpr uint32_t kLetterStage = 28672;
 // reach at most 11 bytes past the word's last letter.
 __device__ __forceinline__ void pack_word(const uint32_t* __restrict__ u, uint32_t base, uint32_t s0, uint32_t L,
                                           uint64_t* __restrict__ out) {
-  const int W = width_of_len(L);
   const uint32_t sel = 0x0123u + (s0 & 3u) * 0x1111u;
   const uint32_t* src = u + ((s0 - base) >> 2);
   uint32_t a = src[0];
+  if (L <= 8) {  // one key word: most words; in (length, rank) order a warp's words mostly share L
+    const uint32_t b = src[1], c = src[2];
+    const uint32_t hi = __byte_perm(a, b, sel) & (~0u << (8 * (4 - min(L, 4u))));
+    const uint32_t lo = L > 4 ? __byte_perm(b, c, sel) & (~0u << (8 * (8 - L))) : 0u;
+    out[0] = ((uint64_t)hi << 32) | lo;
+    return;
+  }
+  const int W = width_of_len(L);
   for (int q = 0; q < W; ++q) {
     uint64_t v = 0;
     const uint32_t b0 = (uint32_t)q * 8;
@@ -59,7 +66,7 @@ __device__ __forceinline__ void pack_word(const uint32_t* __restrict__ u, uint32
   }
 }
 
-__global__ void __launch_bounds__(kWordThreads) k_scatter(
+__global__ void __launch_bounds__(kWordThreads, 5) k_scatter(
     const uint32_t* __restrict__ starts, const uint8_t* __restrict__ letters, const uint32_t* __restrict__ doc_wbase,
     const uint32_t* __restrict__ doc_lbase, const uint32_t* __restrict__ doc_item0, uint32_t ndocs, uint32_t items,
     const uint32_t* __restrict__ seg_lookup, const Segment* __restrict__ segs, uint32_t* __restrict__ cursor,
