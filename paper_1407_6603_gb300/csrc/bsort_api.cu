@@ -428,14 +428,16 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       hmeta = HostMeta{static_cast<uint4*>(dm), (uint32_t)(ml.total / 16), static_cast<uint32_t*>(df), c->seq};
     }
   }
-  CK(cudaMemcpyAsync(c->docs.p, hd, sizeof(DocDesc) * ndocs, cudaMemcpyHostToDevice, st), "copy document table");
+  // one document travels as a kernel argument; more as a table
+  if (ndocs > 1)
+    CK(cudaMemcpyAsync(c->docs.p, hd, sizeof(DocDesc) * ndocs, cudaMemcpyHostToDevice, st), "copy document table");
   CK(cudaMemsetAsync(c->meta.p, 0, ml.cleared, st), "clear meta");
   const DocDesc* d_docs = dptr<DocDesc>(c->docs);
   // K1: strip, tokenize and count lengths in one pass.  Its algorithmic bytes
   // (input read, letters and word starts written) are known only after the
   // counts come back; they are added to its tag below.
   LAUNCH(kTokenize, 0,
-         launch_tokenize1p(d_in, d_docs, ndocs, (uint32_t)chunks, dptr<uint8_t>(c->meta, ml.scratch),
+         launch_tokenize1p(d_in, d_docs, ndocs ? hd[0] : DocDesc{}, ndocs, (uint32_t)chunks, dptr<uint8_t>(c->meta, ml.scratch),
                            dptr<uint8_t>(c->letters), dptr<uint32_t>(c->starts), d_hist,
                            dptr<uint32_t>(c->meta, ml.maxlen), d_wbase, d_lbase, d_item0,
                            d_meta, d_sticky, c->cfg.l_cap, c->cfg.wait_limit, hmeta, st),

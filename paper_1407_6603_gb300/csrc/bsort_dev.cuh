@@ -332,7 +332,9 @@ struct HostMeta {
   uint32_t* flag;
   uint32_t seq;
 };
-cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
+// docs: the document table in device memory; with one document K1 takes
+// doc0 (passed by value) instead and docs is not read.
+cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, DocDesc doc0, uint32_t ndocs, uint32_t nchunks,
                               uint8_t* scratch, uint8_t* letters, uint32_t* starts, uint32_t* hist,
                               uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
                               Meta* sticky, uint32_t l_cap, uint64_t wait_limit, HostMeta hm, cudaStream_t st);

@@ -127,7 +127,7 @@ __device__ __forceinline__ void count_last_word(uint32_t L, uint32_t doc, uint32
 #endif
 
 __global__ void __launch_bounds__(kTokThreads, BSORT_K1_MIN_CTAS) k_tokenize1p(
-    const uint8_t* __restrict__ in, const DocDesc* __restrict__ docs, uint32_t ndocs, uint32_t nchunks,
+    const uint8_t* __restrict__ in, const DocDesc* __restrict__ docs, DocDesc doc0, uint32_t ndocs, uint32_t nchunks,
     uint8_t* scratch, uint8_t* __restrict__ letters_out, uint32_t* __restrict__ starts, uint32_t* hist,
     uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta, Meta* sticky,
     uint32_t l_cap, uint64_t wait_limit, HostMeta hm) {
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kTokThreads, BSORT_K1_MIN_CTAS) k_tokenize1p(
   const uint32_t c = s_c;
   if (c < nchunks) {
     const uint32_t d = s_doc;
-    const DocDesc dd = docs[d];
+    const DocDesc dd = ndocs == 1 ? doc0 : docs[d];
     // 16-byte granules holding at least one byte of the document; the rest reads as spaces
     const uintptr_t first = reinterpret_cast<uintptr_t>(in) + dd.byte_off;
     const uintptr_t last = first + dd.len;
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kTokThreads, BSORT_K1_MIN_CTAS) k_tokenize1p(
     doc_lbase[ndocs] = all.letters;
   }
   for (uint32_t d = t; d < ndocs; d += kTokThreads) {
-    const uint32_t c0 = docs[d].chunk0;
+    const uint32_t c0 = ndocs == 1 ? doc0.chunk0 : docs[d].chunk0;
     const TokAcc b = c0 ? ld_acc(&s->rec[c0 - 1].inc) : kAccZero;
     doc_wbase[d] = b.words;
     doc_lbase[d] = b.letters;
@@ -419,7 +419,7 @@ size_t tokenize1p_scratch_bytes(uint32_t nchunks) {
   return offsetof(K1Scratch, rec) + (size_t)(nchunks ? nchunks : 1) * sizeof(LookRec);
 }
 
-cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t ndocs, uint32_t nchunks,
+cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, DocDesc doc0, uint32_t ndocs, uint32_t nchunks,
                               uint8_t* scratch, uint8_t* letters, uint32_t* starts, uint32_t* hist,
                               uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
                               Meta* sticky, uint32_t l_cap, uint64_t wait_limit, HostMeta hm, cudaStream_t st) {
@@ -430,7 +430,7 @@ cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, uint32_t n
     return cudaFuncSetAttribute(k_tokenize1p, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   });
   if (e != cudaSuccess) return e;
-  k_tokenize1p<<<nchunks ? nchunks : 1u, kTokThreads, smem, st>>>(in, docs, ndocs, nchunks, scratch, letters, starts,
+  k_tokenize1p<<<nchunks ? nchunks : 1u, kTokThreads, smem, st>>>(in, docs, doc0, ndocs, nchunks, scratch, letters, starts,
                                                               hist, doc_maxlen, doc_wbase, doc_lbase, doc_item0, meta, sticky,
                                                               l_cap, wait_limit, hm);
   return cudaGetLastError();
