@@ -346,12 +346,16 @@ bool host_pinned(const void* p, size_t len) {
 // Waits until K1 has raised *flag to seq (its copy of the meta region is in
 // host memory by then).  Every 64 polls it also asks whether the stream has
 // passed `ev` (recorded after K1): a launch that failed or ended without
-// raising the flag is then reported instead of waited on.
+// raising the flag is then reported instead of waited on.  After 200 us of
+// polling it blocks on the event instead, as spin_wait does.
 cudaError_t flag_wait(const uint32_t* flag, uint32_t seq, cudaEvent_t ev) {
+  const auto t0 = std::chrono::steady_clock::now();
   for (uint32_t n = 1;; ++n) {
     if (__atomic_load_n(flag, __ATOMIC_ACQUIRE) == seq) return cudaSuccess;
     if ((n & 63u) == 0) {
-      const cudaError_t e = cudaEventQuery(ev);
+      cudaError_t e = cudaEventQuery(ev);
+      if (e == cudaErrorNotReady && std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(200))
+        e = cudaEventSynchronize(ev);
       if (e == cudaErrorNotReady) continue;
       if (e != cudaSuccess) return e;
       // the stream is past K1: the flag is up, or the kernel did not raise it
