@@ -217,6 +217,17 @@ def test_batch_equals_single(ctx, oracle_mod, synth_mod):
         assert_same(ctx.text(d), exp, f"doc {i} alone")
 
 
+def test_batch_meta_region_copied(ctx, oracle_mod, synth_mod):
+    """96 documents: a meta region (totals, bases, histograms) over 64 KB,
+    which reaches the host by a copy rather than from K1's last CTA (the
+    batches above are small enough for the direct path)."""
+    docs = [synth_mod.batch_doc(*s) for s in synth_mod.batch_shapes(96)]
+    st, rs = ctx.batch(docs)
+    assert st == 0, ctx.last_error()
+    for i, d in enumerate(docs):
+        assert_same(rs[i], oracle_mod.stable(d, nthreads=8), f"doc {i}")
+
+
 def test_page_locked_and_packed_host_inputs(ctx, bsort_gpu, oracle_mod, synth_mod):
     """Host inputs read in place from page-locked memory, packed documents
     moved as one region (page-locked or not), and scattered ones gathered:
