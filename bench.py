@@ -507,10 +507,13 @@ def measure(args, quiet: bool = False):
             dist.destroy_process_group()
         return None
 
-    # roofline of the dominant kernel family (largest device time in the timed region)
+    # roofline of the dominant kernel family: the largest wall time in the
+    # timed region (the union of its launches' intervals; a family whose
+    # launches run side by side with others' on side streams would be
+    # overstated by the sum of its launch times)
     fams = {k: v for k, v in prof.items() if v[0] > 0}
     # host_gap (the call's one host round trip) is reported but is no kernel
-    dom = max((k for k in fams if k != "host_gap"), key=lambda k: fams[k][1])
+    dom = max((k for k in fams if k != "host_gap"), key=lambda k: wall.get(k) or fams[k][1])
     peak, peak_src = measured_peaks()
 
     def hbm_roofline(fam):
