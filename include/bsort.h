@@ -81,8 +81,9 @@ typedef struct {
                                                 into runs of k4_runs_small tiles
                               k4_runs_small=8|16  that run for the smaller merges (16: clusters
                                                 of 16 CTAs, beyond the portable cluster size)
-                              k4_streams=0|1    1 (default): the tile sorts of the smaller
-                                                classes run beside the largest on side
+                              k4_streams=0|1    1 (default): the tile sort that makes the
+                                                merge passes' runs runs first on the call's
+                                                stream, the others beside it on side
                                                 streams; 0: one after another on the call's
                                                 stream (how the autotuner times a class)
                             Copied at bsort_create; an unknown key or a bad value makes
@@ -215,7 +216,7 @@ typedef struct {
   double start_ms;    /* start, in ms after the first traced launch since the last bsort_profile_read */
   double end_ms;      /* end, on the same clock */
   double bytes;       /* algorithmic bytes */
-  uint32_t stream;    /* 0: the call's stream; 1..4: the side streams of the tile sorts and merges */
+  uint32_t stream;    /* 0: the call's stream; 1..5: the side streams of the tile sorts, 6..9: those of the merge chains */
   uint32_t variant;   /* tile_sort: CTAs per cluster (0: the one-warp sort of tiny buckets);
                          merge_pass / merge_cut: key width in u64 words; else 0 */
 } bsort_trace_rec;
