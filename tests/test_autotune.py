@@ -84,3 +84,21 @@ def test_tuner_output_passes_the_parser(tuned):
 def test_shipped_tune_table_passes_the_parser():
     with open(os.path.join(ROOT, "paper_1407_6603_gb300", "tune_table.txt")) as f:
         _assert_parses(f.read())
+
+
+def test_shipped_table_is_the_built_in_tuning():
+    """The library's built-in tuning (the Tune defaults in bsort_api.cu) is
+    the table shipped beside it."""
+    import re
+
+    src = open(os.path.join(ROOT, "paper_1407_6603_gb300", "csrc", "bsort_api.cu")).read()
+    body = src[src.index("struct Tune {"):src.index("\n};", src.index("struct Tune {"))]
+    built_in = {}
+    for key in ("k4_lanes", "k4_threads"):
+        built_in[key] = ",".join(re.search(key + r"\[4\] = \{([^}]*)\}", body).group(1).replace(" ", "").split(","))
+    for key in ("piped_min", "k4_runs", "k4_runs_small", "k4_streams"):
+        built_in[key] = re.search(r"\b" + key + r" = (\d+);", body).group(1)
+    with open(os.path.join(ROOT, "paper_1407_6603_gb300", "tune_table.txt")) as f:
+        shipped = dict(ln.strip().split("=") for ln in f if ln.strip() and not ln.startswith("#"))
+    for key, value in shipped.items():
+        assert built_in[key] == value, (key, built_in[key], value)
