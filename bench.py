@@ -8,8 +8,12 @@ point.  Prints one JSON line.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
 Workloads (seeded synthetic text shaped like the paper's Hamlet files, which
-are not available here): plain_1m38 (default, 1,447,000 B), plain_190k
-(194,560 B), plain_256m (268,435,456 B).
+are not available here): plain_256m (default, 268,435,456 B, the largest single
+document), plain_1m38 (1,447,000 B), plain_190k (194,560 B), batch_4096 (4,096
+documents, 2.07 GB) and serve (the request stream).  The default run adds the
+other forms beside the headline line under "forms": the 1.4 MB document, the
+whole 4,096-document batch, and the request stream at its configured rate and
+at saturation.
 
 For N > 1 (launched by torch.distributed.run) every rank sorts its own copy of
 the document on its own GPU: the work is independent per document, so there is
@@ -58,10 +62,13 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="plain_1m38",
+    p.add_argument("--workload", default="plain_256m",
                    choices=["plain_190k", "plain_1m38", "plain_256m", "batch_4096", "serve"])
     p.add_argument("--duration", type=float, default=10.0, help="seconds of Poisson arrivals (serve)")
-    p.add_argument("--pool", type=int, default=256, help="distinct documents the serve stream cycles through")
+    p.add_argument("--pool", type=int, default=1024, help="distinct documents the serve stream cycles through")
+    p.add_argument("--rate", type=float, default=None, help="serve: arrivals per second (default: the workload's)")
+    p.add_argument("--saturation-s", type=float, default=5.0,
+                   help="serve: seconds of the closed-loop run at capacity (0: none)")
     p.add_argument("--batch-docs", type=int, default=None, help="use only the first D documents of batch_4096")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -352,26 +359,38 @@ def cpu_baseline_batch(docs) -> dict:
             "words_per_s": nw / dt}
 
 
+FORM_KEYS = ("value", "unit", "words_per_s", "ms_per_step", "p50_ms", "p99_ms", "steps", "warmup", "config",
+             "roofline", "roofline_hbm", "path_roofline", "cpu_baseline", "e2e", "plain_per_doc", "gpu_launches",
+             "clocks")
+
+
 def run_ours(args) -> None:
     line = measure(args)
     if line is None:
         return
-    if args.workload == "plain_1m38" and not args.no_forms and line["n_gpus"] == 1:
-        # the batched form beside the plain one, on the same GPU (a short run)
+    if args.workload == "plain_256m" and not args.no_forms and not args.prefix_bytes and line["n_gpus"] == 1:
+        # the other forms beside the headline, on the same GPU: the paper-sized
+        # document, the whole batch (batched against one call per document) and
+        # the request stream (at its rate, then at capacity)
         import torch
 
+        forms = {}
+        for name, argv in (("plain_1m38", ["--workload", "plain_1m38", "--steps", "50", "--warmup", "5",
+                                           "--no-cpu-baseline"]),
+                           ("batch_4096", ["--workload", "batch_4096", "--steps", "5", "--warmup", "3",
+                                           "--e2e-steps", "3"])):
+            torch.cuda.empty_cache()
+            try:
+                f = measure(parse_args(argv), quiet=True)
+                forms[name] = {k: f[k] for k in FORM_KEYS if k in f}
+            except Exception as e:  # the headline line stands on its own
+                forms[name] = {"error": repr(e)[:300]}
         torch.cuda.empty_cache()
         try:
-            b = measure(parse_args(["--workload", "batch_4096", "--steps", "3", "--warmup", "3", "--no-cpu-baseline",
-                                    "--e2e-steps", "1"]), quiet=True)
-            line["forms"] = {"batch_4096": {
-                "value": b["value"], "unit": "MB/s", "words_per_s": b["words_per_s"], "ms_per_step": b["ms_per_step"],
-                "documents": b["config"]["documents"], "bytes": b["config"]["bytes"],
-                "plain_per_doc_words_per_s": b["plain_per_doc"]["words_per_s"],
-                "batched_over_plain_words": b["plain_per_doc"]["batched_over_plain_words"],
-                "roofline": b["roofline"]}}
-        except Exception as e:  # the main line stands on its own
-            line["forms"] = {"batch_4096": {"error": repr(e)[:200]}}
+            forms["serve"] = serve_measure(parse_args(["--workload", "serve", "--duration", "5", "--pool", "512"]))
+        except Exception as e:
+            forms["serve"] = {"error": repr(e)[:300]}
+        line["forms"] = forms
     print(json.dumps(line), flush=True)
 
 
@@ -610,111 +629,175 @@ def measure(args, quiet: bool = False):
     return line
 
 
-def run_serve(args) -> None:
-    """The request stream: Poisson arrivals at 2,000 documents/s, each document
-    log-uniform in [1 KiB, 16 MiB] (a pool of distinct documents cycled
-    through), submitted as they arrive to the continuous-batching server and
-    polled back; p50/p99 of submit-to-result latency and the served rate."""
-    import hashlib
+def fast_digest(*arrays) -> tuple:
+    """CRC-32 and length of each array's bytes: cheap enough to check every
+    served result (zlib releases the GIL, so a thread pool keeps up), and
+    any changed, moved or missing byte changes it except with probability
+    about 2^-32 per result."""
+    import zlib
+
+    import numpy as np
+
+    out = []
+    for a in arrays:
+        b = np.ascontiguousarray(a).view(np.uint8).reshape(-1)
+        out.append((int(b.size), zlib.crc32(b)))
+    return tuple(out)
+
+
+def serve_measure(args) -> dict | None:
+    """The request stream: Poisson arrivals (2,000 documents/s by default),
+    each document log-uniform in [1 KiB, 16 MiB] (a pool of distinct
+    documents cycled through), submitted as they arrive to the
+    continuous-batching server and polled back; p50/p99 of submit-to-result
+    latency and the served rate.  Then the same server at capacity (a closed
+    loop that keeps the queue full), beside the plain path (one bsort_text
+    call per document) on the same documents.  Every served result is checked
+    against the oracle's result for its document."""
     import threading
     from concurrent.futures import ThreadPoolExecutor
 
     import numpy as np
     import torch
 
+    import oracle
     import paper_1407_6603_gb300 as bs
     import synth
 
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
     if rank != 0:
-        return  # the request stream runs on one GPU
+        return None  # the request stream runs on one GPU
     bs.load()
     cores = os.cpu_count() or 8
     with ThreadPoolExecutor(cores) as ex:
         pool = list(ex.map(synth.serve_doc, range(args.pool)))
-    rate = synth.SERVE["rate"]
-    n_req = int(rate * args.duration)
-    t_arr = synth.arrivals(n_req, rate=rate)
-    ctx = bs.Context(device=local_rank)
-    ctx.serve_start(hbm_budget=64 << 30, workers=2, max_batch_docs=256)
-    # warm-up: every pool document once (not timed), which also fixes each
-    # document's result digest for the checks below
-    first = {}
-    for i, d in enumerate(pool):
-        assert ctx.submit(d, i) == 0
-    while len(first) < len(pool):
-        for tag, res, _ in ctx.poll(256):
-            first[tag] = hashlib.sha256(res.counts.tobytes() + res.offsets.tobytes() + res.stream.tobytes()).hexdigest()
-        time.sleep(0.001)
-    sampler = ClockSampler(local_rank).start()
-    lat, words, nbytes, bad = [], [0], [0], []
-    done = threading.Event()
-    lag = []
-
-    def consumer():
-        got = 0
-        while got < n_req:
-            for tag, res, ns in ctx.poll(256):
-                got += 1
-                lat.append(ns / 1e6)
-                words[0] += res.n_words
-                if tag < len(pool) * 2 and tag % 97 == 0:  # spot check of digests while running
-                    dg = hashlib.sha256(res.counts.tobytes() + res.offsets.tobytes() + res.stream.tobytes()).hexdigest()
-                    if dg != first[tag % len(pool)]:
-                        bad.append(tag)
-            time.sleep(0.0002)
-        done.set()
-
-    th = threading.Thread(target=consumer)
-    t0 = time.perf_counter()
-    th.start()
-    for i in range(n_req):
-        wait = t0 + t_arr[i] - time.perf_counter()
-        if wait > 0:
-            time.sleep(wait)
-        else:
-            lag.append(-wait)
-        d = pool[i % len(pool)]
-        nbytes[0] += d.size
-        assert ctx.submit(d, i) == 0
-    t_submit_end = time.perf_counter()
-    done.wait()
-    t1 = time.perf_counter()
-    th.join()
-    clocks = sampler.stop()
-    ctx.serve_stop()
-    ctx.close()
-    # correctness of the served results: every pool document's digest against the oracle
-    import oracle
 
     def oracle_digest(d):
         r = oracle.stable(d, nthreads=1)
-        return hashlib.sha256(r["counts"].astype(np.uint64).tobytes() + r["offsets"].astype(np.uint32).tobytes()
-                              + r["stream"].tobytes()).hexdigest()
+        return fast_digest(r["counts"].astype(np.uint64), r["offsets"].astype(np.uint32), r["stream"])
 
     with ThreadPoolExecutor(cores) as ex:
-        odig = list(ex.map(oracle_digest, pool))
-    mismatched = [i for i in range(len(pool)) if odig[i] != first[i]] + bad
-    wall = t1 - t0
-    lat_sorted = sorted(lat)
-    line = {
-        "metric": METRIC, "value": nbytes[0] / wall / 1e6, "unit": "MB/s", "n_gpus": 1, "steps": n_req,
-        "warmup": len(pool), "ms_per_step": wall / n_req * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded text generator)",
+        expect = list(ex.map(oracle_digest, pool))
+    rate = args.rate or synth.SERVE["rate"]
+    workers, max_batch = 2, 256
+    ctx = bs.Context(device=local_rank)
+    ctx.serve_start(hbm_budget=64 << 30, workers=workers, max_batch_docs=max_batch)
+    checker = ThreadPoolExecutor(max(2, cores // 2))
+
+    def check(tag, res):
+        return fast_digest(res.counts, res.offsets, res.stream) == expect[tag % len(pool)]
+
+    # warm-up: every pool document once (not timed), checked like the rest
+    warm = []
+    for i, d in enumerate(pool):
+        assert ctx.submit(d, i) == 0
+    got = 0
+    while got < len(pool):
+        for tag, res, _ in ctx.poll(256):
+            warm.append(checker.submit(check, tag, res))
+            got += 1
+        time.sleep(0.001)
+
+    def stream_run(n_req, t_arr, max_outstanding):
+        """Submits n_req requests (at the arrival times t_arr, or as fast as
+        the outstanding bound allows when t_arr is None) and collects them."""
+        lat, words, nbytes, lag, futs = [], [0], [0], [], []
+        done = threading.Event()
+        got_n = [0]
+
+        def consumer():
+            while got_n[0] < n_req:
+                for tag, res, ns in ctx.poll(256):
+                    got_n[0] += 1
+                    lat.append(ns / 1e6)
+                    words[0] += res.n_words
+                    futs.append(checker.submit(check, tag, res))
+                time.sleep(0.0002)
+            done.set()
+
+        th = threading.Thread(target=consumer)
+        t0 = time.perf_counter()
+        th.start()
+        for i in range(n_req):
+            if t_arr is not None:
+                wait = t0 + t_arr[i] - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+                else:
+                    lag.append(-wait)
+            else:
+                while i - got_n[0] >= max_outstanding:
+                    time.sleep(0.0001)
+            d = pool[i % len(pool)]
+            nbytes[0] += d.size
+            assert ctx.submit(d, i) == 0
+        t_submit_end = time.perf_counter()
+        done.wait()
+        t1 = time.perf_counter()
+        th.join()
+        ok = sum(1 for f in futs if f.result())
+        lat_sorted = sorted(lat)
+        wall = t1 - t0
+        return {"requests": n_req, "mb_per_s": nbytes[0] / wall / 1e6, "words_per_s": words[0] / wall,
+                "p50_ms": lat_sorted[len(lat_sorted) // 2],
+                "p99_ms": lat_sorted[min(len(lat_sorted) - 1, int(round(0.99 * (len(lat_sorted) - 1))))],
+                "offered_mb_per_s": nbytes[0] / (t_submit_end - t0) / 1e6,
+                "submit_lag_ms_max": max(lag) * 1e3 if lag else 0.0, "wall_s": wall,
+                "checked": len(futs), "mismatched": len(futs) - ok}
+
+    sampler = ClockSampler(local_rank).start()
+    n_req = int(rate * args.duration)
+    at_rate = stream_run(n_req, synth.arrivals(n_req, rate=rate), None)
+    clocks = sampler.stop()
+    sat = None
+    if args.saturation_s > 0:
+        # capacity: as many requests as the arrival run served per second,
+        # scaled to the saturation time, with the queue kept full
+        n_sat = max(len(pool), int(at_rate["requests"] / at_rate["wall_s"] * args.saturation_s))
+        sat = stream_run(n_sat, None, 4 * workers * max_batch)
+    ctx.serve_stop()
+    warm_bad = sum(1 for f in warm if not f.result())
+    ctx.close()
+    # the plain per-document path on the same documents: one bsort_text call
+    # each (host in, host out, as the server's results), for a few seconds
+    plain = None
+    with bs.Context(device=local_rank) as pc:
+        pinned = bs.pack_host(pool)
+        pc.text(pinned[0], copy=False)
+        t0 = time.perf_counter()
+        nw = nb = calls = 0
+        while time.perf_counter() - t0 < 3.0:
+            d = pinned[calls % len(pinned)]
+            nw += pc.text(d, copy=False).n_words
+            nb += d.size
+            calls += 1
+        dt = time.perf_counter() - t0
+        plain = {"words_per_s": nw / dt, "mb_per_s": nb / dt / 1e6, "calls": calls, "entry": "bsort_text per document"}
+    checker.shutdown()
+    checked = len(pool) + at_rate["checked"] + (sat["checked"] if sat else 0)
+    mismatched = warm_bad + at_rate["mismatched"] + (sat["mismatched"] if sat else 0)
+    return {
+        "metric": METRIC, "value": at_rate["mb_per_s"], "unit": "MB/s", "n_gpus": 1, "steps": n_req,
+        "warmup": len(pool), "ms_per_step": at_rate["wall_s"] / max(n_req, 1) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic (seeded text generator)",
         "config": {"workload": "serve", "requests": n_req, "arrival_rate_per_s": rate, "duration_s": args.duration,
-                   "distinct_documents": len(pool), "bytes": nbytes[0], "entry": "bsort_submit / bsort_poll",
-                   "workers": 2, "hbm_budget_bytes": 64 << 30},
-        "words_per_s": words[0] / wall,
-        "p50_ms": lat_sorted[len(lat_sorted) // 2],
-        "p99_ms": lat_sorted[min(len(lat_sorted) - 1, int(round(0.99 * (len(lat_sorted) - 1))))],
-        "offered_mb_per_s": nbytes[0] / (t_submit_end - t0) / 1e6,
-        "submit_lag_ms_max": max(lag) * 1e3 if lag else 0.0,
-        "results_checked_against_oracle": len(pool) + len([t for t in range(min(n_req, 2 * len(pool))) if t % 97 == 0]),
-        "results_mismatched": len(mismatched),
+                   "distinct_documents": len(pool), "entry": "bsort_submit / bsort_poll", "workers": workers,
+                   "max_batch_docs": max_batch, "hbm_budget_bytes": 64 << 30},
+        "words_per_s": at_rate["words_per_s"], "p50_ms": at_rate["p50_ms"], "p99_ms": at_rate["p99_ms"],
+        "offered_mb_per_s": at_rate["offered_mb_per_s"], "submit_lag_ms_max": at_rate["submit_lag_ms_max"],
+        "saturation": sat, "plain_per_doc": plain,
+        "served_over_plain_words": (sat["words_per_s"] / plain["words_per_s"]) if sat and plain else None,
+        "results_checked_against_oracle": checked, "results_mismatched": mismatched,
+        "requests_total": len(pool) + n_req + (sat["requests"] if sat else 0),
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+
+
+def run_serve(args) -> None:
+    line = serve_measure(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
 
 
 def main(argv=None) -> None:

@@ -21,6 +21,10 @@
  *     the last failure on a context is available from bsort_last_error().
  *   - A failed call leaves its output struct(s) zeroed.
  *   - A context is not thread-safe: one host thread at a time.
+ *   - Host-side fault injection for tests: the environment variable
+ *     BSORT_FAULT=alloc makes every allocation a call needs fail
+ *     (BSORT_E_NOMEM), BSORT_FAULT=timeout makes every call report a bounded
+ *     device wait as run out (BSORT_E_TIMEOUT); both leave the context usable.
  *   - Output buffers belong to the context.  They stay valid until the next
  *     bsort_text / bsort_text_device / bsort_batch call on the same context,
  *     bsort_result_release() or bsort_destroy(), whichever comes first.
@@ -56,8 +60,11 @@ typedef struct {
   int32_t device;        /* CUDA device ordinal; -1 (default) = the current device */
   int32_t profile;       /* 1: time every kernel launch with CUDA events (see bsort_profile_read);
                             0 (default): no events are recorded */
-  uint64_t wait_limit;   /* iteration limit of every device-side spin wait (0 = default, about
-                            a second); when one runs out the call returns BSORT_E_TIMEOUT */
+  uint64_t wait_limit;   /* iteration limit of every device-side spin wait on other CTAs
+                            (0 = default, about a second); when one runs out the call returns
+                            BSORT_E_TIMEOUT (the device entry points: see bsort_device_finish).
+                            A CTA's wait for its own bulk copy into shared memory never gives up
+                            sooner than the default, whatever this value. */
   const char* tune_table; /* NULL (default): built-in tuning.  Otherwise text of `key=value`
                             items separated by spaces, semicolons or newlines, '#' to end of
                             line a comment (the autotuner, paper_1407_6603_gb300/autotune.py,
@@ -151,7 +158,9 @@ bsort_status bsort_text(bsort_ctx* ctx, const uint8_t* bytes, size_t len, bsort_
  * of *out filled and with DEVICE pointers in counts, offsets and stream, whose
  * contents are complete once `stream` reaches the point of return (for
  * example after cudaStreamSynchronize(stream)).
- * Errors: as bsort_text.
+ * Errors: as bsort_text.  A bounded wait of the tokenize kernel that runs
+ * out is reported by this call (BSORT_E_TIMEOUT); one of the sort kernels,
+ * which run after the call returns, by bsort_device_finish().
  */
 bsort_status bsort_text_device(bsort_ctx* ctx, const uint8_t* d_bytes, size_t len, void* stream,
                                bsort_result* out);
@@ -185,6 +194,17 @@ bsort_status bsort_batch(bsort_ctx* ctx, const uint8_t* const* docs, const size_
  */
 bsort_status bsort_batch_device(bsort_ctx* ctx, const uint8_t* d_base, const uint64_t* offs, const uint64_t* lens,
                                 size_t n, void* stream, bsort_result* outs);
+
+/*
+ * Status of the device work that the last bsort_text_device or
+ * bsort_batch_device call on ctx enqueued.  Waits until `stream` (the one
+ * that call was given) has finished it; returns BSORT_E_TIMEOUT when a
+ * bounded device wait of the sort kernels ran out in it (its outputs are
+ * then not valid) and clears that record, else BSORT_OK.  A record that is
+ * never collected this way makes the next call on the context fail with
+ * BSORT_E_TIMEOUT instead.  Errors: BSORT_E_INVAL, BSORT_E_BUSY, BSORT_E_CUDA.
+ */
+bsort_status bsort_device_finish(bsort_ctx* ctx, void* stream);
 
 /*
  * Kernel tracing.  Every launch is counted; with config.profile == 1 each one

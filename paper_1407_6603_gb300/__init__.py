@@ -126,6 +126,8 @@ def load(path: str | None = None):
     lib.bsort_serve_pending.argtypes = [ctx_p]
     lib.bsort_serve_stop.restype = ctypes.c_int
     lib.bsort_serve_stop.argtypes = [ctx_p]
+    lib.bsort_device_finish.restype = ctypes.c_int
+    lib.bsort_device_finish.argtypes = [ctx_p, ctypes.c_void_p]
     lib.bsort_strip_noalloc.restype = ctypes.c_int
     lib.bsort_strip_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_void_p]
@@ -199,6 +201,12 @@ def bsort_batch_device(h, base_ptr: int, offs, lens, stream: int) -> tuple[int, 
     outs = (bsort_result * max(n, 1))()
     st = load().bsort_batch_device(h, base_ptr or None, o, ln, n, stream or None, outs)
     return st, [outs[i] for i in range(n)]
+
+
+def bsort_device_finish(h, stream: int) -> int:
+    """Waits for the last device call's work on ``stream``; its bsort_status
+    (BSORT_E_TIMEOUT when a bounded wait of the sort kernels ran out)."""
+    return int(load().bsort_device_finish(h, stream or None))
 
 
 def bsort_result_release(h, res: bsort_result) -> None:
@@ -505,6 +513,14 @@ class Context:
 
     def last_error(self) -> str:
         return bsort_last_error(self._h)
+
+    def device_finish(self, stream=None) -> int:
+        """Status of the last device call's work (waits for ``stream``, default
+        torch's current stream)."""
+        import torch
+
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return bsort_device_finish(self._h, s.cuda_stream)
 
     def serve_start(self, hbm_budget: int = 0, workers: int = 0, max_batch_docs: int = 0) -> None:
         bsort_serve_start(self._h, hbm_budget, workers, max_batch_docs)

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -211,8 +212,34 @@ bsort_status cuda_fail(bsort_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
   } while (0)
 
+// Host-side fault injection for tests (no GPU fault is involved): the
+// environment variable BSORT_FAULT lists, separated by commas,
+//   alloc    every device or page-locked host allocation that a call needs
+//            fails (the call returns BSORT_E_NOMEM; buffers already large
+//            enough are used as they are)
+//   timeout  every call whose K1 has run reports a bounded device wait as
+//            run out (BSORT_E_TIMEOUT), as a real one would be reported
+// It is read on every use, so a test can set and clear it between calls.
+bool fault_on(const char* what) {
+  const char* f = std::getenv("BSORT_FAULT");
+  if (!f || !*f) return false;
+  const size_t n = std::strlen(what);
+  for (const char* p = f; *p;) {
+    const char* e = std::strchr(p, ',');
+    const size_t len = e ? (size_t)(e - p) : std::strlen(p);
+    if (len == n && std::strncmp(p, what, n) == 0) return true;
+    if (!e) break;
+    p = e + 1;
+  }
+  return false;
+}
+
 bsort_status grow(bsort_ctx* c, DevBuf& b, size_t bytes, const char* what) {
   if (bytes <= b.cap && b.p) return BSORT_OK;
+  if (fault_on("alloc")) {
+    c->err = std::string("device allocation for ") + what + " failed (injected by BSORT_FAULT=alloc)";
+    return BSORT_E_NOMEM;
+  }
   size_t want = std::max<size_t>(bytes, 256);
   want = std::max(want, b.cap + b.cap / 4);  // amortise repeated growth
   if (b.p) {
@@ -233,6 +260,10 @@ bsort_status grow(bsort_ctx* c, DevBuf& b, size_t bytes, const char* what) {
 
 bsort_status grow_host(bsort_ctx* c, HostBuf& b, size_t bytes, const char* what) {
   if (bytes <= b.cap && b.p) return BSORT_OK;
+  if (fault_on("alloc")) {
+    c->err = std::string("pinned host allocation for ") + what + " failed (injected by BSORT_FAULT=alloc)";
+    return BSORT_E_NOMEM;
+  }
   size_t want = std::max<size_t>(bytes, 256);
   want = std::max(want, b.cap + b.cap / 4);
   if (b.p) {
@@ -459,14 +490,21 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     CK(spin_wait(c->counts_ev), "wait for counts");
 
   const Meta* hm = hptr<Meta>(c->h_meta, ml.meta);
-  const Meta* hs = hm;  // K1 copies the context's sticky timeout count into meta
   const uint32_t* h_wbase = hptr<uint32_t>(c->h_meta, ml.wbase);
   const uint32_t* h_lbase = hptr<uint32_t>(c->h_meta, ml.lbase);
   const uint32_t* h_hist = hptr<uint32_t>(c->h_meta, ml.hist);
   const uint32_t* h_maxlen = hptr<uint32_t>(c->h_meta, ml.maxlen);
-  if (hs->err_timeout) {
+  // K1's own bounded waits (this call), then the sort kernels' waits of an
+  // earlier device call whose status nobody collected (bsort_device_finish)
+  if (hm->err_timeout || fault_on("timeout"))
+    return fail(c, BSORT_E_TIMEOUT,
+                hm->err_timeout ? "a bounded device wait of the tokenize kernel ran out (the call's outputs are not valid)"
+                                : "a bounded device wait ran out (injected by BSORT_FAULT=timeout)");
+  if (hm->err_prev) {
     CK(cudaMemsetAsync(d_sticky, 0, sizeof(Meta), st), "clear timeout flag");
-    return fail(c, BSORT_E_TIMEOUT, "a bounded device wait ran out in an earlier call on this context");
+    return fail(c, BSORT_E_TIMEOUT,
+                "a bounded device wait of the sort kernels ran out in an earlier device call on this context, "
+                "whose outputs were not valid (bsort_device_finish reports it in time)");
   }
   const uint32_t n_total = hm->n_total, s_total = hm->s_total, items = hm->items_total;
   {
@@ -1267,6 +1305,23 @@ bsort_status bsort_batch_device(bsort_ctx* c, const uint8_t* d_base, const uint6
     r->stream = dptr<uint8_t>(c->stream) + h_lbase[i];
   }
   return first;
+}
+
+bsort_status bsort_device_finish(bsort_ctx* c, void* stream) {
+  if (!c) return BSORT_E_INVAL;
+  bsort_status s = enter(c);
+  if (s != BSORT_OK) return s;
+  Busy busy(c);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Meta* hs = hptr<Meta>(c->h_sticky);
+  CK(cudaMemcpyAsync(hs, c->sticky.p, sizeof(Meta), cudaMemcpyDeviceToHost, st), "read status");
+  CK(cudaStreamSynchronize(st), "wait for the device work");
+  if (hs->err_timeout) {
+    CK(cudaMemsetAsync(c->sticky.p, 0, sizeof(Meta), st), "clear timeout flag");
+    CK(cudaStreamSynchronize(st), "clear timeout flag");
+    return fail(c, BSORT_E_TIMEOUT, "a bounded device wait of the sort kernels ran out (the outputs are not valid)");
+  }
+  return BSORT_OK;
 }
 
 void bsort_result_release(bsort_ctx* c, bsort_result* res) {

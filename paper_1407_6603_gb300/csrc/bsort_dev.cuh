@@ -29,6 +29,10 @@ constexpr int kSortThreads = 256;           // K4/K5/K6 CTA size
 constexpr int kNumClasses = 6;              // key widths W = 1, 2, 4, 8, 16, 32 u64 words
 constexpr uint32_t kNoSegment = 0xFFFFFFFFu;
 constexpr uint64_t kDefaultWaitLimit = 1ull << 26;
+// Least number of polls a CTA gives one of its own bulk copies into shared
+// memory, whatever the configured wait limit: a copy is never abandoned while
+// it may still land in memory the CTA goes on to use.
+constexpr uint64_t kCopyWaitFloor = 1ull << 26;
 
 // Key width class of a word of L letters: W = next power of two >= ceil(L/8).
 __host__ __device__ inline int width_of_len(uint32_t L) {
@@ -89,8 +93,10 @@ struct Meta {
   uint32_t s_total;       // letters over all documents
   uint32_t items_total;   // K2/K3 work items
   uint32_t err_long;      // words longer than l_cap
-  uint32_t err_timeout;   // bounded waits that ran out (sticky until read)
-  uint32_t pad[3];
+  uint32_t err_timeout;   // bounded waits that ran out: in the sticky copy, those of the sort
+                          // kernels (kept until read); in a call's meta, those of its K1
+  uint32_t err_prev;      // a call's meta: the sticky count when its K1 ran (earlier calls)
+  uint32_t pad[2];
 };
 
 // One (document, length) bucket.  The host orders the table by the K4/K5

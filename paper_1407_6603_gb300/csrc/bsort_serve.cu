@@ -72,7 +72,7 @@ Server* server_of(const bsort_ctx* c) {
 
 void copy_result(const bsort_result& r, Done& d, bool want_offsets) {
   d.res = r;
-  if (r.status != BSORT_OK) {
+  if (r.status != BSORT_OK || !r.counts) {
     d.res.counts = nullptr;
     d.res.offsets = nullptr;
     d.res.stream = nullptr;
@@ -103,8 +103,13 @@ void worker_loop(Server* s, bsort_ctx* ctx) {
         const uint64_t f = s->queue.front().foot;
         if (s->in_flight + f > s->budget) {
           if (!batch.empty()) break;
-          s->cv_space.wait(lk, [&] { return s->stop || s->in_flight + f <= s->budget; });
-          if (s->in_flight + f > s->budget) return;  // stopping
+          // Wait for budget.  Another worker may take the front request
+          // meanwhile, so the loop looks at the queue afresh after the wait.
+          s->cv_space.wait(lk, [&] {
+            return s->stop || s->queue.empty() || s->in_flight + s->queue.front().foot <= s->budget;
+          });
+          if (s->stop && (s->queue.empty() || s->in_flight + s->queue.front().foot > s->budget)) return;
+          continue;
         }
         s->in_flight += f;
         foot += f;
@@ -112,6 +117,7 @@ void worker_loop(Server* s, bsort_ctx* ctx) {
         s->queue.pop_front();
       }
     }
+    if (batch.empty()) continue;  // the queue emptied while this worker waited
     ptrs.resize(batch.size());
     lens.resize(batch.size());
     outs.assign(batch.size(), bsort_result{});
@@ -125,8 +131,9 @@ void worker_loop(Server* s, bsort_ctx* ctx) {
     for (size_t i = 0; i < batch.size(); ++i) {
       Done& d = finished[i];
       d.tag = batch[i].tag;
-      if (st != BSORT_OK && outs[i].status == BSORT_OK && outs[i].stream == nullptr && lens[i] != 0) {
+      if (st != BSORT_OK && outs[i].status == BSORT_OK && outs[i].counts == nullptr) {
         // the whole call failed (not one document): report the call's status
+        // (every document that succeeded, empty ones included, has counts)
         std::memset(&d.res, 0, sizeof(d.res));
         d.res.status = st;
       } else {

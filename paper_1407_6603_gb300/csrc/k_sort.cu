@@ -41,13 +41,16 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(const Segment* __res
     }
     for (uint32_t e = tma_bytes / 8 + t; e < (uint32_t)(T * W); e += kSortThreads)
       sm[e] = e < cnt * W ? g[e] : ~0ull;  // odd tail word, then +inf padding
-    const bool ok = mbar_wait_bounded(&bar, phase, wait_limit);
+    // (the copy's wait has a floor of its own: see sort_supertile)
+    const uint64_t limit = wait_limit > kCopyWaitFloor ? wait_limit : kCopyWaitFloor;
+    const bool ok = mbar_wait_bounded(&bar, phase, limit);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
-      // The copy did not land in time: report, let it drain, stop.
+      // The copy did not land in time: report, give it a second bounded wait
+      // to drain, stop without writing anything.
       if (t == 0) {
         atomicAdd(&meta->err_timeout, 1u);
-        mbar_wait_bounded(&bar, phase ^ 1u, wait_limit);
+        mbar_wait_bounded(&bar, phase ^ 1u, limit);
       }
       __syncthreads();
       return;

@@ -152,6 +152,10 @@ __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t
   const uint32_t a0 = have0 ? carry.a1 : s_cut[0];
   const uint32_t a1 = s_cut[1];
   carry = SplitCarry{si, d1, a1, ps};
+  // Sorted runs give monotone cuts.  Runs read before their pass finished
+  // (a grid barrier that gave up: the call already reports a timeout) may
+  // not; such a tile is skipped, so every access stays in bounds.
+  if (a1 < a0 || d1 - a1 < d0 - a0) return;
   const uint32_t na = a1 - a0, nb = (d1 - a1) - (d0 - a0);
   const uint64_t* gA = A + (size_t)a0 * W;
   const uint64_t* gB = B + (size_t)(d0 - a0) * W;

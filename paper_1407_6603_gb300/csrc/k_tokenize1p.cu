@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kTokThreads, BSORT_K1_MIN_CTAS) k_tokenize1p(
           const uint32_t need = upto == 31 ? kFull : ((1u << (upto + 1)) - 1u);
           if ((ready_mask & need) != need) {
             if (++polls >= wait_limit) {  // gave up: the call reports a timeout
-              if (lane == 0) atomicAdd(&sticky->err_timeout, 1u);
+              if (lane == 0) atomicAdd(&meta->err_timeout, 1u);
               break;
             }
             __nanosleep(32);
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kTokThreads, BSORT_K1_MIN_CTAS) k_tokenize1p(
   __threadfence();
   const TokAcc all = nchunks ? ld_acc(&s->rec[nchunks - 1].inc) : kAccZero;
   if (t == 0) {
-    meta->err_timeout = ld_acquire(&sticky->err_timeout);  // the host reads it with the counts
+    meta->err_prev = ld_acquire(&sticky->err_timeout);  // the host reads it with the counts
     meta->n_total = all.words;
     meta->s_total = all.letters;
     starts[all.words] = all.letters;  // the last word ends at the end of S

@@ -239,21 +239,33 @@ __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint6
   }
   for (uint32_t e = tma_bytes / 8 + t; e < TW; e += NTH)
     buf0[e] = e < cnt * W ? g[e] : ~0ull;  // odd tail word, then +inf padding
-  const bool ok = mbar_wait_bounded(bar, phase, wait_limit);
+  // The copy's wait has a floor of its own (the caller's wait_limit bounds
+  // the waits on other CTAs): a copy of at most 16 KiB lands long before it.
+  const uint64_t limit = wait_limit > kCopyWaitFloor ? wait_limit : kCopyWaitFloor;
+  const bool ok = mbar_wait_bounded(bar, phase, limit);
   phase ^= 1u;
-  if (__syncthreads_or(!ok)) {
-    // The copy did not land in time: report it and let it drain.  The CTA
-    // stays in step with its cluster (no early exit); the call fails.
+  const bool lost = __syncthreads_or(!ok);
+  if (lost) {
+    // The copy did not land in time: report it (the call fails) and give it
+    // a second bounded wait to drain.  The CTA neither sorts nor writes this
+    // supertile, but stays in step with its cluster (no early exit).
     if (t == 0) {
       atomicAdd(&meta->err_timeout, 1u);
-      mbar_wait_bounded(bar, phase ^ 1u, wait_limit);
+      mbar_wait_bounded(bar, phase ^ 1u, limit);
     }
     __syncthreads();
+    // a sorted tile of +inf keys stands in for it, so that the cluster's
+    // merge-path cuts stay monotone (every access in bounds)
+    for (uint32_t e = t; e < padded_words(TW); e += NTH) buf0[e] = ~0ull;
+    __syncthreads();
+  } else {
+    cta_sort<W, G, NTH>(buf0);
   }
-  cta_sort<W, G, NTH>(buf0);
   const uint64_t* res = buf0;
   if constexpr (CL > 1) res = cluster_merge<W, CL, NTH>(buf0, buf1, buf2, r);
-  if (sg.passes == 0) {  // the bucket is sorted: its words go straight out
+  if (lost) {
+    // nothing of this supertile is written
+  } else if (sg.passes == 0) {  // the bucket is sorted: its words go straight out
     emit_tile<NTH>(sg, (uint32_t)j0, cnt, [&](uint32_t j, uint32_t q) { return res[padw(j * W + q)]; }, eo);
   } else {  // a run of CL tiles for K5
     for (uint32_t e = t; e < cnt * W; e += NTH) g[e] = res[padw(e)];

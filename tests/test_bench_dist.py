@@ -65,4 +65,4 @@ def test_single_rank_helpers():
 
     assert bench.reduce_max(3.0, 1) == 3.0
     a = bench.parse_args([])
-    assert a.gpus == 1 and a.warmup >= 3 and a.workload == "plain_1m38"
+    assert a.gpus == 1 and a.warmup >= 3 and a.workload == "plain_256m"

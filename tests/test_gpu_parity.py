@@ -378,3 +378,58 @@ def test_serving_rejects_over_budget(bsort_gpu):
         c.serve_stop()
         got = c.poll(8)
         assert [t for t, _, _ in got] == [2] and got[0][1].words() == [b"doc", b"small"]
+
+
+def _device_span(bs, torch, ptrs_and_sizes, itemsize, typestr):
+    """Host copy of one device buffer spanning [first pointer, last pointer +
+    its size): the outputs of a batch lie in one buffer per kind, in order."""
+    lo = min(p for p, n in ptrs_and_sizes if n)
+    hi = max(p + n * itemsize for p, n in ptrs_and_sizes if n)
+    t = torch.as_tensor(bs._DevView(lo, (hi - lo) // itemsize, typestr), device="cuda")
+    return lo, t.cpu().numpy()
+
+
+@pytest.mark.slow
+def test_batch_4096_full(bsort_gpu, oracle_mod, synth_mod):
+    """All 4,096 documents of the batch workload (2.07 GB) in one
+    bsort_batch_device call, as the benchmark runs it; every document's
+    counts, offsets and stream byte for byte against the oracle's result for
+    that document alone."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+
+    cores = os.cpu_count() or 8
+    docs = synth_mod.batch(None, threads=cores)
+    assert len(docs) == 4096
+    lens = [int(d.size) for d in docs]
+    offs = np.concatenate([[0], np.cumsum(lens)[:-1]]).astype(np.uint64).tolist()
+    base = torch.from_numpy(np.concatenate(docs)).cuda()
+    with bsort_gpu.Context() as c:
+        st, rs = c.batch_device_raw(base, offs, lens)
+        torch.cuda.synchronize()
+        assert st == 0, c.last_error()
+        assert all(r.status == 0 for r in rs)
+        # (signed views on the device: torch copies int64/int32 everywhere)
+        c0, counts = _device_span(bsort_gpu, torch, [(r.counts, r.max_len + 1) for r in rs], 8, "<i8")
+        o0, offsets = _device_span(bsort_gpu, torch, [(r.offsets, r.n_words + 1) for r in rs], 4, "<i4")
+        counts, offsets = counts.view(np.uint64), offsets.view(np.uint32)
+        s0, stream = _device_span(bsort_gpu, torch, [(r.stream, r.stream_bytes) for r in rs], 1, "|u1")
+    del base
+
+    def check(i):
+        r, exp = rs[i], oracle_mod.stable(docs[i])
+        if (r.n_words, r.max_len, r.stream_bytes) != (exp["n_words"], exp["max_len"], exp["stream_bytes"]):
+            return i
+        a = (r.counts - c0) // 8
+        b = (r.offsets - o0) // 4
+        s = r.stream - s0 if r.stream_bytes else 0
+        same = (np.array_equal(counts[a:a + r.max_len + 1], exp["counts"])
+                and np.array_equal(offsets[b:b + r.n_words + 1], exp["offsets"])
+                and np.array_equal(stream[s:s + r.stream_bytes], exp["stream"]))
+        return None if same else i
+
+    with ThreadPoolExecutor(cores) as ex:
+        bad = [i for i in ex.map(check, range(len(docs))) if i is not None]
+    assert bad == [], f"documents differing from the oracle: {bad[:20]}"

@@ -1,9 +1,11 @@
 """The allocation-free strip + tokenize entry point (bsort_strip_noalloc).
 
 It exists for callers that cannot call cudaMalloc (code running during CUDA
-graph capture, plugins whose host framework owns all device memory).  Its
-output must agree with the existing entry point's: the words it finds, put in
-(length, bytes) order, are exactly the stream, offsets and counts that
+graph capture, plugins whose host framework owns all device memory).  What it
+promises is the document's words in input order, so that list is compared
+element by element with the CPU oracle's tokenizer (oracle.tokenize), and its
+output must also agree with the existing entry point's: the same words, put
+in (length, bytes) order, are exactly the stream, offsets and counts that
 bsort_text_device returns for the same document.  Two calls in a row check
 that the shared scratch array is cleared between calls.
 """
@@ -48,7 +50,15 @@ def _check_against_existing(bs, ctx, d_in, words):
     assert off.tolist() == ref["offsets"].cpu().numpy().astype(np.int64).tolist()
 
 
-def test_noalloc_matches_existing_entry_point_twice(bsort_gpu, synth_mod):
+def _check_against_oracle(oracle_mod, data, words):
+    """The input-order word list, element by element, against the oracle's."""
+    exp = oracle_mod.tokenize(np.ascontiguousarray(data))
+    assert len(words) == len(exp)
+    for i, (w, e) in enumerate(zip(words, exp)):
+        assert w == e, f"word {i}: {w!r} != {e!r}"
+
+
+def test_noalloc_matches_oracle_and_existing_entry_point_twice(bsort_gpu, oracle_mod, synth_mod):
     import torch
 
     docs = [synth_mod.plain("plain_1m38"), synth_mod.text(synth_mod.TAG_FUZZ, 77, 300_001, 2_000, 3.7, 20)]
@@ -56,10 +66,25 @@ def test_noalloc_matches_existing_entry_point_twice(bsort_gpu, synth_mod):
         for data in docs:  # two calls in a row on the same scratch
             d_in = torch.from_numpy(np.ascontiguousarray(data)).cuda()
             words = _noalloc(bsort_gpu, d_in, torch)
+            _check_against_oracle(oracle_mod, data, words)
             _check_against_existing(bsort_gpu, ctx, d_in, words)
 
 
-def test_noalloc_unaligned_and_empty(bsort_gpu, synth_mod):
+def test_noalloc_chunk_straddling_words(bsort_gpu, oracle_mod):
+    """Words and runs of punctuation that straddle the 16 KiB chunks the
+    kernel splits the document into, on both sides of each boundary."""
+    import torch
+
+    rng = np.random.default_rng(79)
+    alphabet = np.frombuffer(b"abcXYZ,.'- \n\t", np.uint8)
+    data = rng.choice(alphabet, size=5 * 16384 + 77)
+    for k in range(1, 6):  # one long word across each chunk boundary
+        data[k * 16384 - 40:k * 16384 + 40] = ord("q")
+    d_in = torch.from_numpy(data).cuda()
+    _check_against_oracle(oracle_mod, data, _noalloc(bsort_gpu, d_in, torch))
+
+
+def test_noalloc_unaligned_and_empty(bsort_gpu, oracle_mod, synth_mod):
     import torch
 
     data = synth_mod.text(synth_mod.TAG_FUZZ, 78, 40_000, 500, 3.7, 20)
@@ -67,7 +92,9 @@ def test_noalloc_unaligned_and_empty(bsort_gpu, synth_mod):
     buf[5:5 + data.size] = torch.from_numpy(data).cuda()
     with bsort_gpu.Context() as ctx:
         view = buf[5:5 + data.size]
-        _check_against_existing(bsort_gpu, ctx, view, _noalloc(bsort_gpu, view, torch))
+        words = _noalloc(bsort_gpu, view, torch)
+        _check_against_oracle(oracle_mod, data, words)
+        _check_against_existing(bsort_gpu, ctx, view, words)
         empty = torch.zeros(0, dtype=torch.uint8, device="cuda")
         assert _noalloc(bsort_gpu, empty, torch) == []
 
