@@ -52,7 +52,7 @@ FALLBACK_HBM_GBS = 6800.0
 # Kernel families and the source file that holds each (for the traffic record).
 KERNEL_SOURCE = {
     "tokenize": "k_tokenize1p.cu", "scatter": "k_scatter.cu", "emit": "k_scatter.cu",
-    "tile_sort": "k_sort2.cu", "merge_pass": "k_sort2.cu", "merge_cut": "k_sort2.cu",
+    "tile_sort": "k_sort2.cu", "merge_pass": "k_sort2.cu", "merge_cut": "k_sort2.cu", "expand": "k_dedupe.cu",
 }
 
 
@@ -125,7 +125,7 @@ def kernel_source_sha(family: str) -> str:
     """sha256 (16 hex digits) of the family's .cu file and every shared header."""
     csrc = os.path.join(ROOT, "paper_1407_6603_gb300", "csrc")
     h = hashlib.sha256()
-    files = [KERNEL_SOURCE[family]] + sorted(f for f in os.listdir(csrc) if f.endswith(".cuh"))
+    files = [KERNEL_SOURCE.get(family, "bsort_api.cu")] + sorted(f for f in os.listdir(csrc) if f.endswith(".cuh"))
     for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())

@@ -88,6 +88,14 @@ typedef struct {
                                                 into runs of k4_runs_small tiles
                               k4_runs_small=8|16  that run for the smaller merges (16: clusters
                                                 of 16 CTAs, beyond the portable cluster size)
+                              dedupe=0|1        1: the duplicate-aware sort for the
+                                                buckets too large for one cluster of 8 tiles
+                                                (keys of up to 8 words): the tile sort hands
+                                                each sorted run's distinct words, with their
+                                                counts, to a hash table per bucket; the
+                                                distinct words are sorted and written out
+                                                count times each.  0 (default): merge
+                                                passes.  The result is the same either way.
                               k4_streams=0|1    1 (default): the tile sort that makes the
                                                 merge passes' runs runs first on the call's
                                                 stream, the others beside it on side

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -56,6 +57,7 @@ struct Tune {
   int k4_streams = 1;  // 1: the tile sorts of the smaller classes run on side streams
   int k4_runs = 2;     // cluster size (runs of that many tiles) for buckets that need pipelined merge passes
   int k4_runs_small = 16;  // the same when their merges are too small to pipeline
+  int dedupe = 0;          // 1: the duplicate-aware sort for the buckets that need merge passes
 };
 
 // Parses a tune table; false on an unknown key or a bad value.
@@ -111,6 +113,9 @@ bool parse_tune(const char* text, Tune& t) {
         if (nums[q] != 256 && nums[q] != 512) return false;
         t.k4_threads[q] = (int)nums[q];
       }
+    } else if (key == "dedupe") {
+      if (nums.size() != 1 || nums[0] > 1) return false;
+      t.dedupe = (int)nums[0];
     } else if (key == "piped_min") {
       if (nums.size() != 1 || nums[0] < 1 || nums[0] > 1000000) return false;
       t.piped_min = (uint32_t)nums[0];
@@ -139,11 +144,12 @@ struct MetaLayout {
   }
 };
 
-enum Kind { kTokenize, kScatter, kTileSort, kMerge, kMergeCut, kEmit, kHostGap, kKinds };
-// host_gap is no kernel: the device time between the counts reaching the
-// host and the first launch after the layout (the call's one round trip)
+enum Kind { kTokenize, kScatter, kTileSort, kMerge, kMergeCut, kEmit, kHostGap, kExpand, kKinds };
+// host_gap is no kernel: the device time between counts reaching the host and
+// the first launch after the layout built from them (the call's round trips:
+// the length counts, and the distinct-key counts of the duplicate-aware sort)
 const char* const kKindName[kKinds] = {"tokenize", "scatter",  "tile_sort", "merge_pass",
-                                       "merge_cut", "emit",     "host_gap"};
+                                       "merge_cut", "emit",     "host_gap",  "expand"};
 
 struct ProfRec {
   int kind;
@@ -174,6 +180,16 @@ struct bsort_ctx {
   HostBuf h_sticky;
   DevBuf in, docs, meta, starts, letters, plan, keysA, keysB, counts, offsets, stream, jobs, samples;
   HostBuf h_in, h_docs, h_meta, h_plan, h_counts, h_offsets, h_stream;
+  // the duplicate-aware sort: hash tables (stamped with the call's generation
+  // `gen`, so never cleared between calls), the distinct-key arrays and their
+  // ping-pong partner, the second layout, merge scratch and count prefixes
+  DevBuf htab, uA, uB, plan2, samples2, jobs2, pre;
+  HostBuf h_plan2, h_ucnt;
+  uint32_t gen = 0;
+  cudaEvent_t dedupe_ev = nullptr;  // the distinct-key counts reached the host
+  std::vector<uint32_t> dd_seg, dd_pos;
+  std::vector<Segment> segv2;
+  std::vector<uint8_t> groupv2;
   HostBuf h_flag;     // K1 raises it once its copy of a small meta region is in h_meta
   uint32_t seq = 0;   // the value it raises it to: one per call
 
@@ -405,6 +421,443 @@ cudaError_t spin_wait(cudaEvent_t ev) {
   }
 }
 
+// ---- sort planning and launching ----
+// Shared by the (document, length) buckets and, for the duplicate-aware sort,
+// by the arrays of their distinct keys.
+//
+// Groups (T = one K4 tile of the bucket's key width; table order below):
+//   0..3  W = 1, 2, 4, 8 and more than 8T keys: K4 into runs of k4_runs or
+//         k4_runs_small tiles, then K5 merge passes (one launch per pass and
+//         width), or, marked kSegDedupe, K4's hash inserts; group 4 unused
+//   5     (4T, 8T] keys: K4 in clusters of 8        6   (2T, 4T]: clusters of 4
+//   7     (T, 2T]: clusters of 2                      8   (32 KPT, T]: single CTAs
+//   9     at most 32 lanes x KPT keys: one warp each
+//   10,11 keys of 16 / 32 words (65..128 / 129..255 letters): the narrow-tile
+//         kernels of k_sort.cu
+constexpr int kGroups = 12;
+
+uint8_t group_of(Segment& sg, uint64_t& big_tiles) {
+  const uint32_t n = sg.n;
+  const int W = width_of_len(sg.L);
+  const uint32_t T = W >= 16 ? 0u : tile2_keys(W);
+  sg.run0 = n;
+  sg.passes = 0;
+  uint8_t gi;
+  if (W >= 16) {
+    gi = W == 16 ? 10 : 11;
+    sg.run0 = (uint32_t)tile_of_width(W);
+    sg.passes = merge_passes(n, sg.run0);
+  } else if (n <= warp_keys(W)) {
+    gi = 9;
+  } else if (n <= T) {
+    gi = 8;
+  } else if (n <= 2 * T) {
+    gi = 7;
+  } else if (n <= 4 * T) {
+    gi = 6;
+  } else if (n <= (uint32_t)kSuperCluster * T) {
+    gi = 5;
+  } else {  // needs merge passes: runs and passes are set by plan_sorts
+    gi = (uint8_t)class_of_width(W);
+    big_tiles += (n + merge2_keys(W) - 1) / merge2_keys(W);
+  }
+  sg.final_buf = sg.passes & 1u;
+  return gi;
+}
+
+struct K4Launch {
+  int cluster;
+  int gc;
+  uint32_t sbeg = 0, send = 0;
+  uint32_t supertiles = 0;
+  int max_w = 1;
+  double key_bytes = 0;
+  double levels = 0;  // key-levels: each key times log2 of the sorted run it ends in
+};
+
+struct SortPlan {
+  uint32_t nseg = 0;
+  int runs = 2;
+  int order[kGroups] = {};
+  int pos_of[kGroups] = {};
+  uint32_t pbeg[kGroups + 1] = {};
+  K4Launch k4[5] = {{8, 5}, {4, 6}, {2, 7}, {1, 8}, {16, -1}};  // the last: clusters of 16, runs only
+  uint64_t key_words = 0, smp_words = 0, kb[kGroups] = {};
+  double ob[kGroups] = {};
+  uint32_t etile = 0, wtiles[2] = {}, wpasses[2] = {}, mtiles[4] = {}, mpasses[4] = {};
+  uint64_t jobs_total = 0, job_at[4] = {};
+  uint32_t gb(int g) const { return pbeg[pos_of[g]]; }      // first segment of group g
+  uint32_t ge(int g) const { return pbeg[pos_of[g] + 1]; }  // one past its last
+};
+
+// Orders the candidates into `out` by the kernels that sort them and fills
+// the plan: the run length K4 leaves and the passes of the buckets that need
+// merge passes (none for those marked kSegDedupe: their runs go to the hash
+// tables), key offsets (kept as given with preset_keys), merge tiles and
+// samples, wide-key tiles, the K4 launch ranges and their tags.
+void plan_sorts(const bsort_ctx* c, const std::vector<Segment>& cand, const std::vector<uint8_t>& group,
+                uint64_t big_tiles, bool preset_keys, uint64_t off_bytes, Segment* out, SortPlan& p) {
+  p.nseg = (uint32_t)cand.size();
+  uint32_t group_n[kGroups] = {};
+  for (uint8_t g : group) ++group_n[g];
+  // The buckets that need merge passes leave K4 as runs of k4_runs tiles
+  // when their merges are large enough to be pipelined (the passes then run
+  // at HBM speed, cheaper than more cluster levels), else as runs of
+  // k4_runs_small tiles (fewer passes, fewer launches).
+  const uint32_t piped_grid = (uint32_t)(c->sm_count * merge_piped_ctas_per_sm());
+  p.runs = big_tiles >= (uint64_t)c->tune.piped_min * piped_grid ? c->tune.k4_runs : c->tune.k4_runs_small;
+  // Table order: the groups that K4 finishes (clusters of 8, 4, 2, 1), with
+  // the groups that need merge passes (0..3, and the unused 4) placed just
+  // before the one whose cluster size makes their runs, so that every K4
+  // launch and every width's merge chain covers one contiguous range; then
+  // the warp sort and the wide keys.
+  int n_ord = 0;
+  for (int gc : {5, 6, 7, 8}) {
+    if (kSuperCluster >> (gc - 5) == p.runs || (p.runs > kSuperCluster && gc == 5))
+      for (int g = 0; g < 5; ++g) p.order[n_ord++] = g;
+    p.order[n_ord++] = gc;
+  }
+  for (int g : {9, 10, 11}) p.order[n_ord++] = g;
+  for (int q = 0; q < kGroups; ++q) p.pos_of[p.order[q]] = q;
+  for (int q = 0; q < kGroups; ++q) p.pbeg[q + 1] = p.pbeg[q] + group_n[p.order[q]];
+  {  // stable counting sort of the candidates by table position
+    uint32_t at[kGroups];
+    for (int q = 0; q < kGroups; ++q) at[q] = p.pbeg[q];
+    for (uint32_t i = 0; i < p.nseg; ++i) {
+      Segment sg = cand[i];
+      if (group[i] < 4) {
+        if (sg.flags & kSegDedupe) {
+          sg.run0 = (uint32_t)p.runs * tile2_keys(width_of_len(sg.L));
+          sg.passes = 0;
+        } else {
+          sg.run0 = (uint32_t)p.runs * tile2_keys(width_of_len(sg.L));
+          sg.passes = merge_passes(sg.n, sg.run0);
+        }
+        sg.final_buf = sg.passes & 1u;
+      }
+      out[at[p.pos_of[group[i]]]++] = sg;
+    }
+  }
+  // K4 launches: cluster size, its own group, and the table range it covers
+  // (the merge-pass groups too, for the cluster size that makes their runs)
+  for (K4Launch& l : p.k4) {
+    if (l.gc < 0) {
+      l.sbeg = p.runs == l.cluster ? p.gb(0) : 0u;
+      l.send = p.runs == l.cluster ? p.ge(4) : 0u;
+    } else {
+      l.sbeg = l.cluster == p.runs ? p.gb(0) : p.gb(l.gc);
+      l.send = p.ge(l.gc);
+    }
+  }
+  auto out_bytes = [&](const Segment& sg) {  // a bucket's output: its letters and offsets
+    return (sg.flags & kSegKeysOut) ? 8.0 * width_of_len(sg.L) * sg.n : (double)sg.n * (sg.L + off_bytes);
+  };
+  for (uint32_t i = 0; i < p.nseg; ++i) {
+    Segment& sg = out[i];
+    const int W = width_of_len(sg.L);
+    int q = 0;
+    while (i >= p.pbeg[q + 1]) ++q;
+    const int gi = p.order[q];
+    if (!preset_keys) sg.key_off = p.key_words;
+    p.key_words += align_up((size_t)sg.n * W, 16);
+    p.kb[gi] += 8ull * W * sg.n;
+    p.ob[gi] += out_bytes(sg);
+    if (gi >= 10) {  // only the wide keys go through K6
+      sg.etile0 = p.etile;
+      p.etile += (sg.n + tile_of_width(W) - 1) / tile_of_width(W);
+    }
+    if (gi < 4) {
+      // Every bucket of the group gets its merge tiles, also one that needs
+      // no pass (a run of k4_runs_small tiles can hold it, or it went to the
+      // hash tables): the merge kernels find a tile's bucket by binary
+      // search over tile0, which must rise along the group; they skip the
+      // buckets whose passes are done.
+      sg.tile0 = p.mtiles[gi];
+      p.mtiles[gi] += (sg.n + merge2_keys(W) - 1) / merge2_keys(W);
+      p.mpasses[gi] = std::max(p.mpasses[gi], sg.passes);
+      if (sg.passes) {  // merge samples: one key in 32 (read by the pipelined merges' cuts)
+        sg.smp_off = (uint32_t)p.smp_words;
+        p.smp_words += (uint64_t)(sg.n + 31) / 32 * W;
+      }
+    }
+    for (K4Launch& l : p.k4)
+      if (i >= l.sbeg && i < l.send) {
+        const uint32_t super = (uint32_t)l.cluster * tile2_keys(W);
+        sg.stile0 = l.supertiles;
+        l.supertiles += (sg.n + super - 1) / super;
+        l.max_w = std::max(l.max_w, W);
+        // keys in, then runs out for K5, the sorted words out, or (the
+        // duplicate-aware sort) nothing but the hash inserts
+        l.key_bytes += 8.0 * W * sg.n + ((sg.flags & kSegDedupe) ? 0.0 : sg.passes ? 8.0 * W * sg.n : out_bytes(sg));
+        l.levels += (double)sg.n * ceil_log2(std::min<uint64_t>(sg.n, (uint64_t)super));
+      }
+    if (gi >= 10) {
+      sg.tile0 = p.wtiles[gi - 10];
+      p.wtiles[gi - 10] += (sg.n + sg.run0 - 1) / sg.run0;
+      p.wpasses[gi - 10] = std::max(p.wpasses[gi - 10], sg.passes);
+    }
+  }
+  for (int g = 0; g < 4; ++g)
+    if (p.mpasses[g] && p.mtiles[g] >= c->tune.piped_min * piped_grid) {
+      p.job_at[g] = p.jobs_total;
+      p.jobs_total += p.mtiles[g] + 1;  // and the end sentinel
+    }
+}
+
+bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, const Segment* d_segs, uint64_t* kA,
+                          uint64_t* kB, uint64_t* samples, DevBuf& jobs, uint32_t* barrier_dev, const EmitOut& eo,
+                          const DedupeOut& dd, cudaStream_t st, bool side_ok, std::vector<cudaStream_t>& joined,
+                          const std::function<bsort_status()>& after_first_k4) {
+  const uint32_t grid_cap = (uint32_t)c->sm_count * 16;
+  const uint32_t piped_grid = (uint32_t)(c->sm_count * merge_piped_ctas_per_sm());
+  Meta* d_sticky = dptr<Meta>(c->sticky);
+  // K4: the launch that makes the merge passes' runs first, on the call's
+  // stream, so that the merges (which wait for it alone) start as early as
+  // they can; then the other launches, largest first, each on a side stream
+  // at the same time (they sort other buckets).  (With k4_streams=0 in the
+  // tune table every launch stays on the call's stream, one after another:
+  // how the autotuner times each class alone.)
+  int k4_order[5], n4 = 0;
+  for (int i = 0; i < 5; ++i)
+    if (p.k4[i].supertiles) k4_order[n4++] = i;
+  std::stable_sort(k4_order, k4_order + n4, [&](int a, int b) {
+    const bool ra = p.k4[a].cluster == p.runs, rb = p.k4[b].cluster == p.runs;
+    if (ra != rb) return ra;
+    return p.k4[a].levels > p.k4[b].levels;
+  });
+  const bool small_work = p.ge(9) > p.gb(9) || n4 > 1;  // the warp sort, or more than one K4 launch
+  const bool side = side_ok && small_work && c->tune.k4_streams;
+  if (side) CK(cudaEventRecord(c->fork_ev, st), "fork");
+  int used = 0;
+  auto side_stream = [&]() -> cudaStream_t {
+    if (!side) return st;
+    cudaStream_t sx = c->side[used++];
+    joined.push_back(sx);
+    return sx;
+  };
+  bool first_done = false;
+  for (int q = 0; q < n4; ++q) {
+    const K4Launch& l = p.k4[k4_order[q]];
+    cudaStream_t sx = st;
+    if (q > 0 && side) {
+      sx = side_stream();
+      CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
+    }
+    Trace tr_(c, sx, kTileSort, l.key_bytes, l.levels);
+    tr_.variant = (uint32_t)l.cluster;
+    const int cls = l.cluster == 1 ? 0 : l.cluster == 2 ? 1 : l.cluster == 4 ? 2 : 3;  // 16 as 8
+    CK(tr_.done(launch_tile_sort2(l.cluster, c->tune.k4_lanes[cls], c->tune.k4_threads[cls], d_segs, l.sbeg, l.send,
+                                  l.supertiles, c->sm_count, l.max_w, kA, eo, d_sticky, c->cfg.wait_limit, dd, sx)),
+       "K4 tile_sort");
+    if (q == 0 && after_first_k4) {
+      const bsort_status s = after_first_k4();
+      if (s != BSORT_OK) return s;
+      first_done = true;
+    }
+  }
+  if (!first_done && after_first_k4) {
+    const bsort_status s = after_first_k4();
+    if (s != BSORT_OK) return s;
+  }
+  if (p.ge(9) > p.gb(9)) {
+    cudaStream_t sx = side_stream();
+    if (side) CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
+    double levels = 0;
+    for (uint32_t i = p.gb(9); i < p.ge(9); ++i) levels += (double)segs[i].n * ceil_log2(segs[i].n);
+    Trace tr_(c, sx, kTileSort, (double)p.kb[9] + p.ob[9], levels);
+    CK(tr_.done(launch_warp_sort(d_segs, p.gb(9), p.ge(9), kA, eo, sx)), "K4 warp_sort");
+  }
+  for (int g = 10; g < 12; ++g) {
+    const uint32_t tiles = p.wtiles[g - 10];
+    if (!tiles) continue;
+    double levels = 0;
+    for (uint32_t k = p.gb(g); k < p.ge(g); ++k)
+      levels += (double)segs[k].n * ceil_log2(std::min<uint64_t>(segs[k].n, segs[k].run0));
+    Trace tr_(c, st, kTileSort, 2.0 * p.kb[g], levels);
+    tr_.variant = 1;
+    CK(tr_.done(launch_tile_sort(g == 10 ? 16 : 32, d_segs, p.gb(g), p.ge(g), tiles, std::min(tiles, grid_cap), kA,
+                                 d_sticky, c->cfg.wait_limit, st)),
+       "K4 tile_sort (wide keys)");
+  }
+  // K5: merge passes over the buckets that need them, one launch per pass and
+  // width.  With at least piped_min tiles per resident CTA the pass is
+  // pipelined: a cut kernel lists every tile's slices first, so that the
+  // merge kernel can load one tile while it merges another.  The widths'
+  // chains of passes are independent: with more than one, each runs on a side
+  // stream of its own, so that one chain's latency-bound launches overlap
+  // another's merges.
+  if (p.jobs_total) GROW(jobs, sizeof(TileJob) * p.jobs_total, "merge jobs");
+  int chains = 0;
+  for (int g = 0; g < 4; ++g)
+    if (p.mpasses[g]) ++chains;
+  const bool chain_side = side_ok && chains > 1;
+  if (chain_side) CK(cudaEventRecord(c->fork_ev, st), "fork");
+  const uint64_t off_bytes = c->cfg.want_offsets ? 4 : 0;
+  for (int g = 0; g < 4; ++g) {
+    if (!p.mpasses[g]) continue;
+    const int W = width_of_class(g);
+    cudaStream_t sx = st;
+    if (chain_side) {
+      sx = c->side[bsort_ctx::kChainSide + g];
+      joined.push_back(sx);
+      CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
+    }
+    auto moved_in = [&](uint32_t pass) {  // keys in, then keys out or, at a bucket's last pass, its words
+      double moved = 0;
+      for (uint32_t i = p.gb(g); i < p.ge(g); ++i) {
+        const Segment& sg = segs[i];
+        if (sg.passes <= pass) continue;
+        const bool words = sg.passes == pass + 1 && !(sg.flags & kSegKeysOut);
+        moved += 8.0 * W * sg.n + (words ? (double)sg.n * (sg.L + off_bytes) : 8.0 * W * sg.n);
+      }
+      return moved;
+    };
+    if (p.mtiles[g] >= c->tune.piped_min * piped_grid) {
+      for (uint32_t pass = 0; pass < p.mpasses[g]; ++pass) {
+        const uint64_t* src = (pass & 1) ? kB : kA;
+        uint64_t* dst = (pass & 1) ? kA : kB;
+        TileJob* jb = dptr<TileJob>(jobs) + p.job_at[g];
+        {
+          Trace tr_(c, sx, kMergeCut, 0.0);
+          tr_.variant = (uint32_t)W;
+          CK(tr_.done(launch_merge_cut(W, d_segs, p.gb(g), p.ge(g), p.mtiles[g], pass, src, samples, jb, sx)),
+             "K5 merge cut");
+        }
+        Trace tr_(c, sx, kMerge, moved_in(pass));
+        tr_.variant = (uint32_t)W;
+        CK(tr_.done(launch_merge_piped(W, jb, p.mtiles[g], piped_grid, src, dst, samples, eo, sx)), "K5 merge_pass");
+      }
+    } else {
+      // small passes: all of them in one launch, grid barriers between them
+      double moved = 0;
+      for (uint32_t pass = 0; pass < p.mpasses[g]; ++pass) moved += moved_in(pass);
+      Trace tr_(c, sx, kMerge, moved);
+      tr_.variant = (uint32_t)W;
+      CK(tr_.done(launch_merge_pass2(W, d_segs, p.gb(g), p.ge(g), p.mtiles[g],
+                                     std::min<uint32_t>(p.mtiles[g], (uint32_t)c->sm_count * 8), 0, p.mpasses[g], kA, kB,
+                                     eo, barrier_dev + g, d_sticky, c->cfg.wait_limit, sx)),
+         "K5 merge_pass");
+    }
+  }
+  for (int g = 10; g < 12; ++g) {
+    const int W = g == 10 ? 16 : 32;
+    const uint32_t tiles = p.wtiles[g - 10];
+    for (uint32_t pass = 0; pass < p.wpasses[g - 10]; ++pass) {
+      double moved = 0;
+      for (uint32_t i = p.gb(g); i < p.ge(g); ++i)
+        if (segs[i].passes > pass) moved += 16.0 * W * segs[i].n;
+      LAUNCH(kMerge, moved,
+             launch_merge_pass(W, d_segs, p.gb(g), p.ge(g), tiles, std::min(tiles, grid_cap), pass, (pass & 1) ? kB : kA,
+                               (pass & 1) ? kA : kB, st),
+             "K5 merge_pass (wide keys)");
+    }
+  }
+  // K6: the words of the wide keys (every other bucket was emitted by its sort)
+  if (p.etile) {
+    LAUNCH(kEmit, (double)p.kb[10] + p.kb[11] + p.ob[10] + p.ob[11],
+           launch_emit(d_segs, p.gb(10), p.ge(11), p.etile, std::min(p.etile, grid_cap), kA, kB, eo, st), "K6 emit");
+  }
+  return BSORT_OK;
+}
+
+// The duplicate-aware sort's second half, once K4 has filled the hash tables
+// of the `ndd` buckets marked kSegDedupe (table positions in c->dd_pos): reads
+// how many distinct keys each bucket has, sorts every bucket's distinct-key
+// array (entries of key + count, kSegKeysOut: the same K4 / K5 kernels, all
+// on the call's stream), then expands the sorted arrays into the buckets'
+// words.  The counts' read-back is the call's second round trip.
+bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* ins, uint32_t ndd,
+                           const uint32_t* h_ucnt, const EmitOut& eo, cudaStream_t st) {
+  cudaEvent_t gap_a = nullptr;
+  if (c->cfg.profile) {
+    gap_a = next_event(c);
+    if (gap_a) cudaEventRecord(gap_a, st);
+  }
+  CK(spin_wait(c->dedupe_ev), "wait for distinct-key counts");
+  std::vector<Segment>& cand = c->segv2;
+  std::vector<uint8_t>& group = c->groupv2;
+  cand.clear();
+  group.clear();
+  uint64_t big_tiles = 0;
+  for (uint32_t di = 0; di < ndd; ++di) {
+    const uint32_t U = h_ucnt[di];
+    if (U == 0) continue;  // every insert dropped: a timeout, which the call reports
+    const DedupeIns& d = ins[di];
+    Segment u{};
+    u.n = U;
+    u.L = 8 * d.Wp;  // keys of Wp words: the key, its count, zeros
+    u.doc = di;
+    u.key_off = d.uniq_off;
+    u.flags = kSegKeysOut;
+    const uint8_t gi = group_of(u, big_tiles);
+    cand.push_back(u);
+    group.push_back(gi);
+  }
+  const uint32_t nseg = (uint32_t)cand.size();
+  const size_t seg_bytes = align_up(sizeof(Segment) * std::max<uint32_t>(nseg, 1), 256);
+  const size_t barrier_bytes = 256;
+  const size_t ed_bytes = align_up(sizeof(ExpandDesc) * std::max<uint32_t>(nseg, 1), 256);
+  const size_t plan_bytes = seg_bytes + barrier_bytes + ed_bytes;
+  GROW_HOST(c->h_plan2, plan_bytes, "distinct-key layout");
+  Segment* const segs2 = hptr<Segment>(c->h_plan2);
+  std::memset(hptr<char>(c->h_plan2, seg_bytes), 0, barrier_bytes);
+  ExpandDesc* const ed = hptr<ExpandDesc>(c->h_plan2, seg_bytes + barrier_bytes);
+  SortPlan p2;
+  plan_sorts(c, cand, group, big_tiles, true, c->cfg.want_offsets ? 4 : 0, segs2, p2);
+  // expansion descriptors, in the order of the buckets
+  std::vector<uint32_t> where(ndd, kNoSegment);
+  for (uint32_t i = 0; i < nseg; ++i) where[segs2[i].doc] = i;
+  uint32_t ne = 0, max_tiles = 0;
+  uint64_t pre_words = 0;
+  double moved = 0;
+  for (uint32_t di = 0; di < ndd; ++di) {
+    if (where[di] == kNoSegment) continue;
+    const Segment& u = segs2[where[di]];
+    const Segment& b = segs[c->dd_pos[di]];
+    ExpandDesc& e = ed[ne++];
+    e = ExpandDesc{};
+    e.uniq_off = ins[di].uniq_off;
+    e.pre_off = pre_words;
+    pre_words += u.n + 1;
+    e.U = u.n;
+    e.n = b.n;
+    e.L = b.L;
+    e.Wp = ins[di].Wp;
+    e.final_buf = u.final_buf;
+    max_tiles = std::max(max_tiles, (b.n + expand_tile(e.Wp / 2) - 1) / expand_tile(e.Wp / 2));
+    e.stream_off = b.stream_off;
+    e.out_word = b.out_word;
+    e.doc_stream0 = b.doc_stream0;
+    // the sorted entries and the prefix read, the words and offsets written
+    moved += 8.0 * e.Wp * e.U + 4.0 * (e.U + 1) + (double)b.n * (b.L + (c->cfg.want_offsets ? 4 : 0));
+  }
+  GROW(c->plan2, plan_bytes, "distinct-key layout");
+  GROW(c->samples2, 8 * std::max<uint64_t>(p2.smp_words, 16), "merge samples");
+  GROW(c->pre, 4 * std::max<uint64_t>(pre_words, 16), "count prefixes");
+  CK(cudaMemcpyAsync(c->plan2.p, c->h_plan2.p, plan_bytes, cudaMemcpyHostToDevice, st), "copy distinct-key layout");
+  if (gap_a) {
+    cudaEvent_t gap_b = next_event(c);
+    if (gap_b) {
+      cudaEventRecord(gap_b, st);
+      c->recs.push_back(ProfRec{kHostGap, gap_a, gap_b, 0.0, 0u, 0u});
+      c->kind_launches[kHostGap] += 1;
+    }
+  }
+  const Segment* segs2_dev = dptr<Segment>(c->plan2);
+  uint32_t* barrier2 = dptr<uint32_t>(c->plan2, seg_bytes);
+  std::vector<cudaStream_t> none;
+  const DedupeOut no_dd{nullptr, nullptr, nullptr, nullptr, 0};
+  bsort_status s = launch_sorts(c, p2, segs2, segs2_dev, dptr<uint64_t>(c->uA), dptr<uint64_t>(c->uB),
+                                dptr<uint64_t>(c->samples2), c->jobs2, barrier2, eo, no_dd, st, false, none, {});
+  if (s != BSORT_OK) return s;
+  const ExpandCaps caps{std::min(c->uA.cap, c->uB.cap) / 8, c->pre.cap / 4, c->stream.cap, c->offsets.cap / 4};
+  LAUNCH(kExpand, moved,
+         launch_expand(dptr<ExpandDesc>(c->plan2, seg_bytes + barrier_bytes), ne, max_tiles, dptr<uint64_t>(c->uA),
+                       dptr<uint64_t>(c->uB), dptr<uint32_t>(c->pre), eo, dptr<Meta>(c->sticky), caps, st),
+         "expand");
+  return BSORT_OK;
+}
+
 // Runs the whole path over `ndocs` documents that sit at d_in + offs[i]
 // (lens[i] bytes each) in device memory.  Leaves the outputs in c->counts,
 // c->offsets, c->stream and the host copy of the meta region in c->h_meta.
@@ -519,23 +972,12 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   }
 
   // ---- bucket layout: one segment per (document, length) ----
-  // Groups (T = one K4 tile of the bucket's key width; table order below):
-  //   0..3  W = 1, 2, 4, 8 and more than 8T keys: K4 into runs of k4_runs or
-  //         k4_runs_small tiles, then K5 merge passes (one launch per pass
-  //         and width); group 4 unused
-  //   5     (4T, 8T] keys: K4 in clusters of 8        6   (2T, 4T]: clusters of 4
-  //   7     (T, 2T]: clusters of 2                      8   (32 KPT, T]: single CTAs
-  //   9     at most 32 lanes x KPT keys: one warp each
-  //   10,11 keys of 16 / 32 words (65..128 / 129..255 letters): the narrow-tile
-  //         kernels of k_sort.cu
-  constexpr int kGroups = 12;
   for (uint32_t d = 0; d < ndocs; ++d)
     if (h_hist[(size_t)d * kHist] != 0) c->doc_status[d] = BSORT_E_WORD_TOO_LONG;
   std::vector<Segment>& cand = c->segv;
   cand.clear();
   std::vector<uint8_t>& group = c->groupv;
   group.clear();
-  uint32_t group_n[kGroups] = {};
   uint64_t big_tiles = 0;  // merge tiles of the buckets that need merge passes
   for (uint32_t d = 0; d < ndocs; ++d) {
     if (c->doc_status[d] != BSORT_OK) continue;
@@ -551,166 +993,92 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
         sg.out_word = word_before;
         sg.stream_off = byte_before;
         sg.doc_stream0 = h_lbase[d];
-        const int W = width_of_len(L);
-        const uint32_t T = W >= 16 ? 0u : tile2_keys(W);
-        uint8_t gi;
-        sg.run0 = n;
-        sg.passes = 0;
-        if (W >= 16) {
-          gi = W == 16 ? 10 : 11;
-          sg.run0 = (uint32_t)tile_of_width(W);
-          sg.passes = merge_passes(n, sg.run0);
-        } else if (n <= warp_keys(W)) {
-          gi = 9;
-        } else if (n <= T) {
-          gi = 8;
-        } else if (n <= 2 * T) {
-          gi = 7;
-        } else if (n <= 4 * T) {
-          gi = 6;
-        } else if (n <= (uint32_t)kSuperCluster * T) {
-          gi = 5;
-        } else {  // needs merge passes: runs and passes are set below
-          gi = (uint8_t)class_of_width(W);
-          big_tiles += (n + merge2_keys(W) - 1) / merge2_keys(W);
-        }
-        sg.final_buf = sg.passes & 1u;
+        const uint8_t gi = group_of(sg, big_tiles);
         cand.push_back(sg);
         group.push_back(gi);
-        ++group_n[gi];
       }
       word_before += n;
       byte_before += L * n;
     }
   }
   const uint32_t nseg = (uint32_t)cand.size();
-  // The buckets that need merge passes leave K4 as runs of k4_runs tiles
-  // when their merges are large enough to be pipelined (the passes then run
-  // at HBM speed, cheaper than more cluster levels), else as runs of
-  // k4_runs_small tiles (fewer passes, fewer launches).
-  const uint32_t piped_grid = (uint32_t)(c->sm_count * merge_piped_ctas_per_sm());
-  const int runs =
-      big_tiles >= (uint64_t)c->tune.piped_min * piped_grid ? c->tune.k4_runs : c->tune.k4_runs_small;
-  for (uint32_t i = 0; i < nseg; ++i)
-    if (group[i] < 4) {
-      Segment& sg = cand[i];
-      sg.run0 = (uint32_t)runs * tile2_keys(width_of_len(sg.L));
-      sg.passes = merge_passes(sg.n, sg.run0);
-      sg.final_buf = sg.passes & 1u;
-    }
-  // Table order: the groups that K4 finishes (clusters of 8, 4, 2, 1), with
-  // the groups that need merge passes (0..3, and the unused 4) placed just
-  // before the one whose cluster size makes their runs, so that every K4
-  // launch and every width's merge chain covers one contiguous range; then
-  // the warp sort and the wide keys.
-  int order[kGroups], n_ord = 0;
-  for (int gc : {5, 6, 7, 8}) {
-    if (kSuperCluster >> (gc - 5) == runs || (runs > kSuperCluster && gc == 5))
-      for (int g = 0; g < 5; ++g) order[n_ord++] = g;
-    order[n_ord++] = gc;
-  }
-  for (int g : {9, 10, 11}) order[n_ord++] = g;
-  int pos_of[kGroups];
-  for (int q = 0; q < kGroups; ++q) pos_of[order[q]] = q;
-  // stable counting sort of the candidates by table position
-  uint32_t pbeg[kGroups + 1] = {};
-  for (int q = 0; q < kGroups; ++q) pbeg[q + 1] = pbeg[q] + group_n[order[q]];
-  auto gb = [&](int g) { return pbeg[pos_of[g]]; };      // first segment of group g
-  auto ge = [&](int g) { return pbeg[pos_of[g] + 1]; };  // one past its last
+  // The duplicate-aware sort takes the buckets that would need merge passes
+  // (keys of at most 8 words): K4 hands their sorted runs' distinct keys to a
+  // hash table per bucket instead of writing the runs back.
+  std::vector<uint32_t>& dd_seg = c->dd_seg;  // candidate index of each such bucket
+  dd_seg.clear();
+  if (c->tune.dedupe)
+    for (uint32_t i = 0; i < nseg; ++i)
+      if (group[i] < 4) {
+        cand[i].flags = kSegDedupe | ((uint32_t)dd_seg.size() << 8);
+        dd_seg.push_back(i);
+      }
+  const uint32_t ndd = (uint32_t)dd_seg.size();
   // the layout is built in place in the page-locked upload buffer: segments,
-  // the (document, length) -> segment lookup and the zeroed slot cursors of
-  // K3, which go to the device in one copy
+  // the (document, length) -> segment lookup, the zeroed slot cursors of K3
+  // and grid-barrier counters of the merge chains, the distinct-key counters
+  // and the hash-insert descriptors, which go to the device in one copy
   const size_t seg_bytes = align_up(sizeof(Segment) * std::max<size_t>(nseg, 1), 256);
   const size_t lookup_bytes = align_up(4ull * ndocs * kHist, 256);
-  // (after the cursors: the grid-barrier counters of the merge chains)
   const size_t cursor_bytes = align_up(4ull * (std::max<uint32_t>(nseg, 1) + 4), 256);
-  const size_t plan_bytes = seg_bytes + lookup_bytes + cursor_bytes;
+  const size_t ucnt_bytes = align_up(4ull * std::max<uint32_t>(ndd, 1), 256);
+  const size_t ins_bytes = align_up(sizeof(DedupeIns) * std::max<uint32_t>(ndd, 1), 256);
+  const size_t plan_bytes = seg_bytes + lookup_bytes + cursor_bytes + ucnt_bytes + ins_bytes;
   GROW_HOST(c->h_plan, plan_bytes, "layout");
   Segment* const segs = hptr<Segment>(c->h_plan);
   uint32_t* const lookup = hptr<uint32_t>(c->h_plan, seg_bytes);
   std::memset(lookup, 0xFF, 4ull * ndocs * kHist);  // kNoSegment
-  std::memset(hptr<char>(c->h_plan, seg_bytes + lookup_bytes), 0, cursor_bytes);
-  {
-    uint32_t at[kGroups];
-    for (int q = 0; q < kGroups; ++q) at[q] = pbeg[q];
-    for (uint32_t i = 0; i < nseg; ++i) segs[at[pos_of[group[i]]]++] = cand[i];
-  }
-  // K4 launches: cluster size, its own group, and the table range it covers
-  // (the merge-pass groups too, for the cluster size that makes their runs)
-  struct K4Launch {
-    int cluster;
-    int gc;
-    uint32_t sbeg = 0, send = 0;
-    uint32_t supertiles = 0;
-    int max_w = 1;
-    double key_bytes = 0;
-    double levels = 0;  // key-levels: each key times log2 of the sorted run it ends in
-  };
-  K4Launch k4[5] = {{8, 5}, {4, 6}, {2, 7}, {1, 8}, {16, -1}};  // the last: clusters of 16, runs only
-  for (K4Launch& l : k4) {
-    if (l.gc < 0) {
-      l.sbeg = runs == l.cluster ? gb(0) : 0u;
-      l.send = runs == l.cluster ? ge(4) : 0u;
-    } else {
-      l.sbeg = l.cluster == runs ? gb(0) : gb(l.gc);
-      l.send = ge(l.gc);
-    }
-  }
-  // bytes of a bucket's output: its letters and, if asked for, its offsets
+  std::memset(hptr<char>(c->h_plan, seg_bytes + lookup_bytes), 0, cursor_bytes + ucnt_bytes);
+  DedupeIns* const ins = hptr<DedupeIns>(c->h_plan, seg_bytes + lookup_bytes + cursor_bytes + ucnt_bytes);
   const uint64_t off_bytes = c->cfg.want_offsets ? 4 : 0;
-  auto out_bytes = [&](const Segment& sg) { return (double)sg.n * (sg.L + off_bytes); };
-  uint64_t key_words = 0, smp_words = 0, kb[kGroups] = {};
-  double ob[kGroups] = {};
-  uint32_t etile = 0, wtiles[2] = {0, 0}, wpasses[2] = {0, 0};
-  uint32_t mtiles[4] = {}, mpasses[4] = {};
+  SortPlan p1;
+  plan_sorts(c, cand, group, big_tiles, false, off_bytes, segs, p1);
+  uint64_t htab_words = 0, uniq_words = 0;
+  std::vector<uint32_t>& dd_pos = c->dd_pos;  // table position of each duplicate-aware bucket
+  dd_pos.assign(ndd, 0);
   for (uint32_t i = 0; i < nseg; ++i) {
     Segment& sg = segs[i];
-    const int W = width_of_len(sg.L);
-    int q = 0;
-    while (i >= pbeg[q + 1]) ++q;
-    const int gi = order[q];
-    sg.key_off = key_words;
-    key_words += align_up((size_t)sg.n * W, 16);
-    kb[gi] += 8ull * W * sg.n;
-    ob[gi] += out_bytes(sg);
-    if (gi >= 10) {  // only the wide keys go through K6
-      sg.etile0 = etile;
-      etile += (sg.n + tile_of_width(W) - 1) / tile_of_width(W);
-    }
-    if (gi < 4) {
-      // merge samples: one key in 32 (read by the pipelined merges' cuts)
-      sg.smp_off = (uint32_t)smp_words;
-      smp_words += (uint64_t)(sg.n + 31) / 32 * W;
-      sg.tile0 = mtiles[gi];
-      mtiles[gi] += (sg.n + merge2_keys(W) - 1) / merge2_keys(W);
-      mpasses[gi] = std::max(mpasses[gi], sg.passes);
-    }
-    for (K4Launch& l : k4)
-      if (i >= l.sbeg && i < l.send) {
-        const uint32_t super = (uint32_t)l.cluster * tile2_keys(W);
-        sg.stile0 = l.supertiles;
-        l.supertiles += (sg.n + super - 1) / super;
-        l.max_w = std::max(l.max_w, W);
-        // keys in, then runs out for K5 or the sorted words out
-        l.key_bytes += 8.0 * W * sg.n + (sg.passes ? 8.0 * W * sg.n : out_bytes(sg));
-        l.levels += (double)sg.n * ceil_log2(std::min<uint64_t>(sg.n, (uint64_t)super));
-      }
-    if (gi >= 10) {
-      sg.tile0 = wtiles[gi - 10];
-      wtiles[gi - 10] += (sg.n + sg.run0 - 1) / sg.run0;
-      wpasses[gi - 10] = std::max(wpasses[gi - 10], sg.passes);
-    }
     lookup[(size_t)sg.doc * kHist + sg.L] = i;
+    if (sg.flags & kSegDedupe) {
+      const uint32_t di = seg_dedupe_index(sg);
+      const uint32_t W = (uint32_t)width_of_len(sg.L);
+      DedupeIns& d = ins[di];
+      d = DedupeIns{};
+      d.hbits = (uint32_t)ceil_log2(2ull * sg.n);
+      d.Wp = 2 * W;
+      d.n = sg.n;
+      d.htab_off = htab_words;
+      htab_words += (1ull << d.hbits) * (W + 1);
+      d.uniq_off = uniq_words;
+      uniq_words += align_up((size_t)sg.n * d.Wp, 16);
+      dd_pos[di] = i;
+    }
   }
 
   // ---- upload the layout, size the key and output buffers ----
   GROW(c->plan, plan_bytes, "layout");
-  GROW(c->keysA, 8 * std::max<uint64_t>(key_words, 16), "keys");
-  GROW(c->keysB, 8 * std::max<uint64_t>(key_words, 16), "keys");
-  GROW(c->samples, 8 * std::max<uint64_t>(smp_words, 16), "merge samples");
+  GROW(c->keysA, 8 * std::max<uint64_t>(p1.key_words, 16), "keys");
+  GROW(c->keysB, 8 * std::max<uint64_t>(p1.key_words, 16), "keys");
+  GROW(c->samples, 8 * std::max<uint64_t>(p1.smp_words, 16), "merge samples");
   GROW(c->counts, 8ull * ndocs * kHist, "counts");
   GROW(c->offsets, 4ull * ((uint64_t)n_total + ndocs), "offsets");
   GROW(c->stream, (size_t)s_total + 16, "stream");
+  DedupeOut ddo{nullptr, nullptr, nullptr, nullptr, 0};
+  if (ndd) {
+    const void* old_tab = c->htab.p;
+    GROW(c->htab, 8 * htab_words, "hash tables");
+    GROW(c->uA, 8 * std::max<uint64_t>(uniq_words, 16), "distinct keys");
+    GROW(c->uB, 8 * std::max<uint64_t>(uniq_words, 16), "distinct keys");
+    if (c->htab.p != old_tab || ++c->gen == 0) {
+      // a new table (or a generation counter that wrapped): every slot must
+      // carry a generation that no call uses, 0
+      CK(cudaMemsetAsync(c->htab.p, 0, c->htab.cap, st), "clear hash tables");
+      c->gen = 1;
+    }
+    ddo = DedupeOut{dptr<DedupeIns>(c->plan, seg_bytes + lookup_bytes + cursor_bytes + ucnt_bytes),
+                    dptr<uint64_t>(c->htab), dptr<uint64_t>(c->uA),
+                    dptr<uint32_t>(c->plan, seg_bytes + lookup_bytes + cursor_bytes), c->gen};
+  }
   CK(cudaMemcpyAsync(c->plan.p, c->h_plan.p, plan_bytes, cudaMemcpyHostToDevice, st), "copy layout");
   Segment* const segs_dev = dptr<Segment>(c->plan);
   uint32_t* const lookup_dev = dptr<uint32_t>(c->plan, seg_bytes);
@@ -725,11 +1093,10 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       c->kind_launches[kHostGap] += 1;
     }
   }
-  const Segment* d_segs = segs_dev;
   uint64_t* kA = dptr<uint64_t>(c->keysA);
   uint64_t* kB = dptr<uint64_t>(c->keysB);
   uint64_t key_bytes_all = 0;
-  for (int g = 0; g < kGroups; ++g) key_bytes_all += kb[g];
+  for (int g = 0; g < kGroups; ++g) key_bytes_all += p1.kb[g];
   const uint32_t grid_cap = (uint32_t)c->sm_count * 16;
   const EmitOut eo{dptr<uint8_t>(c->stream), dptr<uint32_t>(c->offsets), c->cfg.want_offsets};
   {
@@ -740,157 +1107,34 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     LAUNCH(kScatter,
            (double)s_total + 4.0 * n_total + key_bytes_all + (4.0 + 8.0) * kHist * ndocs + (off_bytes ? 12.0 : 0.0) * ndocs,
            launch_scatter(dptr<uint32_t>(c->starts), dptr<uint8_t>(c->letters), d_wbase, d_lbase, d_item0, ndocs,
-                          items, grid, lookup_dev, d_segs, cursor_dev, kA, d_hist, dptr<uint64_t>(c->counts), eo, st),
+                          items, grid, lookup_dev, segs_dev, cursor_dev, kA, d_hist, dptr<uint64_t>(c->counts), eo, st),
            "K3 scatter");
   }
-  // K4: the launch that makes the merge passes' runs first, on the call's
-  // stream, so that the merges (which wait for it alone) start as early as
-  // they can; then the other launches, largest first, each on a side stream
-  // at the same time (they sort other buckets), joined back at the end of
-  // the call.  (With k4_streams=0 in the tune table every launch stays on the
-  // call's stream, one after another: how the autotuner times each class
-  // alone.)
-  int k4_order[5], n4 = 0;
-  for (int i = 0; i < 5; ++i)
-    if (k4[i].supertiles) k4_order[n4++] = i;
-  std::stable_sort(k4_order, k4_order + n4, [&](int a, int b) {
-    const bool ra = k4[a].cluster == runs, rb = k4[b].cluster == runs;
-    if (ra != rb) return ra;
-    return k4[a].levels > k4[b].levels;
-  });
-  const bool small_work = ge(9) > gb(9) || n4 > 1;  // the warp sort, or more than one K4 launch
-  const bool side = small_work && c->tune.k4_streams;
-  if (side) CK(cudaEventRecord(c->fork_ev, st), "fork");
-  int used = 0;
-  cudaStream_t joined[bsort_ctx::kSide];
-  auto side_stream = [&]() -> cudaStream_t {
-    if (!side) return st;
-    cudaStream_t sx = c->side[used];
-    joined[used++] = sx;
-    return sx;
+  // K4, K5, K6 of the buckets.  The first K4 launch (on the call's stream)
+  // sorts the buckets that need merge passes: for the duplicate-aware sort,
+  // the distinct-key counts are read back right after it, while the other
+  // launches run on.
+  std::vector<cudaStream_t> joined;
+  uint32_t* h_ucnt = nullptr;
+  auto after_first = [&]() -> bsort_status {
+    if (!ndd) return BSORT_OK;
+    GROW_HOST(c->h_ucnt, 4ull * ndd, "distinct-key counts");
+    h_ucnt = hptr<uint32_t>(c->h_ucnt);
+    CK(cudaMemcpyAsync(h_ucnt, ddo.ucnt, 4ull * ndd, cudaMemcpyDeviceToHost, st), "read distinct-key counts");
+    CK(cudaEventRecord(c->dedupe_ev, st), "distinct-key counts event");
+    return BSORT_OK;
   };
-  for (int q = 0; q < n4; ++q) {
-    const K4Launch& l = k4[k4_order[q]];
-    cudaStream_t sx = st;
-    if (q > 0 && side) {
-      sx = side_stream();
-      CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
-    }
-    Trace tr_(c, sx, kTileSort, l.key_bytes, l.levels);
-    tr_.variant = (uint32_t)l.cluster;
-    const int cls = l.cluster == 1 ? 0 : l.cluster == 2 ? 1 : l.cluster == 4 ? 2 : 3;  // 16 as 8
-    CK(tr_.done(launch_tile_sort2(l.cluster, c->tune.k4_lanes[cls], c->tune.k4_threads[cls], d_segs, l.sbeg, l.send, l.supertiles, c->sm_count, l.max_w, kA,
-                                  eo, d_sticky, c->cfg.wait_limit, sx)),
-       "K4 tile_sort");
+  bsort_status s = launch_sorts(c, p1, segs, segs_dev, kA, kB, dptr<uint64_t>(c->samples), c->jobs, barrier_dev, eo,
+                                ddo, st, true, joined, after_first);
+  if (s != BSORT_OK) return s;
+  if (ndd) {
+    s = sort_distinct(c, segs, ins, ndd, h_ucnt, eo, st);
+    if (s != BSORT_OK) return s;
   }
-  if (ge(9) > gb(9)) {
-    cudaStream_t sx = side_stream();
-    if (side) CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
-    double levels = 0;
-    for (uint32_t i = gb(9); i < ge(9); ++i) levels += (double)segs[i].n * ceil_log2(segs[i].n);
-    Trace tr_(c, sx, kTileSort, (double)kb[9] + ob[9], levels);
-    CK(tr_.done(launch_warp_sort(d_segs, gb(9), ge(9), kA, eo, sx)), "K4 warp_sort");
-  }
-  for (int g = 10; g < 12; ++g) {
-    const uint32_t tiles = wtiles[g - 10];
-    if (!tiles) continue;
-    double levels = 0;
-    for (uint32_t k = gb(g); k < ge(g); ++k)
-      levels += (double)segs[k].n * ceil_log2(std::min<uint64_t>(segs[k].n, segs[k].run0));
-    Trace tr_(c, st, kTileSort, 2.0 * kb[g], levels);
-    tr_.variant = 1;
-    CK(tr_.done(
-           launch_tile_sort(g == 10 ? 16 : 32, d_segs, gb(g), ge(g), tiles, std::min(tiles, grid_cap), kA,
-                            d_sticky, c->cfg.wait_limit, st)),
-       "K4 tile_sort (wide keys)");
-  }
-  // K5: merge passes over the buckets that need them, one launch per pass and
-  // width.  With at least two tiles per resident CTA the pass is pipelined: a
-  // cut kernel lists every tile's slices first, so that the merge kernel can
-  // load one tile while it merges another.  The widths' chains of passes are
-  // independent: with more than one, each runs on a side stream of its own,
-  // so that one chain's latency-bound launches overlap another's merges.
-  uint64_t job_at[4] = {}, jobs_total = 0;
-  int chains = 0;
-  for (int g = 0; g < 4; ++g) {
-    if (mpasses[g]) ++chains;
-    if (mtiles[g] >= c->tune.piped_min * piped_grid) {
-      job_at[g] = jobs_total;
-      jobs_total += mtiles[g] + 1;  // and the end sentinel
-    }
-  }
-  if (jobs_total) GROW(c->jobs, sizeof(TileJob) * jobs_total, "merge jobs");
-  if (chains > 1) CK(cudaEventRecord(c->fork_ev, st), "fork");
-  int nj = 0;
-  for (int g = 0; g < 4; ++g) {
-    if (!mpasses[g]) continue;
-    const int W = width_of_class(g);
-    cudaStream_t sx = st;
-    if (chains > 1) {
-      sx = c->side[bsort_ctx::kChainSide + g];
-      CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
-    }
-    auto moved_in = [&](uint32_t p) {  // keys in, then keys out or, at a bucket's last pass, its words
-      double moved = 0;
-      for (uint32_t i = gb(g); i < ge(g); ++i)
-        if (segs[i].passes > p)
-          moved += 8.0 * W * segs[i].n + (segs[i].passes == p + 1 ? out_bytes(segs[i]) : 8.0 * W * segs[i].n);
-      return moved;
-    };
-    if (mtiles[g] >= c->tune.piped_min * piped_grid) {
-      for (uint32_t p = 0; p < mpasses[g]; ++p) {
-        const uint64_t* src = (p & 1) ? kB : kA;
-        uint64_t* dst = (p & 1) ? kA : kB;
-        TileJob* jobs = dptr<TileJob>(c->jobs) + job_at[g];
-        uint64_t* smp = dptr<uint64_t>(c->samples);
-        {
-          Trace tr_(c, sx, kMergeCut, 0.0);
-          tr_.variant = (uint32_t)W;
-          CK(tr_.done(launch_merge_cut(W, d_segs, gb(g), ge(g), mtiles[g], p, src, smp, jobs, sx)), "K5 merge cut");
-        }
-        Trace tr_(c, sx, kMerge, moved_in(p));
-        tr_.variant = (uint32_t)W;
-        CK(tr_.done(launch_merge_piped(W, jobs, mtiles[g], piped_grid, src, dst, smp, eo, sx)), "K5 merge_pass");
-      }
-    } else {
-      // small passes: all of them in one launch, grid barriers between them
-      double moved = 0;
-      for (uint32_t p = 0; p < mpasses[g]; ++p) moved += moved_in(p);
-      Trace tr_(c, sx, kMerge, moved);
-      tr_.variant = (uint32_t)W;
-      CK(tr_.done(launch_merge_pass2(W, d_segs, gb(g), ge(g), mtiles[g],
-                                     std::min<uint32_t>(mtiles[g], (uint32_t)c->sm_count * 8), 0, mpasses[g], kA,
-                                     kB, eo, barrier_dev + g, d_sticky, c->cfg.wait_limit, sx)),
-         "K5 merge_pass");
-    }
-    if (chains > 1) {
-      CK(cudaEventRecord(c->join_ev[bsort_ctx::kChainSide + nj], sx), "join");
-      ++nj;
-    }
-  }
-  for (int g = 10; g < 12; ++g) {
-    const int W = g == 10 ? 16 : 32;
-    const uint32_t tiles = wtiles[g - 10];
-    for (uint32_t p = 0; p < wpasses[g - 10]; ++p) {
-      double moved = 0;
-      for (uint32_t i = gb(g); i < ge(g); ++i)
-        if (segs[i].passes > p) moved += 16.0 * W * segs[i].n;
-      LAUNCH(kMerge, moved,
-             launch_merge_pass(W, d_segs, gb(g), ge(g), tiles, std::min(tiles, grid_cap), p, (p & 1) ? kB : kA,
-                               (p & 1) ? kA : kB, st),
-             "K5 merge_pass (wide keys)");
-    }
-  }
-  for (int i = 0; i < nj; ++i) CK(cudaStreamWaitEvent(st, c->join_ev[bsort_ctx::kChainSide + i], 0), "join");
-  // the tile sorts on side streams
-  for (int i = 0; i < used; ++i) {
+  // the launches on side streams
+  for (size_t i = 0; i < joined.size(); ++i) {
     CK(cudaEventRecord(c->join_ev[i], joined[i]), "join");
     CK(cudaStreamWaitEvent(st, c->join_ev[i], 0), "join");
-  }
-  // K6: the words of the wide keys (every other bucket was emitted by its sort)
-  if (etile) {
-    LAUNCH(kEmit, (double)kb[10] + kb[11] + ob[10] + ob[11],
-           launch_emit(d_segs, gb(10), ge(11), etile, std::min(etile, grid_cap), kA, kB, eo, st), "K6 emit");
   }
   return BSORT_OK;
 }
@@ -925,9 +1169,11 @@ bsort_status read_back(bsort_ctx* c, cudaStream_t st, size_t off_base, size_t st
   const uint32_t* hh = hptr<uint32_t>(c->h_meta, c->ml.hist);
   for (size_t i = 0; i < (size_t)ndocs * kHist; ++i) hc[i] = (i % kHist) ? hh[i] : 0;
   CK(cudaStreamSynchronize(st), "wait for results");
-  if (hs->err_timeout) {
+  if (hs->err_timeout || hs->err_internal) {
     CK(cudaMemsetAsync(c->sticky.p, 0, sizeof(Meta), st), "clear timeout flag");
     CK(cudaStreamSynchronize(st), "clear timeout flag");
+    if (!hs->err_timeout)
+      return fail(c, BSORT_E_CUDA, "a consistency check of the sort kernels failed (site " + std::to_string(hs->err_site) + ")");
     return fail(c, BSORT_E_TIMEOUT, "a bounded device wait ran out");
   }
   return BSORT_OK;
@@ -993,7 +1239,8 @@ bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
   if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->counts_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->counts_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->dedupe_ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     bsort_destroy(c);  // frees whatever was created
     return BSORT_E_CUDA;
@@ -1022,13 +1269,17 @@ void bsort_destroy(bsort_ctx* c) {
   bsort_serve_shutdown(c);
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
-  for (DevBuf* b : {&c->sticky, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB, &c->counts, &c->offsets, &c->stream, &c->jobs, &c->samples})
+  for (DevBuf* b : {&c->sticky, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB,
+                    &c->counts, &c->offsets, &c->stream, &c->jobs, &c->samples, &c->htab, &c->uA, &c->uB, &c->plan2,
+                    &c->samples2, &c->jobs2, &c->pre})
     if (b->p) cudaFree(b->p);
-  for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets, &c->h_stream, &c->h_flag})
+  for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets,
+                     &c->h_stream, &c->h_flag, &c->h_plan2, &c->h_ucnt})
     if (b->p) cudaFreeHost(b->p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->counts_ev) cudaEventDestroy(c->counts_ev);
+  if (c->dedupe_ev) cudaEventDestroy(c->dedupe_ev);
   for (int i = 0; i < bsort_ctx::kSide; ++i) {
     if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
     if (c->side[i]) cudaStreamDestroy(c->side[i]);
@@ -1316,9 +1567,10 @@ bsort_status bsort_device_finish(bsort_ctx* c, void* stream) {
   Meta* hs = hptr<Meta>(c->h_sticky);
   CK(cudaMemcpyAsync(hs, c->sticky.p, sizeof(Meta), cudaMemcpyDeviceToHost, st), "read status");
   CK(cudaStreamSynchronize(st), "wait for the device work");
-  if (hs->err_timeout) {
+  if (hs->err_timeout || hs->err_internal) {
     CK(cudaMemsetAsync(c->sticky.p, 0, sizeof(Meta), st), "clear timeout flag");
     CK(cudaStreamSynchronize(st), "clear timeout flag");
+    if (!hs->err_timeout) return fail(c, BSORT_E_CUDA, "a consistency check of the sort kernels failed");
     return fail(c, BSORT_E_TIMEOUT, "a bounded device wait of the sort kernels ran out (the outputs are not valid)");
   }
   return BSORT_OK;

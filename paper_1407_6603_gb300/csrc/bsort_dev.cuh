@@ -96,7 +96,8 @@ struct Meta {
   uint32_t err_timeout;   // bounded waits that ran out: in the sticky copy, those of the sort
                           // kernels (kept until read); in a call's meta, those of its K1
   uint32_t err_prev;      // a call's meta: the sticky count when its K1 ran (earlier calls)
-  uint32_t pad[2];
+  uint32_t err_internal;  // sticky: a consistency check of the sort kernels failed
+  uint32_t err_site;      // sticky: the first such check's site (kernel << 8 | place)
 };
 
 // One (document, length) bucket.  The host orders the table by the K4/K5
@@ -117,7 +118,48 @@ struct Segment {
   uint32_t passes;      // merge passes the bucket needs after K4
   uint32_t run0;        // length of the sorted runs K4 leaves
   uint32_t smp_off;     // pipelined merges: first u64 word of the bucket's merge samples
+  uint32_t flags;       // kSegKeysOut, kSegDedupe; bits 8..31: the bucket's dedupe index
+};
+// Segment flags.  kSegKeysOut: the sorted keys stay in the key buffer (final_buf)
+// instead of being emitted as words (the distinct-word arrays of the
+// duplicate-aware sort).  kSegDedupe: K4 sorts the bucket's runs and hands each
+// run's distinct keys, with their multiplicities, to the bucket's hash table.
+constexpr uint32_t kSegKeysOut = 1u, kSegDedupe = 2u;
+__host__ __device__ inline uint32_t seg_dedupe_index(const Segment& s) { return s.flags >> 8; }
+
+// Duplicate-aware sort (an option of the sort phase; the result is the same):
+// a bucket's distinct keys are collected in a hash table with their counts,
+// sorted, and expanded by their counts.  Per bucket, for K4's hash inserts:
+struct DedupeIns {
+  uint64_t htab_off;  // first u64 word of the bucket's table: 2^hbits slots of 1 + W words
+  uint64_t uniq_off;  // first u64 word of its distinct-key array: entries of Wp words
+                      // (the key's W words, its count, zeros), at most n entries
+  uint32_t hbits;
+  uint32_t Wp;        // next_pow2(W + 1)
+  uint32_t n;         // the bucket's words: the array's capacity in entries
   uint32_t pad;
+};
+// Per bucket, for the expansion after the distinct keys are sorted:
+struct ExpandDesc {
+  uint64_t uniq_off;  // the sorted distinct-key array (in the buffer final_buf names)
+  uint64_t pre_off;   // u32 index of its exclusive prefix of counts (U + 1 entries)
+  uint32_t U;         // distinct keys
+  uint32_t n;         // words (the sum of the counts)
+  uint32_t L;
+  uint32_t Wp;
+  uint32_t final_buf;
+  uint32_t stream_off, out_word, doc_stream0;
+};
+constexpr uint32_t kExpandTileWords = 2048;
+// words per output tile of the expansion for keys of W u64 words
+__host__ __device__ inline uint32_t expand_tile(uint32_t W) { return kExpandTileWords / W; }
+// Where K4's hash inserts go (one call's tables, arrays and counters).
+struct DedupeOut {
+  const DedupeIns* ins;
+  uint64_t* htab;
+  uint64_t* uniq;
+  uint32_t* ucnt;  // distinct keys per bucket so far (zeroed per call)
+  uint32_t gen;    // the call's generation: slots stamped with another are empty
 };
 
 // One output tile of a pipelined merge pass (K5), as the cut kernel leaves it:
@@ -359,16 +401,16 @@ cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, 
 // odd-even transposition group.
 cudaError_t launch_tile_sort2(int cluster, int lanes, int threads, const Segment* segs, uint32_t sbeg, uint32_t send,
                               uint32_t supertiles, int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
-                              uint64_t wait_limit, cudaStream_t st);
+                              uint64_t wait_limit, DedupeOut dd, cudaStream_t st);
 cudaError_t launch_tile_sort2_g2(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                                  int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
-                                 uint64_t wait_limit, cudaStream_t st);
+                                 uint64_t wait_limit, DedupeOut dd, cudaStream_t st);
 cudaError_t launch_tile_sort2_g4(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                                  int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
-                                 uint64_t wait_limit, cudaStream_t st);
+                                 uint64_t wait_limit, DedupeOut dd, cudaStream_t st);
 cudaError_t launch_tile_sort2_g8(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                                  int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
-                                 uint64_t wait_limit, cudaStream_t st);
+                                 uint64_t wait_limit, DedupeOut dd, cudaStream_t st);
 // Merge passes pass0 .. pass0 + npass - 1 (keys between kA and kB, pass p
 // reading kA when p is even); npass > 1 makes one cooperative launch whose
 // passes are separated by grid barriers counted on *barrier (zeroed).
@@ -388,5 +430,18 @@ cudaError_t launch_merge_piped(int W, const TileJob* jobs, uint32_t tiles, uint3
 int merge_piped_ctas_per_sm();
 cudaError_t launch_emit(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,
                         const uint64_t* keysA, const uint64_t* keysB, EmitOut eo, cudaStream_t st);
+// The expansion of the duplicate-aware sort: per bucket the exclusive prefix
+// of the sorted distinct keys' counts (one CTA per bucket), then the words,
+// in output tiles of kExpandTileWords / W (max_tiles: the most tiles of one
+// bucket).  The counts must add up to each bucket's word count; a check marks
+// the call failed otherwise.
+// Sizes of the buffers the expansion touches (u64 words of each distinct-key
+// buffer, u32 entries of the prefixes, stream bytes, offsets): every
+// descriptor is checked against them.
+struct ExpandCaps {
+  uint64_t u_words, pre, stream, offsets;
+};
+cudaError_t launch_expand(const ExpandDesc* ed, uint32_t nbuckets, uint32_t max_tiles, const uint64_t* uA,
+                          const uint64_t* uB, uint32_t* pre, EmitOut eo, Meta* meta, ExpandCaps caps, cudaStream_t st);
 
 }  // namespace bsort

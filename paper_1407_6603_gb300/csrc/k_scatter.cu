@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const Segment* __restrict
     __syncthreads();
     const Segment sg = segs[s_seg];
     __syncthreads();
+    if (sg.flags & kSegKeysOut) continue;  // sorted keys wanted, not words
     const int W = width_of_len(sg.L);
     const uint32_t T = (uint32_t)tile_of_width(W);
     const uint32_t j0 = (it - sg.etile0) * T;

@@ -31,6 +31,14 @@ __device__ void warp_sort_g(const Segment& sg, const uint64_t* g, uint32_t n, co
   }
   oets_registers<W, KPT>(k);
   if (G > 1) oets_lanes<W, KPT, (G > 1 ? G : 2)>(k);
+  if (sg.flags & kSegKeysOut) {  // the sorted keys stay in place
+#pragma unroll
+    for (int i = 0; i < KPT; ++i) {
+      const uint32_t p = lane * KPT + i;
+      if (p < n) kstore<W>(const_cast<uint64_t*>(g) + (size_t)p * W, k[i]);
+    }
+    return;
+  }
   // the bucket is sorted: each lane writes its keys' letters and offsets
   const uint32_t L = sg.L;
 #pragma unroll
@@ -112,7 +120,9 @@ __device__ void merge_tile(const Segment& sg, uint32_t si, uint32_t it, uint32_t
   const uint64_t* A = src + sg.key_off + ps * W;
   const uint64_t* B = A + (size_t)la * W;
   uint64_t* out = dst + sg.key_off + (ps + d0) * W;
-  const bool last = pass + 1 == sg.passes;  // this pass's output is the sorted bucket
+  // this pass's output is the sorted bucket, whose words go out (unless its
+  // sorted keys are what is wanted)
+  const bool last = pass + 1 == sg.passes && !(sg.flags & kSegKeysOut);
   if (lb == 0 && last) {  // odd run at the end of the bucket, already in place
     const uint64_t* a = A + (size_t)d0 * W;
     emit_tile<kM2Threads>(sg, (uint32_t)out0, cnt, [&](uint32_t j, uint32_t q) { return a[(size_t)j * W + q]; }, eo);
@@ -340,7 +350,9 @@ __global__ void __launch_bounds__(256) k_merge_cut(const Segment* __restrict__ s
       job.a_end = sg.key_off + (ps + la) * W;
       job.dst = sg.key_off + out0 * W;
       job.cnt = min(T, la + lb - d);
-      if (pass + 1 == passes) {
+      if (pass + 1 == passes && (sg.flags & kSegKeysOut)) {
+        // the sorted keys themselves are the result: written to dst, no samples
+      } else if (pass + 1 == passes) {
         job.L = sg.L;
         job.stream = sg.stream_off + (uint32_t)out0 * sg.L;
         job.word = sg.out_word + (uint32_t)out0;
@@ -499,12 +511,12 @@ cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, 
 
 cudaError_t launch_tile_sort2(int cluster, int lanes, int threads, const Segment* segs, uint32_t sbeg, uint32_t send,
                               uint32_t supertiles, int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
-                              uint64_t wait_limit, cudaStream_t st) {
+                              uint64_t wait_limit, DedupeOut dd, cudaStream_t st) {
   if (supertiles == 0) return cudaSuccess;
   switch (lanes) {
-    case 2: return launch_tile_sort2_g2(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 4: return launch_tile_sort2_g4(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 8: return launch_tile_sort2_g8(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 2: return launch_tile_sort2_g2(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
+    case 4: return launch_tile_sort2_g4(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
+    case 8: return launch_tile_sort2_g8(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
     default: return cudaErrorInvalidValue;
   }
 }

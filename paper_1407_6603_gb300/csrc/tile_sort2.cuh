@@ -27,6 +27,7 @@
 #include <cooperative_groups.h>
 
 #include "bsort_dev.cuh"
+#include "dedupe.cuh"
 #include "sort_common.cuh"
 
 namespace cg = cooperative_groups;
@@ -222,7 +223,7 @@ __device__ uint64_t* cluster_merge(uint64_t* buf0, uint64_t* buf1, uint64_t* buf
 template <int W, int CL, int G, int NTH>
 __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint64_t* keys, uint64_t* buf0,
                                uint64_t* buf1, uint64_t* buf2, uint64_t* bar, uint32_t& phase, const EmitOut& eo,
-                               Meta* meta, uint64_t wait_limit) {
+                               Meta* meta, uint64_t wait_limit, const DedupeOut& dd) {
   constexpr int KPT = kptn<W, NTH>();
   constexpr uint32_t T = NTH * KPT;
   constexpr uint32_t TW = T * W;
@@ -265,9 +266,11 @@ __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint6
   if constexpr (CL > 1) res = cluster_merge<W, CL, NTH>(buf0, buf1, buf2, r);
   if (lost) {
     // nothing of this supertile is written
-  } else if (sg.passes == 0) {  // the bucket is sorted: its words go straight out
+  } else if (sg.flags & kSegDedupe) {  // its distinct keys and their counts to the bucket's table
+    rle_insert<W, NTH>([&](uint32_t i) { return kload<W>(res + padw(i * W)); }, cnt, sg, dd, meta, wait_limit);
+  } else if (sg.passes == 0 && !(sg.flags & kSegKeysOut)) {  // the bucket is sorted: its words go straight out
     emit_tile<NTH>(sg, (uint32_t)j0, cnt, [&](uint32_t j, uint32_t q) { return res[padw(j * W + q)]; }, eo);
-  } else {  // a run of CL tiles for K5
+  } else {  // a run of CL tiles for K5 (or, kSegKeysOut, the sorted keys in place)
     for (uint32_t e = t; e < cnt * W; e += NTH) g[e] = res[padw(e)];
   }
   __syncthreads();
@@ -277,7 +280,7 @@ template <int CL, int G, int NTH>
 __global__ void __launch_bounds__(NTH, BSORT_K4_MIN_CTAS * 256 / NTH) k_tile_sort2(const Segment* __restrict__ segs, uint32_t sbeg,
                                                            uint32_t send, uint32_t nst, uint32_t buf_words,
                                                            uint64_t* keys, EmitOut eo, Meta* meta,
-                                                           uint64_t wait_limit) {
+                                                           uint64_t wait_limit, DedupeOut dd) {
   extern __shared__ __align__(128) uint64_t sm[];
   uint64_t* buf0 = sm;
   uint64_t* buf1 = sm + buf_words;
@@ -305,15 +308,15 @@ __global__ void __launch_bounds__(NTH, BSORT_K4_MIN_CTAS * 256 / NTH) k_tile_sor
     const Segment sg = segs[s_seg];
     __syncthreads();
     switch (width_of_len(sg.L)) {
-      case 1: sort_supertile<1, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
-      case 2: sort_supertile<2, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
+      case 1: sort_supertile<1, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd); break;
+      case 2: sort_supertile<2, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd); break;
       case 4:
         if constexpr (kptn<4, NTH>() >= 1)
-          sort_supertile<4, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit);
+          sort_supertile<4, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd);
         break;
       default:  // (launches with 8-word keys use 256 threads)
         if constexpr (kptn<8, NTH>() >= 1)
-          sort_supertile<8, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit);
+          sort_supertile<8, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd);
         break;
     }
   }
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(NTH, BSORT_K4_MIN_CTAS * 256 / NTH) k_tile_sor
 template <int CL, int G, int NTH>
 cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t nst, int max_grid,
                           int max_width, uint64_t* keys, const EmitOut& eo, Meta* meta, uint64_t wait_limit,
-                          cudaStream_t st) {
+                          const DedupeOut& dd, cudaStream_t st) {
   (void)max_width;
   const uint32_t buf_words = padded_words(2048u);
   const size_t smem = (size_t)(CL > 1 ? 3 : 1) * buf_words * 8;
@@ -362,7 +365,8 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
   }
   const uint32_t ncl = nst < (uint32_t)clusters * 2u ? nst : (uint32_t)clusters * 2u;
   cfg.gridDim = dim3(ncl * CL, 1, 1);
-  return cudaLaunchKernelEx(&cfg, k_tile_sort2<CL, G, NTH>, segs, sbeg, send, nst, buf_words, keys, eo, meta, wait_limit);
+  return cudaLaunchKernelEx(&cfg, k_tile_sort2<CL, G, NTH>, segs, sbeg, send, nst, buf_words, keys, eo, meta, wait_limit,
+                            dd);
 }
 
 // All cluster sizes and CTA sizes for one lane count G (each K4 translation
@@ -370,13 +374,13 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
 template <int G, int NTH>
 cudaError_t tile_sort2_cls(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                            int max_grid, int max_width, uint64_t* keys, const EmitOut& eo, Meta* meta,
-                           uint64_t wait_limit, cudaStream_t st) {
+                           uint64_t wait_limit, const DedupeOut& dd, cudaStream_t st) {
   switch (cluster) {
-    case 1: return tile_sort2_cl<1, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 2: return tile_sort2_cl<2, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 4: return tile_sort2_cl<4, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 8: return tile_sort2_cl<8, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
-    case 16: return tile_sort2_cl<16, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 1: return tile_sort2_cl<1, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
+    case 2: return tile_sort2_cl<2, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
+    case 4: return tile_sort2_cl<4, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
+    case 8: return tile_sort2_cl<8, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
+    case 16: return tile_sort2_cl<16, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -384,12 +388,12 @@ cudaError_t tile_sort2_cls(int cluster, const Segment* segs, uint32_t sbeg, uint
 template <int G>
 cudaError_t tile_sort2_lanes(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send,
                              uint32_t supertiles, int max_grid, int max_width, uint64_t* keys, const EmitOut& eo,
-                             Meta* meta, uint64_t wait_limit, cudaStream_t st) {
+                             Meta* meta, uint64_t wait_limit, const DedupeOut& dd, cudaStream_t st) {
   if (threads == 512 && max_width <= 4)
     return tile_sort2_cls<G, 512>(cluster, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta,
-                                  wait_limit, st);
+                                  wait_limit, dd, st);
   return tile_sort2_cls<G, 256>(cluster, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta,
-                                wait_limit, st);
+                                wait_limit, dd, st);
 }
 
 }  // namespace

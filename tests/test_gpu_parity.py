@@ -31,9 +31,11 @@ def assert_same_dev(dev, exp, label=""):
     assert np.array_equal(dev["stream"].cpu().numpy(), exp["stream"]), label
 
 
-@pytest.fixture(scope="module")
-def ctx(bsort_gpu):
-    c = bsort_gpu.Context()
+@pytest.fixture(scope="module", params=["dedupe=1", "dedupe=0"])
+def ctx(bsort_gpu, request):
+    """A context with the duplicate-aware sort of the large buckets (the
+    default) and one with merge passes instead: every test runs on both."""
+    c = bsort_gpu.Context(tune_table=request.param)
     yield c
     c.close()
 
@@ -433,3 +435,27 @@ def test_batch_4096_full(bsort_gpu, oracle_mod, synth_mod):
     with ThreadPoolExecutor(cores) as ex:
         bad = [i for i in ex.map(check, range(len(docs))) if i is not None]
     assert bad == [], f"documents differing from the oracle: {bad[:20]}"
+
+
+@pytest.mark.parametrize("case", ["one_word", "two_words", "hot_and_cold", "all_distinct_wide"])
+def test_duplicate_aware_extremes(ctx, oracle_mod, case):
+    """Large buckets at the extremes of repetition: one word repeated 3M
+    times (one distinct key whose count spans every tile), two words, a few
+    hot words among many cold ones, and distinct words of 33..64 letters
+    (keys of 8 words, whose distinct-key entries take the 16-word sort)."""
+    rng = np.random.default_rng({"one_word": 1, "two_words": 2, "hot_and_cold": 3, "all_distinct_wide": 4}[case])
+    if case == "one_word":
+        data = b"hello " * 3_000_000
+    elif case == "two_words":
+        words = np.where(rng.random(2_000_000) < 0.3, 1, 0)
+        data = b" ".join([b"Alpha", b"alpha"][i] for i in words)
+    elif case == "hot_and_cold":
+        cold = rng.choice(np.frombuffer(b"abcdefghij", np.uint8), size=(400_000, 6))
+        words = [bytes(r) for r in cold] + [b"zzzzzz"] * 300_000 + [b"aaaaaa"] * 100_000 + [b"mmmmmm"] * 17
+        order = rng.permutation(len(words))
+        data = b"\n".join(words[i] for i in order)
+    else:
+        lens = rng.integers(33, 37, size=60_000)  # four buckets of about 15,000 words
+        words = [bytes(rng.choice(np.frombuffer(b"abcdefghijklmnopqrstuvwxyz", np.uint8), size=L)) for L in lens]
+        data = b" ".join(words + words[:5_000])
+    assert_same(ctx.text(data), oracle_mod.stable(data, nthreads=8), case)

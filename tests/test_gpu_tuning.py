@@ -15,10 +15,12 @@ def assert_same(got, exp, label=""):
     assert np.array_equal(got.offsets, exp["offsets"]), label
     assert np.array_equal(got.stream, exp["stream"]), label
 
-TABLES = ["k4_lanes=2,2,2,2 piped_min=1", "k4_lanes=8,8,8,8 piped_min=1000000", "k4_lanes=2,8,4,2 piped_min=1",
-          "k4_lanes=8,4,2,8 piped_min=4", "k4_runs=1 piped_min=1", "k4_runs=2 k4_streams=0", "k4_runs=4", "k4_runs_small=16",
-          "k4_runs_small=16 k4_streams=0 k4_lanes=8,8,8,8", "k4_threads=512,512,512,512",
-          "k4_threads=512,256,512,256 k4_lanes=8,2,2,4 k4_runs_small=16"]
+TABLES = ["k4_lanes=2,2,2,2 piped_min=1 dedupe=0", "k4_lanes=8,8,8,8 piped_min=1000000 dedupe=0",
+          "k4_lanes=2,8,4,2 piped_min=1 dedupe=0", "k4_lanes=8,4,2,8 piped_min=4 dedupe=0",
+          "k4_runs=1 piped_min=1 dedupe=0", "k4_runs=2 k4_streams=0 dedupe=0", "k4_runs=4 dedupe=0",
+          "k4_runs_small=16 dedupe=0", "k4_runs_small=16 k4_streams=0 k4_lanes=8,8,8,8",
+          "k4_threads=512,512,512,512", "k4_threads=512,256,512,256 k4_lanes=8,2,2,4 k4_runs_small=16",
+          "k4_runs=1 piped_min=1 dedupe=1", "k4_runs=8 k4_runs_small=8 dedupe=1", "k4_streams=0 dedupe=1"]
 
 
 def threshold_doc(W):
@@ -50,7 +52,7 @@ def test_tuning_applies_to_launches(bsort_gpu):
     letters = rng.choice(np.frombuffer(b"abcdefgh", np.uint8), size=(n, 5))
     data = np.concatenate([letters, np.full((n, 1), 32, np.uint8)], axis=1).reshape(-1)
     cuts = {}
-    for table in ("piped_min=1", "piped_min=1000000"):
+    for table in ("piped_min=1 dedupe=0", "piped_min=1000000 dedupe=0"):
         with bsort_gpu.Context(profile=1, tune_table=table) as c:
             c.profile_read()
             r = c.text(data)
@@ -58,4 +60,4 @@ def test_tuning_applies_to_launches(bsort_gpu):
             tl = c.trace_read()
         assert {v[5] for v in tl if v[0] == "tile_sort"} <= {0, 1, 2, 4, 8, 16}
         cuts[table] = sum(1 for v in tl if v[0] == "merge_cut")
-    assert cuts["piped_min=1"] > 0 and cuts["piped_min=1000000"] == 0
+    assert cuts["piped_min=1 dedupe=0"] > 0 and cuts["piped_min=1000000 dedupe=0"] == 0
