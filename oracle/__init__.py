@@ -65,6 +65,10 @@ def bind(path: str):
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         f.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(_Result)]
+    for name in ("oracle_bubble_order", "oracle_stable_order"):
+        f = getattr(lib, name)
+        f.restype = ctypes.c_int
+        f.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Result)]
     lib.oracle_tokenize.restype = ctypes.c_int64
     lib.oracle_tokenize.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_void_p),
                                     ctypes.POINTER(ctypes.c_void_p)]
@@ -90,10 +94,13 @@ def _as_u8(data) -> np.ndarray:
     return a.reshape(-1)
 
 
-def _run(lib, fname: str, data, nthreads: int) -> dict:
+def _run(lib, fname: str, data, nthreads: int, order: int | None = None) -> dict:
     a = _as_u8(data)
     r = _Result()
-    rc = getattr(lib, fname)(a.ctypes.data if a.size else None, a.size, int(nthreads), ctypes.byref(r))
+    f = getattr(lib, fname)
+    ptr = a.ctypes.data if a.size else None
+    rc = (f(ptr, a.size, int(nthreads), ctypes.byref(r)) if order is None
+          else f(ptr, a.size, int(order), int(nthreads), ctypes.byref(r)))
     try:
         if rc != 0:
             raise RuntimeError(f"{fname} failed with code {rc}")
@@ -123,6 +130,23 @@ def bubble(data, nthreads: int = 1, lib=None) -> dict:
 def stable(data, nthreads: int = 1, lib=None) -> dict:
     """O2: std::stable_sort by (length, bytes), grouped per length bucket."""
     return _run(lib or _load(), "oracle_stable", data, nthreads)
+
+
+# Orders (the boundary's bsort_order): 0 ASCII per length bucket (the
+# paper's Section III step 4), 1 folded (alphabetic, case ignored, ties in
+# ASCII order) per length bucket, 2 whole-file ASCII order without length
+# buckets (Table 1, row 2), 3 length buckets in input order (Table 1, row 3).
+ORDER_ASCII, ORDER_FOLDED, ORDER_WHOLE, ORDER_LENGTH = 0, 1, 2, 3
+
+
+def bubble_order(data, order: int, nthreads: int = 1, lib=None) -> dict:
+    """O1 in any order: bubble sort with the order's comparison."""
+    return _run(lib or _load(), "oracle_bubble_order", data, nthreads, order)
+
+
+def stable_order(data, order: int, nthreads: int = 1, lib=None) -> dict:
+    """O2 in any order: std::stable_sort with the order's comparison."""
+    return _run(lib or _load(), "oracle_stable_order", data, nthreads, order)
 
 
 def tokenize(data, lib=None) -> list[bytes]:

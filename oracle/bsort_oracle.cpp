@@ -265,6 +265,131 @@ int64_t oracle_tokenize(const uint8_t* bytes, uint64_t len, uint8_t** letters_ou
   return static_cast<int64_t>(words.size());
 }
 
+// ------------------------------------------------------ other orders ----
+//
+// The same words in the other orders the paper names or leaves open:
+//   order 1, folded: length buckets (Section II phase 2), each in alphabetic
+//            order: letters compared with case ignored, and words whose
+//            letters agree that way in ASCII order (a reading of "alphabetic
+//            order", Section II phase 3, against "ASCII code for each
+//            letter", Section III step 4);
+//   order 2, whole: no length buckets: all words in ASCII order, a word
+//            before every longer word it begins (Table 1, "bubble sort based
+//            on alphabetic order");
+//   order 3, length: length buckets, each in input order (Table 1, "bubble
+//            sort based on the length of the word": bubble sort exchanges
+//            only on a strictly greater length, so equal lengths keep their
+//            order).
+// O1 (oracle_bubble_order) bubble sorts with the order's comparison: each
+// length bucket for orders 1 and 3 (every comparison inside a bucket of
+// order 3 finds equal lengths, so a bucket stays in input order), all words
+// at once for order 2.  O2 (oracle_stable_order) uses std::stable_sort with
+// the same comparisons.
+
+namespace {
+
+unsigned char fold(char c) { return static_cast<unsigned char>((c >= 'A' && c <= 'Z') ? c + 32 : c); }
+
+// order 1 within one length: case-blind letters first, then ASCII
+bool folded_less(const std::string& a, const std::string& b) {
+  for (size_t i = 0; i < a.size() && i < b.size(); ++i)
+    if (fold(a[i]) != fold(b[i])) return fold(a[i]) < fold(b[i]);
+  if (a.size() != b.size()) return a.size() < b.size();
+  return bytes_less(a, b);
+}
+
+// true when a must come after b under `order`
+bool order_greater(int order, const std::string& a, const std::string& b) {
+  switch (order) {
+    case 1: return folded_less(b, a);
+    case 2: return bytes_less(b, a);      // lexicographic by unsigned bytes: a prefix comes first
+    case 3: return a.size() > b.size();
+    default: return bytes_less(b, a);
+  }
+}
+
+// Textbook bubble sort of whole words (Section I), early exit as above.
+void bubble_sort_words(std::vector<std::string>& v, int order) {
+  for (size_t sweep = 1; sweep < v.size(); ++sweep) {
+    bool moved = false;
+    for (size_t j = 0; j + sweep < v.size(); ++j)
+      if (order_greater(order, v[j], v[j + 1])) {
+        std::swap(v[j], v[j + 1]);
+        moved = true;
+      }
+    if (!moved) return;
+  }
+}
+
+// Counts per length as in fill_result; offsets and stream in the order of `words`.
+int fill_flat(const std::vector<std::string>& words, oracle_result* out) {
+  uint32_t max_len = 0;
+  uint64_t bytes = 0;
+  for (const auto& w : words) {
+    max_len = std::max<uint32_t>(max_len, static_cast<uint32_t>(w.size()));
+    bytes += w.size();
+  }
+  out->max_len = max_len;
+  out->n_words = words.size();
+  out->stream_bytes = bytes;
+  out->counts = static_cast<uint64_t*>(std::calloc(max_len + 1, sizeof(uint64_t)));
+  out->offsets = static_cast<uint32_t*>(std::malloc((words.size() + 1) * sizeof(uint32_t)));
+  out->stream = static_cast<uint8_t*>(std::malloc(bytes ? bytes : 1));
+  if (!out->counts || !out->offsets || !out->stream) return -2;
+  uint64_t pos = 0;
+  for (size_t j = 0; j < words.size(); ++j) {
+    ++out->counts[words[j].size()];
+    out->offsets[j] = static_cast<uint32_t>(pos);
+    std::memcpy(out->stream + pos, words[j].data(), words[j].size());
+    pos += words[j].size();
+  }
+  out->offsets[words.size()] = static_cast<uint32_t>(pos);
+  return 0;
+}
+
+}  // namespace
+
+// O1 for every order (0 as oracle_bubble, without its counters): bubble sort
+// per length bucket, OpenMP over the buckets, or (order 2) of all words.
+int oracle_bubble_order(const uint8_t* bytes, uint64_t len, int order, int nthreads, oracle_result* out) {
+  if (!out || (!bytes && len) || order < 0 || order > 3) return -1;
+  std::memset(out, 0, sizeof(*out));
+  std::vector<std::string> words = tokenize_state_machine(bytes, len);
+  if (order == 2) {
+    bubble_sort_words(words, 2);
+    return fill_flat(words, out);
+  }
+  size_t longest = 0;
+  for (const auto& w : words) longest = std::max(longest, w.size());
+  std::vector<std::vector<std::string>> buckets(longest + 1);
+  for (auto& w : words) buckets[w.size()].push_back(std::move(w));
+  const long nb = static_cast<long>(longest);
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(dynamic, 1)
+  for (long L = 1; L <= nb; ++L) bubble_sort_words(buckets[L], order);
+  return fill_result(buckets, out);
+}
+
+// O2 for every order: tokenizer B, then std::stable_sort with the order's
+// comparison (per length bucket, or all words for order 2).
+int oracle_stable_order(const uint8_t* bytes, uint64_t len, int order, int nthreads, oracle_result* out) {
+  if (!out || (!bytes && len) || order < 0 || order > 3) return -1;
+  std::memset(out, 0, sizeof(*out));
+  std::vector<std::string> words = tokenize_split_filter(bytes, len);
+  auto less = [order](const std::string& a, const std::string& b) { return order_greater(order, b, a); };
+  if (order == 2) {
+    std::stable_sort(words.begin(), words.end(), less);
+    return fill_flat(words, out);
+  }
+  size_t longest = 0;
+  for (const auto& w : words) longest = std::max(longest, w.size());
+  std::vector<std::vector<std::string>> buckets(longest + 1);
+  for (auto& w : words) buckets[w.size()].push_back(std::move(w));
+  const long nb = static_cast<long>(longest);
+#pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(dynamic, 1)
+  for (long L = 1; L <= nb; ++L) std::stable_sort(buckets[L].begin(), buckets[L].end(), less);
+  return fill_result(buckets, out);
+}
+
 void oracle_free(oracle_result* r) {
   if (!r) return;
   std::free(r->counts);

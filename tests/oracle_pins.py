@@ -215,7 +215,78 @@ def pin_thread_count_invariance(lib):
     assert oracle.bubble(data, 4, lib=lib)["swaps"] == ref["swaps"]
 
 
+# ---- the other orders (oracle.ORDER_*) ----
+# References written from each order's definition with Python's own sort:
+#   folded: (length, letters with case ignored, bytes);
+#   whole:  the bytes alone (Python compares bytes lexicographically, a
+#           prefix before its extensions);
+#   length: the length alone, Python's sort being stable (input order kept).
+ORDER_KEYS = {
+    oracle.ORDER_ASCII: lambda w: (len(w), w),
+    oracle.ORDER_FOLDED: lambda w: (len(w), w.lower(), w),
+    oracle.ORDER_WHOLE: lambda w: w,
+    oracle.ORDER_LENGTH: len,
+}
+
+
+def pin_orders_hand_example(lib):
+    # Tokens of the example, in input order: Hello world The catsat on a mat
+    # The end apple Apple APPLE aPple.  Worked by hand:
+    #   folded: length 3 by case-blind letters: end < mat < the (The, The);
+    #           length 5: the four spellings of "apple" first, among
+    #           themselves in ASCII order (APPLE < Apple < aPple < apple),
+    #           then Hello, world;
+    #   whole:  upper-case letters before lower-case ones, a prefix first;
+    #   length: each length keeps input order.
+    data = b"Hello, world! The cat-sat\non a mat; The end. apple Apple APPLE aPple"
+    want = {
+        oracle.ORDER_FOLDED: [b"a", b"on", b"end", b"mat", b"The", b"The", b"APPLE", b"Apple", b"aPple", b"apple",
+                              b"Hello", b"world", b"catsat"],
+        oracle.ORDER_WHOLE: [b"APPLE", b"Apple", b"Hello", b"The", b"The", b"a", b"aPple", b"apple", b"catsat", b"end",
+                             b"mat", b"on", b"world"],
+        oracle.ORDER_LENGTH: [b"a", b"on", b"The", b"mat", b"The", b"end", b"Hello", b"world", b"apple", b"Apple",
+                              b"APPLE", b"aPple", b"catsat"],
+    }
+    for order, words in want.items():
+        for res in (oracle.bubble_order(data, order, 1, lib=lib), oracle.stable_order(data, order, 1, lib=lib)):
+            assert _words(res) == words, (order, _words(res))
+            assert res["counts"].tolist() == [0, 1, 1, 4, 0, 6, 1]
+    # a prefix comes before its extensions; case is not folded in the whole order
+    res = oracle.stable_order(b"abc ab b a ba B", oracle.ORDER_WHOLE, 1, lib=lib)
+    assert _words(res) == [b"B", b"a", b"ab", b"abc", b"b", b"ba"]
+
+
+def pin_orders_vs_python(lib):
+    rng = random.Random(11)
+    for trial in range(6):
+        data = _fuzz_doc(rng, 3000 if trial < 3 else 400)
+        toks = python_tokens(data)
+        for order, key in ORDER_KEYS.items():
+            want = sorted(toks, key=key)
+            got = _words(oracle.stable_order(data, order, 2, lib=lib))
+            assert got == want, (order, trial)
+            if trial >= 3:  # bubble sort of the whole text is quadratic: small documents only
+                assert _words(oracle.bubble_order(data, order, 2, lib=lib)) == want, (order, trial)
+        assert _words(oracle.stable_order(data, oracle.ORDER_ASCII, 1, lib=lib)) == _words(oracle.stable(data, 1, lib=lib))
+
+
+def pin_orders_brute_force(lib):
+    # Every order of a small multiset with case variants: the sorted orders
+    # give one result whatever the input order; the length order gives the
+    # input order within each length.
+    base = [b"ab", b"Ab", b"aB", b"a", b"B", b"ba", b"abc"]
+    for perm in itertools.permutations(base):
+        data = b" ".join(perm)
+        for order, key in ORDER_KEYS.items():
+            got = _words(oracle.bubble_order(data, order, 1, lib=lib))
+            assert got == sorted(perm, key=key), (order, perm)
+            assert got == _words(oracle.stable_order(data, order, 1, lib=lib))
+
+
 ALL_PINS = [
+    pin_orders_hand_example,
+    pin_orders_vs_python,
+    pin_orders_brute_force,
     pin_hand_example,
     pin_special_cases,
     pin_brute_force_permutations,

@@ -42,6 +42,13 @@ MUTANTS = {
     "split_filter_keeps_punct": ("if (is_letter(b[k])) w.push_back", "if (b[k] != ',') w.push_back"),
     "case_folded": ("      cur.push_back(static_cast<char>(c));",
                     "      cur.push_back(static_cast<char>(c | 0x20));"),
+    "folded_ties_reversed": ("  return bytes_less(a, b);\n}", "  return bytes_less(b, a);\n}"),
+    "folded_letters_reversed": ("return fold(a[i]) < fold(b[i]);", "return fold(a[i]) > fold(b[i]);"),
+    "folded_ignores_case_ties": ("  if (a.size() != b.size()) return a.size() < b.size();\n  return bytes_less(a, b);",
+                                 "  return a.size() < b.size();"),
+    "whole_by_length_first": ("    case 2: return bytes_less(b, a);",
+                              "    case 2: return a.size() != b.size() ? a.size() > b.size() : bytes_less(b, a);"),
+    "length_order_unstable": ("    case 3: return a.size() > b.size();", "    case 3: return a.size() >= b.size();"),
     "max_len_off_by_one": ("if (!buckets[L].empty()) max_len = static_cast<uint32_t>(L);",
                            "if (!buckets[L].empty()) max_len = static_cast<uint32_t>(L) + 1;"),
 }
