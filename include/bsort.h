@@ -88,14 +88,17 @@ typedef struct {
                                                 into runs of k4_runs_small tiles
                               k4_runs_small=8|16  that run for the smaller merges (16: clusters
                                                 of 16 CTAs, beyond the portable cluster size)
-                              dedupe=0|1        1: the duplicate-aware sort for the
-                                                buckets too large for one cluster of 8 tiles
-                                                (keys of up to 8 words): the tile sort hands
+                              dedupe=0|1|2      the duplicate-aware sort for the buckets too
+                                                large for one cluster of 8 tiles (keys of up
+                                                to 8 words): 1 (default) on inputs whose
+                                                merges would be pipelined (see piped_min;
+                                                smaller ones gain nothing), 2 always, 0
+                                                never (merge passes).  The tile sort hands
                                                 each sorted run's distinct words, with their
                                                 counts, to a hash table per bucket; the
                                                 distinct words are sorted and written out
-                                                count times each.  0 (default): merge
-                                                passes.  The result is the same either way.
+                                                count times each.  The result is the same
+                                                either way.
                               k4_streams=0|1    1 (default): the tile sort that makes the
                                                 merge passes' runs runs first on the call's
                                                 stream, the others beside it on side
@@ -103,13 +106,40 @@ typedef struct {
                                                 stream (how the autotuner times a class)
                             Copied at bsort_create; an unknown key or a bad value makes
                             bsort_create fail with BSORT_E_INVAL. */
+  uint32_t order;        /* bsort_order: the order of the result (default BSORT_ORDER_ASCII) */
+  uint32_t key_pack;     /* bsort_key_pack: how the sort kernels encode a word's letters; it
+                            changes the speed, not the result (default BSORT_KEYS_BYTES) */
 } bsort_config;
+
+/* Orders of the result.  Each one's oracle and reading of the paper: */
+typedef enum {
+  BSORT_ORDER_ASCII = 0,  /* length buckets, shorter first, each sorted by the ASCII codes of its
+                             letters (Section III step 4): the paper's method */
+  BSORT_ORDER_FOLDED = 1, /* length buckets, each in alphabetic order: letters compared with case
+                             ignored, words whose letters then agree in ASCII order (a reading of
+                             Section II phase 3, "alphabetic order") */
+  BSORT_ORDER_WHOLE = 2,  /* no length buckets: every word in ASCII order, a word before each
+                             longer word it begins (Table 1, bubble sort of the file "based on
+                             alphabetic order") */
+  BSORT_ORDER_LENGTH = 3  /* length buckets, each in input order: a stable sort by length alone
+                             (Table 1, bubble sort "based on the length of the word") */
+} bsort_order;
+
+/* Key encodings of the sort kernels (an option of the GPU path; the paper
+ * sorts characters): */
+typedef enum {
+  BSORT_KEYS_BYTES = 0,   /* one byte a letter, 8 letters a 64-bit key word */
+  BSORT_KEYS_LETTERS6 = 1 /* six bits a letter (A..Z, a..z in ASCII order), 10 letters a key word:
+                             fewer key bytes to move for words of 9, 10, 17..21, 33..42 letters */
+} bsort_key_pack;
 
 /*
  * One document's result.
  *   counts[L], 0 <= L <= max_len: number of words of L letters; counts[0] == 0.
  *   stream: the sorted words back to back, no separators: bucket 1 first,
- *           each bucket in ascending unsigned byte order.
+ *           each bucket in ascending unsigned byte order (in the context's
+ *           bsort_order: the words of every order but BSORT_ORDER_WHOLE still
+ *           come in length buckets, shorter first).
  *   offsets[j], 0 <= j <= n_words: word j is stream[offsets[j] .. offsets[j+1]);
  *           offsets[0] == 0 and offsets[n_words] == stream_bytes.  NULL when the
  *           context was created with want_offsets == 0.
@@ -127,7 +157,7 @@ typedef struct {
 } bsort_result;
 
 /* Default configuration: l_cap 255, offsets on, current device, default wait limit,
- * built-in tuning. */
+ * built-in tuning, ASCII order, byte keys. */
 void bsort_config_default(bsort_config* cfg);
 
 /*

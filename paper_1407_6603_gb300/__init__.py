@@ -35,7 +35,13 @@ STATUS_NAMES = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_TOO_LARG
 
 class bsort_config(ctypes.Structure):
     _fields_ = [("l_cap", ctypes.c_uint32), ("want_offsets", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("wait_limit", ctypes.c_uint64), ("tune_table", ctypes.c_char_p)]
+                ("profile", ctypes.c_int32), ("wait_limit", ctypes.c_uint64), ("tune_table", ctypes.c_char_p),
+                ("order", ctypes.c_uint32), ("key_pack", ctypes.c_uint32)]
+
+
+# bsort_order and bsort_key_pack
+ORDER_ASCII, ORDER_FOLDED, ORDER_WHOLE, ORDER_LENGTH = 0, 1, 2, 3
+KEYS_BYTES, KEYS_LETTERS6 = 0, 1
 
 
 class bsort_kernel_stat(ctypes.Structure):
@@ -404,10 +410,15 @@ class Context:
     """Owns a bsort context (CUDA stream, device arena, pinned host buffers)."""
 
     def __init__(self, l_cap: int = 255, want_offsets: bool = True, device: int = -1, wait_limit: int = 0,
-                 profile: bool = False, tune_table: str | None = None):
+                 profile: bool = False, tune_table: str | None = None, order: int = ORDER_ASCII,
+                 key_pack: int = KEYS_BYTES):
         """tune_table: None for the built-in tuning, else the text of a tune
-        table (see bsort_config.tune_table; autotune.py writes one)."""
+        table (see bsort_config.tune_table; autotune.py writes one).  order:
+        the result's order (ORDER_*); key_pack: the sort keys' encoding
+        (KEYS_*, the same result)."""
         cfg = bsort_config_default()
+        cfg.order = order
+        cfg.key_pack = key_pack
         cfg.l_cap = l_cap
         cfg.want_offsets = 1 if want_offsets else 0
         cfg.device = device

@@ -57,7 +57,8 @@ struct Tune {
   int k4_streams = 1;  // 1: the tile sorts of the smaller classes run on side streams
   int k4_runs = 2;     // cluster size (runs of that many tiles) for buckets that need pipelined merge passes
   int k4_runs_small = 16;  // the same when their merges are too small to pipeline
-  int dedupe = 0;          // 1: the duplicate-aware sort for the buckets that need merge passes
+  int dedupe = 1;          // the duplicate-aware sort for the buckets that need merge passes:
+                           // 0 never, 1 on large inputs, 2 always
 };
 
 // Parses a tune table; false on an unknown key or a bad value.
@@ -114,7 +115,7 @@ bool parse_tune(const char* text, Tune& t) {
         t.k4_threads[q] = (int)nums[q];
       }
     } else if (key == "dedupe") {
-      if (nums.size() != 1 || nums[0] > 1) return false;
+      if (nums.size() != 1 || nums[0] > 2) return false;
       t.dedupe = (int)nums[0];
     } else if (key == "piped_min") {
       if (nums.size() != 1 || nums[0] < 1 || nums[0] > 1000000) return false;
@@ -175,6 +176,7 @@ struct bsort_ctx {
   bool busy = false;
   Tune tune;
   std::string tune_text;  // the caller's tune table, copied
+  uint32_t codec = kCodeBytes;  // key encoding (from order and key_pack)
 
   DevBuf sticky;  // a Meta kept across calls: err_timeout of bounded device waits
   HostBuf h_sticky;
@@ -183,7 +185,7 @@ struct bsort_ctx {
   // the duplicate-aware sort: hash tables (stamped with the call's generation
   // `gen`, so never cleared between calls), the distinct-key arrays and their
   // ping-pong partner, the second layout, merge scratch and count prefixes
-  DevBuf htab, uA, uB, plan2, samples2, jobs2, pre;
+  DevBuf htab, uA, uB, plan2, samples2, jobs2, pre, ssum, tfirst;
   HostBuf h_plan2, h_ucnt;
   uint32_t gen = 0;
   cudaEvent_t dedupe_ev = nullptr;  // the distinct-key counts reached the host
@@ -438,7 +440,7 @@ constexpr int kGroups = 12;
 
 uint8_t group_of(Segment& sg, uint64_t& big_tiles) {
   const uint32_t n = sg.n;
-  const int W = width_of_len(sg.L);
+  const int W = (int)sg.W;
   const uint32_t T = W >= 16 ? 0u : tile2_keys(W);
   sg.run0 = n;
   sg.passes = 0;
@@ -527,10 +529,10 @@ void plan_sorts(const bsort_ctx* c, const std::vector<Segment>& cand, const std:
       Segment sg = cand[i];
       if (group[i] < 4) {
         if (sg.flags & kSegDedupe) {
-          sg.run0 = (uint32_t)p.runs * tile2_keys(width_of_len(sg.L));
+          sg.run0 = (uint32_t)p.runs * tile2_keys((int)sg.W);
           sg.passes = 0;
         } else {
-          sg.run0 = (uint32_t)p.runs * tile2_keys(width_of_len(sg.L));
+          sg.run0 = (uint32_t)p.runs * tile2_keys((int)sg.W);
           sg.passes = merge_passes(sg.n, sg.run0);
         }
         sg.final_buf = sg.passes & 1u;
@@ -550,11 +552,11 @@ void plan_sorts(const bsort_ctx* c, const std::vector<Segment>& cand, const std:
     }
   }
   auto out_bytes = [&](const Segment& sg) {  // a bucket's output: its letters and offsets
-    return (sg.flags & kSegKeysOut) ? 8.0 * width_of_len(sg.L) * sg.n : (double)sg.n * (sg.L + off_bytes);
+    return (sg.flags & kSegKeysOut) ? 8.0 * sg.W * sg.n : (double)sg.n * (sg.L + off_bytes);
   };
   for (uint32_t i = 0; i < p.nseg; ++i) {
     Segment& sg = out[i];
-    const int W = width_of_len(sg.L);
+    const int W = (int)sg.W;
     int q = 0;
     while (i >= p.pbeg[q + 1]) ++q;
     const int gi = p.order[q];
@@ -788,6 +790,7 @@ bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* i
     u.L = 8 * d.Wp;  // keys of Wp words: the key, its count, zeros
     u.doc = di;
     u.key_off = d.uniq_off;
+    u.W = d.Wp;
     u.flags = kSegKeysOut;
     const uint8_t gi = group_of(u, big_tiles);
     cand.push_back(u);
@@ -807,7 +810,7 @@ bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* i
   // expansion descriptors, in the order of the buckets
   std::vector<uint32_t> where(ndd, kNoSegment);
   for (uint32_t i = 0; i < nseg; ++i) where[segs2[i].doc] = i;
-  uint32_t ne = 0, max_tiles = 0;
+  uint32_t ne = 0, max_tiles = 0, tiles = 0, max_U = 0;
   uint64_t pre_words = 0;
   double moved = 0;
   for (uint32_t di = 0; di < ndd; ++di) {
@@ -824,7 +827,11 @@ bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* i
     e.L = b.L;
     e.Wp = ins[di].Wp;
     e.final_buf = u.final_buf;
-    max_tiles = std::max(max_tiles, (b.n + expand_tile(e.Wp / 2) - 1) / expand_tile(e.Wp / 2));
+    const uint32_t bt = (b.n + expand_tile(e.Wp / 2) - 1) / expand_tile(e.Wp / 2);
+    e.tile0 = tiles;
+    tiles += bt;
+    max_tiles = std::max(max_tiles, bt);
+    max_U = std::max(max_U, u.n);
     e.stream_off = b.stream_off;
     e.out_word = b.out_word;
     e.doc_stream0 = b.doc_stream0;
@@ -834,6 +841,8 @@ bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* i
   GROW(c->plan2, plan_bytes, "distinct-key layout");
   GROW(c->samples2, 8 * std::max<uint64_t>(p2.smp_words, 16), "merge samples");
   GROW(c->pre, 4 * std::max<uint64_t>(pre_words, 16), "count prefixes");
+  GROW(c->ssum, 4 * std::max<uint64_t>((uint64_t)ne * expand_slices(max_U), 16), "count prefixes");
+  GROW(c->tfirst, 4 * std::max<uint64_t>(tiles, 16), "tile starts");
   CK(cudaMemcpyAsync(c->plan2.p, c->h_plan2.p, plan_bytes, cudaMemcpyHostToDevice, st), "copy distinct-key layout");
   if (gap_a) {
     cudaEvent_t gap_b = next_event(c);
@@ -850,10 +859,12 @@ bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* i
   bsort_status s = launch_sorts(c, p2, segs2, segs2_dev, dptr<uint64_t>(c->uA), dptr<uint64_t>(c->uB),
                                 dptr<uint64_t>(c->samples2), c->jobs2, barrier2, eo, no_dd, st, false, none, {});
   if (s != BSORT_OK) return s;
-  const ExpandCaps caps{std::min(c->uA.cap, c->uB.cap) / 8, c->pre.cap / 4, c->stream.cap, c->offsets.cap / 4};
+  const ExpandCaps caps{std::min(c->uA.cap, c->uB.cap) / 8, c->pre.cap / 4, c->stream.cap, c->offsets.cap / 4,
+                        c->tfirst.cap / 4};
   LAUNCH(kExpand, moved,
-         launch_expand(dptr<ExpandDesc>(c->plan2, seg_bytes + barrier_bytes), ne, max_tiles, dptr<uint64_t>(c->uA),
-                       dptr<uint64_t>(c->uB), dptr<uint32_t>(c->pre), eo, dptr<Meta>(c->sticky), caps, st),
+         launch_expand(dptr<ExpandDesc>(c->plan2, seg_bytes + barrier_bytes), ne, max_U, max_tiles,
+                       dptr<uint64_t>(c->uA), dptr<uint64_t>(c->uB), dptr<uint32_t>(c->pre), dptr<uint32_t>(c->ssum),
+                       dptr<uint32_t>(c->tfirst), eo, dptr<Meta>(c->sticky), caps, st),
          "expand");
   return BSORT_OK;
 }
@@ -993,6 +1004,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
         sg.out_word = word_before;
         sg.stream_off = byte_before;
         sg.doc_stream0 = h_lbase[d];
+        sg.W = (uint32_t)key_width(c->codec, L);
         const uint8_t gi = group_of(sg, big_tiles);
         cand.push_back(sg);
         group.push_back(gi);
@@ -1004,10 +1016,13 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   const uint32_t nseg = (uint32_t)cand.size();
   // The duplicate-aware sort takes the buckets that would need merge passes
   // (keys of at most 8 words): K4 hands their sorted runs' distinct keys to a
-  // hash table per bucket instead of writing the runs back.
+  // hash table per bucket instead of writing the runs back.  It pays on large
+  // inputs, whose merges would be pipelined (the same threshold); on smaller
+  // ones its second round trip and launches cost more than the merges save.
   std::vector<uint32_t>& dd_seg = c->dd_seg;  // candidate index of each such bucket
   dd_seg.clear();
-  if (c->tune.dedupe)
+  const uint64_t piped_tiles = (uint64_t)c->tune.piped_min * c->sm_count * merge_piped_ctas_per_sm();
+  if (c->tune.dedupe == 2 || (c->tune.dedupe == 1 && big_tiles >= piped_tiles))
     for (uint32_t i = 0; i < nseg; ++i)
       if (group[i] < 4) {
         cand[i].flags = kSegDedupe | ((uint32_t)dd_seg.size() << 8);
@@ -1041,7 +1056,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     lookup[(size_t)sg.doc * kHist + sg.L] = i;
     if (sg.flags & kSegDedupe) {
       const uint32_t di = seg_dedupe_index(sg);
-      const uint32_t W = (uint32_t)width_of_len(sg.L);
+      const uint32_t W = sg.W;
       DedupeIns& d = ins[di];
       d = DedupeIns{};
       d.hbits = (uint32_t)ceil_log2(2ull * sg.n);
@@ -1098,7 +1113,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   uint64_t key_bytes_all = 0;
   for (int g = 0; g < kGroups; ++g) key_bytes_all += p1.kb[g];
   const uint32_t grid_cap = (uint32_t)c->sm_count * 16;
-  const EmitOut eo{dptr<uint8_t>(c->stream), dptr<uint32_t>(c->offsets), c->cfg.want_offsets};
+  const EmitOut eo{dptr<uint8_t>(c->stream), dptr<uint32_t>(c->offsets), c->cfg.want_offsets, c->codec};
   {
     // K3 also writes each document's counts and closing offset, so it runs
     // even when no document has a word
@@ -1205,6 +1220,8 @@ void bsort_config_default(bsort_config* cfg) {
   cfg->profile = 0;
   cfg->wait_limit = 0;
   cfg->tune_table = nullptr;
+  cfg->order = BSORT_ORDER_ASCII;
+  cfg->key_pack = BSORT_KEYS_BYTES;
 }
 
 bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
@@ -1218,6 +1235,7 @@ bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
   if (conf.wait_limit == 0) conf.wait_limit = kDefaultWaitLimit;
   conf.want_offsets = conf.want_offsets ? 1 : 0;
   conf.profile = conf.profile ? 1 : 0;
+  if (conf.order > BSORT_ORDER_FOLDED || conf.key_pack > BSORT_KEYS_LETTERS6) return BSORT_E_INVAL;
   Tune tune;
   if (!parse_tune(conf.tune_table, tune)) return BSORT_E_INVAL;
   int dev = conf.device;
@@ -1233,6 +1251,7 @@ bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
   if (!c) return BSORT_E_NOMEM;
   c->cfg = conf;
   c->device = dev;
+  c->codec = conf.order == BSORT_ORDER_FOLDED ? kCodeFold : conf.key_pack == BSORT_KEYS_LETTERS6 ? kCodeSix : kCodeBytes;
   c->tune = tune;
   if (conf.tune_table) c->tune_text = conf.tune_table;
   c->cfg.tune_table = conf.tune_table ? c->tune_text.c_str() : nullptr;
@@ -1271,7 +1290,7 @@ void bsort_destroy(bsort_ctx* c) {
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
   for (DevBuf* b : {&c->sticky, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB,
                     &c->counts, &c->offsets, &c->stream, &c->jobs, &c->samples, &c->htab, &c->uA, &c->uB, &c->plan2,
-                    &c->samples2, &c->jobs2, &c->pre})
+                    &c->samples2, &c->jobs2, &c->pre, &c->ssum, &c->tfirst})
     if (b->p) cudaFree(b->p);
   for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets,
                      &c->h_stream, &c->h_flag, &c->h_plan2, &c->h_ucnt})

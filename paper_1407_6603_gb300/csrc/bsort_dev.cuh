@@ -45,6 +45,30 @@ __host__ __device__ inline int width_of_len(uint32_t L) {
   return 1 << (32 - __builtin_clz(k - 1));
 #endif
 }
+// Key encodings.  A key is a bit string from the most significant bit of its
+// first u64 word, zero past its last letter, so that unsigned order of the W
+// words is the order wanted:
+//   kCodeBytes  8 bits a letter, its ASCII byte (ASCII order);
+//   kCodeSix    6 bits a letter, A..Z -> 1..26 and a..z -> 27..52 (the same
+//               order, 10 letters a word instead of 8);
+//   kCodeFold   5 bits a letter, its letter case-blind (a/A -> 1 .. z/Z -> 26),
+//               then one bit a letter, 0 for upper case (alphabetic order,
+//               ties in ASCII order).
+// No letter codes to 0, so a word sorts before every longer word it begins
+// when keys are padded with zeros to a common width.
+constexpr uint32_t kCodeBytes = 0, kCodeSix = 1, kCodeFold = 2;
+__host__ __device__ inline uint32_t bits_per_letter(uint32_t codec) { return codec == kCodeBytes ? 8u : 6u; }
+// Key width in u64 words of L letters: the next power of two that holds them.
+__host__ __device__ inline int key_width(uint32_t codec, uint32_t L) {
+  const uint32_t k = (L * bits_per_letter(codec) + 63) / 64;
+  if (k <= 1) return 1;
+#ifdef __CUDA_ARCH__
+  return 1 << (32 - __clz(k - 1));
+#else
+  return 1 << (32 - __builtin_clz(k - 1));
+#endif
+}
+
 __host__ __device__ inline int class_of_width(int W) {
   return W == 1 ? 0 : W == 2 ? 1 : W == 4 ? 2 : W == 8 ? 3 : W == 16 ? 4 : 5;
 }
@@ -119,7 +143,10 @@ struct Segment {
   uint32_t run0;        // length of the sorted runs K4 leaves
   uint32_t smp_off;     // pipelined merges: first u64 word of the bucket's merge samples
   uint32_t flags;       // kSegKeysOut, kSegDedupe; bits 8..31: the bucket's dedupe index
+  uint32_t W;           // key width in u64 words
+  uint32_t pad2[3];
 };
+static_assert(sizeof(Segment) == 80, "a segment is five 16-byte words");
 // Segment flags.  kSegKeysOut: the sorted keys stay in the key buffer (final_buf)
 // instead of being emitted as words (the distinct-word arrays of the
 // duplicate-aware sort).  kSegDedupe: K4 sorts the bucket's runs and hands each
@@ -148,7 +175,9 @@ struct ExpandDesc {
   uint32_t L;
   uint32_t Wp;
   uint32_t final_buf;
+  uint32_t tile0;     // first output tile, numbered over the expanded buckets
   uint32_t stream_off, out_word, doc_stream0;
+  uint32_t pad;
 };
 constexpr uint32_t kExpandTileWords = 2048;
 // words per output tile of the expansion for keys of W u64 words
@@ -201,11 +230,13 @@ __host__ __device__ inline uint32_t warp_keys(int W) { return (uint32_t)(32 * (W
 // costs no global loads.
 constexpr uint32_t kSegCache = 256;
 
-// Where sorted words go: the output stream and per-word offsets.
+// Where sorted words go: the output stream and per-word offsets, and how
+// the keys are encoded.
 struct EmitOut {
   uint8_t* stream;
   uint32_t* offsets;
   int want_offsets;
+  uint32_t codec;
 };
 
 #if defined(__CUDACC__)
@@ -217,18 +248,51 @@ struct EmitOut {
 __host__ __device__ __forceinline__ uint64_t recip_of(uint32_t L) { return ((1ull << 32) + L - 1) / L; }
 __host__ __device__ __forceinline__ uint32_t quot(uint32_t n, uint64_t m) { return (uint32_t)(((uint64_t)n * m) >> 32); }
 
+// n bits (n <= 32) at bit offset off of a key whose u64 words kw(q) gives.
+template <class KW>
+__device__ __forceinline__ uint32_t key_bits(KW kw, uint32_t off, uint32_t n) {
+  const uint32_t w = off >> 6, sh = off & 63;
+  uint64_t v = kw(w) << sh;
+  if (sh + n > 64) v |= kw(w + 1) >> (64 - sh);
+  return (uint32_t)(v >> (64 - n));
+}
+// Letters 8q .. 8q + 7 of a key of L letters as big-endian ASCII bytes (zero
+// past L), whatever the encoding; kw(q') gives the key's u64 word q'.
+template <class KW>
+__device__ __forceinline__ uint64_t ascii8(uint32_t codec, uint32_t L, KW kw, uint32_t q) {
+  if (codec == kCodeBytes) return kw(q);
+  uint64_t r = 0;
+  const uint32_t i0 = 8 * q, i1 = min(L, i0 + 8);
+  for (uint32_t i = i0; i < i1; ++i) {
+    uint32_t ch;
+    if (codec == kCodeSix) {
+      const uint32_t c = key_bits(kw, 6 * i, 6);
+      ch = c <= 26 ? 'A' - 1 + c : 'a' - 27 + c;
+    } else {
+      const uint32_t c = key_bits(kw, 5 * i, 5);
+      ch = (key_bits(kw, 5 * L + i, 1) ? 'a' - 1 : 'A' - 1) + c;
+    }
+    r |= (uint64_t)ch << (56 - 8 * (i - i0));
+  }
+  return r;
+}
+
 // Emits cnt sorted keys of L letters as the letters of the words (phase 3's
 // output, Section II: each length's sorted words, shorter lengths first) at p0
 // and, when offs is set, word j's offset within its document, rel0 + j L, at
-// offs[j].  key_word(j, q) gives u64 word q of key j: big-endian letters, zero
-// past the word's L letters.  The run's bytes are one contiguous range of the
+// offs[j].  key_word(j, q) gives u64 word q of key j, encoded with codec
+// (for kCodeBytes: big-endian letters, zero past the word's L letters).  The run's bytes are one contiguous range of the
 // stream (at most 2^24 bytes): the NTH threads write its 16-byte aligned
 // middle with whole 16-byte stores, each gathering its 16 bytes piece by piece
 // (one piece = the rest of one key word, at most 8 bytes), and its ragged ends
 // byte by byte, so no byte outside the range is touched and runs never overlap.
 template <int NTH, class F>
 __device__ __forceinline__ void emit_run(uint32_t L, uint8_t* p0, uint32_t* offs, uint32_t rel0, uint32_t cnt,
-                                         F key_word) {
+                                         F key_word_raw, uint32_t codec) {
+  // the key words as ASCII letters, 8 to a word (the keys' own words for kCodeBytes)
+  auto key_word = [&](uint32_t j, uint32_t q) -> uint64_t {
+    return ascii8(codec, L, [&](uint32_t w) { return key_word_raw(j, w); }, q);
+  };
   const uint64_t m = recip_of(L);
   const int t = threadIdx.x;
   const uint32_t nbytes = cnt * L;
@@ -277,7 +341,7 @@ __device__ __forceinline__ void emit_tile(const Segment& sg, uint32_t k0, uint32
                                           const EmitOut& eo) {
   emit_run<NTH>(sg.L, eo.stream + sg.stream_off + (size_t)k0 * sg.L,
                 eo.want_offsets ? eo.offsets + sg.out_word + k0 : nullptr, sg.stream_off - sg.doc_stream0 + k0 * sg.L,
-                cnt, key_word);
+                cnt, key_word, eo.codec);
 }
 
 // The last index d in [0, n) with key(d) <= x, for keys ascending in d and
@@ -431,17 +495,22 @@ int merge_piped_ctas_per_sm();
 cudaError_t launch_emit(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles, uint32_t grid,
                         const uint64_t* keysA, const uint64_t* keysB, EmitOut eo, cudaStream_t st);
 // The expansion of the duplicate-aware sort: per bucket the exclusive prefix
-// of the sorted distinct keys' counts (one CTA per bucket), then the words,
-// in output tiles of kExpandTileWords / W (max_tiles: the most tiles of one
-// bucket).  The counts must add up to each bucket's word count; a check marks
-// the call failed otherwise.
+// of the sorted distinct keys' counts (max_U: the most distinct keys of one
+// bucket), then the words, in output tiles of kExpandTileWords / W
+// (max_tiles: the most tiles of one bucket; ExpandDesc::tile0 numbers them
+// across buckets).  The counts must add up to each bucket's word count; a
+// check marks the call failed otherwise.
 // Sizes of the buffers the expansion touches (u64 words of each distinct-key
-// buffer, u32 entries of the prefixes, stream bytes, offsets): every
-// descriptor is checked against them.
+// buffer, u32 entries of the prefixes, stream bytes, offsets, tiles of the
+// tile-start table): every descriptor is checked against them.
 struct ExpandCaps {
-  uint64_t u_words, pre, stream, offsets;
+  uint64_t u_words, pre, stream, offsets, tiles;
 };
-cudaError_t launch_expand(const ExpandDesc* ed, uint32_t nbuckets, uint32_t max_tiles, const uint64_t* uA,
-                          const uint64_t* uB, uint32_t* pre, EmitOut eo, Meta* meta, ExpandCaps caps, cudaStream_t st);
+cudaError_t launch_expand(const ExpandDesc* ed, uint32_t nbuckets, uint32_t max_U, uint32_t max_tiles,
+                          const uint64_t* uA, const uint64_t* uB, uint32_t* pre, uint32_t* ssum, uint32_t* tfirst,
+                          EmitOut eo, Meta* meta, ExpandCaps caps, cudaStream_t st);
+// Entries of the slice sums launch_expand needs per bucket (buffer ssum holds
+// nbuckets x expand_slices(max_U)); tfirst holds one entry per output tile.
+size_t expand_slices(uint32_t max_U);
 
 }  // namespace bsort

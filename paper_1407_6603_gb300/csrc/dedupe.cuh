@@ -79,8 +79,7 @@ __device__ void hash_add(const Key<W>& k, uint64_t count, const DedupeIns& d, ui
       for (int q = 0; q < W; ++q) e[q] = k.w[q];
       e[W] = count;
       for (uint32_t q = W + 1; q < d.Wp; ++q) e[q] = 0ull;
-      __threadfence();
-      st_release_u64(slot, gen | u);
+      st_release_u64(slot, gen | u);  // (a release: the key and entry writes above are seen first)
       return;
     }
     if ((uint32_t)hdr == kSlotBusy) {  // another thread is writing this slot's key
@@ -108,28 +107,35 @@ __device__ void hash_add(const Key<W>& k, uint64_t count, const DedupeIns& d, ui
   atomicAdd(&meta->err_timeout, 1u);  // a full table (its capacity of 2n keys makes this unreachable)
 }
 
-// The epilogue: key_at(i) is the tile's i-th sorted key, i < cnt.  Thread t
-// looks at positions t, t + NTH, ...; a position that starts a group of
-// equal keys finds the group's end by binary search and adds the group.
+// The epilogue: key_at(i) is the tile's i-th sorted key, i < cnt <= NTH * 8.
+// The positions that start a group of equal keys are marked in a bit mask
+// (one ballot per warp and round); a group's size is the distance to the next
+// marked position.  Thread t adds the groups that start at its positions t,
+// t + NTH, ... to the bucket's table.
 template <int W, int NTH, class F>
-__device__ void rle_insert(F key_at, uint32_t cnt, const Segment& sg, const DedupeOut& o, Meta* meta,
-                           uint64_t wait_limit) {
+__device__ void rle_insert(F key_at, uint32_t cnt, const Segment& sg, const DedupeOut& o, uint32_t* s_heads,
+                           Meta* meta, uint64_t wait_limit) {
   const uint32_t di = seg_dedupe_index(sg);
   const DedupeIns d = o.ins[di];
-  for (uint32_t i = threadIdx.x; i < cnt; i += NTH) {
-    const Key<W> k = key_at(i);
-    if (i > 0 && !klt(key_at(i - 1), k)) continue;  // inside a group
-    // the group ends at the first position in (i, cnt) whose key is greater
-    uint32_t lo = i + 1, hi = cnt;
-    while (lo < hi) {
-      const uint32_t m = (lo + hi) >> 1;
-      if (klt(k, key_at(m)))
-        hi = m;
-      else
-        lo = m + 1;
-    }
-    hash_add<W>(k, lo - i, d, di, o, meta, wait_limit);
+  const uint32_t words = (cnt + 31) / 32;
+  for (uint32_t i0 = 0; i0 < cnt; i0 += NTH) {  // every warp marks 32 consecutive positions per round
+    const uint32_t i = i0 + threadIdx.x;
+    const bool head = i < cnt && (i == 0 || klt(key_at(i - 1), key_at(i)));
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, head);
+    if ((threadIdx.x & 31) == 0 && i < cnt) s_heads[i >> 5] = m;
   }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < cnt; i += NTH) {
+    const uint32_t wi = i >> 5, b = i & 31;
+    if (!((s_heads[wi] >> b) & 1u)) continue;
+    // the next head after i, or cnt
+    uint32_t rest = b == 31 ? 0u : s_heads[wi] >> (b + 1) << (b + 1);
+    uint32_t wj = wi;
+    while (!rest && ++wj < words) rest = s_heads[wj];
+    const uint32_t end = rest ? min(cnt, wj * 32 + (uint32_t)(__ffs(rest) - 1)) : cnt;
+    hash_add<W>(key_at(i), end - i, d, di, o, meta, wait_limit);
+  }
+  __syncthreads();
 }
 
 }  // namespace

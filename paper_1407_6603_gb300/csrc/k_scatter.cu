@@ -27,7 +27,7 @@ constexpr int kWordsPerThread = kWordBlock / kWordThreads;
 // CTA holds about 45 KB of shared memory, so five fit on an SM.
 constexpr uint32_t kLetterStage = 28672;
 
-// Packs one word into its key.  Key word q of a word that starts at S offset
+// Packs one word into its byte key (kCodeBytes).  Key word q of a word that starts at S offset
 // s0 holds its letters 8q..8q+7, first letter in the most significant byte.
 // With the letters read as aligned 32-bit words u[] (u[0] at S offset
 // `base`), bytes p..p+3 (p = s0 + 8q) lie in u[k], u[k+1] for
@@ -66,11 +66,64 @@ __device__ __forceinline__ void pack_word(const uint32_t* __restrict__ u, uint32
   }
 }
 
+// Packs one word into its key with a letter code (kCodeSix, kCodeFold; see
+// bsort_dev.cuh): the codes from the key's most significant bit down, then
+// zeros to W words.  Letter i is the byte at S offset s0 + i of the letters
+// read as 32-bit words u[] (u[0] at S offset `base`, a multiple of 4).
+__device__ __forceinline__ void pack_codes(uint32_t codec, const uint32_t* __restrict__ u, uint32_t base, uint32_t s0,
+                                           uint32_t L, uint32_t W, uint64_t* __restrict__ out) {
+  uint64_t acc = 0;  // bits not yet written, from the top
+  uint32_t nacc = 0, q = 0;
+  auto put = [&](uint32_t v, uint32_t nb) {  // appends the nb low bits of v
+    if (nacc + nb <= 64) {
+      acc |= (uint64_t)v << (64 - nacc - nb);
+      nacc += nb;
+      if (nacc == 64) {
+        out[q++] = acc;
+        acc = 0;
+        nacc = 0;
+      }
+    } else {
+      const uint32_t first = 64 - nacc;
+      out[q++] = acc | ((uint64_t)v >> (nb - first));
+      nacc = nb - first;
+      acc = (uint64_t)v << (64 - nacc);
+    }
+  };
+  auto letter = [&](uint32_t i) {
+    const uint32_t x = s0 + i - base;
+    return (u[x >> 2] >> (8 * (x & 3))) & 0xFFu;
+  };
+  for (uint32_t i = 0; i < L; ++i) {
+    const uint32_t c = letter(i);
+    if (codec == kCodeSix)
+      put(c <= 'Z' ? c - ('A' - 1) : c - ('a' - 27), 6);
+    else
+      put((c | 0x20u) - ('a' - 1), 5);
+  }
+  if (codec == kCodeFold)
+    for (uint32_t i = 0; i < L; ++i) put((letter(i) >> 5) & 1u, 1);
+  if (nacc) out[q++] = acc;
+  while (q < W) out[q++] = 0;
+}
+
+// A word's key of W words with the given encoding.
+__device__ __forceinline__ void pack_key(uint32_t codec, const uint32_t* __restrict__ u, uint32_t base, uint32_t s0,
+                                         uint32_t L, uint32_t W, uint64_t* __restrict__ out) {
+  if (codec != kCodeBytes) {
+    pack_codes(codec, u, base, s0, L, W, out);
+    return;
+  }
+  pack_word(u, base, s0, L, out);
+  for (uint32_t q = (uint32_t)width_of_len(L); q < W; ++q) out[q] = 0;  // a wider key (the whole-text order)
+}
+
 __global__ void __launch_bounds__(kWordThreads, 5) k_scatter(
     const uint32_t* __restrict__ starts, const uint8_t* __restrict__ letters, const uint32_t* __restrict__ doc_wbase,
     const uint32_t* __restrict__ doc_lbase, const uint32_t* __restrict__ doc_item0, uint32_t ndocs, uint32_t items,
     const uint32_t* __restrict__ seg_lookup, const Segment* __restrict__ segs, uint32_t* __restrict__ cursor,
-    uint64_t* __restrict__ keys, const uint32_t* __restrict__ hist, uint64_t* __restrict__ counts, EmitOut eo) {
+    uint64_t* __restrict__ keys, const uint32_t* __restrict__ hist, uint64_t* __restrict__ counts, EmitOut eo,
+    uint32_t codec) {
   // per-document counts (bin 0 is always 0 in a result) and each document's
   // closing offset; the words themselves are emitted by the sort kernels
   const uint32_t gsz = gridDim.x * blockDim.x;
@@ -82,6 +135,7 @@ __global__ void __launch_bounds__(kWordThreads, 5) k_scatter(
   __shared__ uint32_t cnt[kHist];
   __shared__ uint64_t s_out[kHist];  // word offset in `keys` of the CTA's first slot of each length
   __shared__ uint32_t s_lookup[kHist];
+  __shared__ uint8_t s_w[kHist];  // key width of each length's bucket
   __shared__ uint32_t s_st[kWordBlock + 1];
   __shared__ uint16_t s_idx[kWordBlock];  // the item's words (index in the item) by (length, rank)
   __shared__ uint32_t s_wtot[kWordThreads / 32];
@@ -100,7 +154,11 @@ __global__ void __launch_bounds__(kWordThreads, 5) k_scatter(
     const uint32_t nw = min(w0 + kWordBlock, doc_wbase[d + 1]) - w0;
     // the block's word starts and the document's length -> bucket row
     for (uint32_t i = t; i <= nw; i += kWordThreads) s_st[i] = starts[w0 + i];
-    for (int i = t; i < kHist; i += kWordThreads) s_lookup[i] = seg_lookup[(size_t)d * kHist + i];
+    for (int i = t; i < kHist; i += kWordThreads) {
+      const uint32_t si = seg_lookup[(size_t)d * kHist + i];
+      s_lookup[i] = si;
+      s_w[i] = si == kNoSegment ? 0 : (uint8_t)segs[si].W;
+    }
     __syncthreads();
     // the block's letters, one contiguous range of S, copied in the
     // background (S has 16 bytes of slack past its end) while the words are
@@ -131,7 +189,7 @@ __global__ void __launch_bounds__(kWordThreads, 5) k_scatter(
     const uint32_t c = cnt[t];
     if (c) {
       const uint32_t si = s_lookup[t];
-      s_out[t] = segs[si].key_off + (uint64_t)atomicAdd(&cursor[si], c) * width_of_len(t);
+      s_out[t] = segs[si].key_off + (uint64_t)atomicAdd(&cursor[si], c) * s_w[t];
     }
     uint32_t inc = c;
 #pragma unroll
@@ -161,7 +219,7 @@ __global__ void __launch_bounds__(kWordThreads, 5) k_scatter(
       for (uint32_t j = t; j < nv; j += kWordThreads) {
         const uint32_t i = s_idx[j];
         const uint32_t s0 = s_st[i], L = s_st[i + 1] - s0;
-        pack_word(u, base, s0, L, keys + s_out[L] + (size_t)(j - cnt[L]) * width_of_len(L));
+        pack_key(codec, u, base, s0, L, s_w[L], keys + s_out[L] + (size_t)(j - cnt[L]) * s_w[L]);
       }
     };
     if (staged)
@@ -189,7 +247,7 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const Segment* __restrict
     const Segment sg = segs[s_seg];
     __syncthreads();
     if (sg.flags & kSegKeysOut) continue;  // sorted keys wanted, not words
-    const int W = width_of_len(sg.L);
+    const int W = sg.W;
     const uint32_t T = (uint32_t)tile_of_width(W);
     const uint32_t j0 = (it - sg.etile0) * T;
     const uint32_t cnt = min(T, sg.n - j0);
@@ -206,7 +264,7 @@ cudaError_t launch_scatter(const uint32_t* starts, const uint8_t* letters, const
                            uint64_t* keys, const uint32_t* hist, uint64_t* counts, EmitOut eo, cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
   k_scatter<<<grid, kWordThreads, 0, st>>>(starts, letters, doc_wbase, doc_lbase, doc_item0, ndocs, items, seg_lookup,
-                                           segs, cursor, keys, hist, counts, eo);
+                                           segs, cursor, keys, hist, counts, eo, eo.codec);
   return cudaGetLastError();
 }
 

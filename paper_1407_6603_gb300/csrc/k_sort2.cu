@@ -46,11 +46,21 @@ __device__ void warp_sort_g(const Segment& sg, const uint64_t* g, uint32_t n, co
     const uint32_t p = lane * KPT + i;
     if (p < n) {
       uint8_t* dst = eo.stream + sg.stream_off + (size_t)p * L;
+      if (eo.codec == kCodeBytes) {
 #pragma unroll
-      for (int q = 0; q < W; ++q)
+        for (int q = 0; q < W; ++q)
 #pragma unroll
-        for (int b = 0; b < 8; ++b)
-          if ((uint32_t)(q * 8 + b) < L) dst[q * 8 + b] = (uint8_t)(k[i].w[q] >> (56 - 8 * b));
+          for (int b = 0; b < 8; ++b)
+            if ((uint32_t)(q * 8 + b) < L) dst[q * 8 + b] = (uint8_t)(k[i].w[q] >> (56 - 8 * b));
+      } else {
+        uint64_t kw[W];  // (a copy, so that k itself is only indexed by constants)
+#pragma unroll
+        for (int q = 0; q < W; ++q) kw[q] = k[i].w[q];
+        for (uint32_t q = 0; q * 8 < L; ++q) {
+          const uint64_t a = ascii8(eo.codec, L, [&](uint32_t w) { return kw[w]; }, q);
+          for (uint32_t b = 0; b < 8 && q * 8 + b < L; ++b) dst[q * 8 + b] = (uint8_t)(a >> (56 - 8 * b));
+        }
+      }
       if (eo.want_offsets) eo.offsets[sg.out_word + p] = sg.stream_off - sg.doc_stream0 + p * L;
     }
   }
@@ -80,7 +90,7 @@ __global__ void __launch_bounds__(256) k_warp_sort(const Segment* __restrict__ s
   for (uint32_t i = sbeg + blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; i < send; i += warps) {
     const Segment& sg = segs[i];
     const uint64_t* g = keys + sg.key_off;
-    switch (width_of_len(sg.L)) {
+    switch (sg.W) {
       case 1: warp_sort<1>(sg, g, sg.n, eo); break;
       case 2: warp_sort<2>(sg, g, sg.n, eo); break;
       case 4: warp_sort<4>(sg, g, sg.n, eo); break;
@@ -446,7 +456,7 @@ __global__ void __launch_bounds__(kM2Threads, BSORT_K5_MIN_CTAS) k_merge_piped(c
     const uint32_t L = j.L;
     if (L) {
       emit_run<kM2Threads>(L, eo.stream + j.stream, eo.want_offsets ? eo.offsets + j.word : nullptr, j.rel, cnt,
-                           [&](uint32_t q, uint32_t w) { return buf[padw(q * W + w)]; });
+                           [&](uint32_t q, uint32_t w) { return buf[padw(q * W + w)]; }, eo.codec);
     } else {
       uint64_t* out = dst + j.dst;
       for (uint32_t e = t; e < cnt * W; e += kM2Threads) out[e] = buf[padw(e)];

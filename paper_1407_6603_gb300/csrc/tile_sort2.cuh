@@ -223,7 +223,7 @@ __device__ uint64_t* cluster_merge(uint64_t* buf0, uint64_t* buf1, uint64_t* buf
 template <int W, int CL, int G, int NTH>
 __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint64_t* keys, uint64_t* buf0,
                                uint64_t* buf1, uint64_t* buf2, uint64_t* bar, uint32_t& phase, const EmitOut& eo,
-                               Meta* meta, uint64_t wait_limit, const DedupeOut& dd) {
+                               Meta* meta, uint64_t wait_limit, const DedupeOut& dd, uint32_t* s_heads) {
   constexpr int KPT = kptn<W, NTH>();
   constexpr uint32_t T = NTH * KPT;
   constexpr uint32_t TW = T * W;
@@ -267,7 +267,8 @@ __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint6
   if (lost) {
     // nothing of this supertile is written
   } else if (sg.flags & kSegDedupe) {  // its distinct keys and their counts to the bucket's table
-    rle_insert<W, NTH>([&](uint32_t i) { return kload<W>(res + padw(i * W)); }, cnt, sg, dd, meta, wait_limit);
+    rle_insert<W, NTH>([&](uint32_t i) { return kload<W>(res + padw(i * W)); }, cnt, sg, dd, s_heads, meta,
+                       wait_limit);
   } else if (sg.passes == 0 && !(sg.flags & kSegKeysOut)) {  // the bucket is sorted: its words go straight out
     emit_tile<NTH>(sg, (uint32_t)j0, cnt, [&](uint32_t j, uint32_t q) { return res[padw(j * W + q)]; }, eo);
   } else {  // a run of CL tiles for K5 (or, kSegKeysOut, the sorted keys in place)
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(NTH, BSORT_K4_MIN_CTAS * 256 / NTH) k_tile_sor
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t s_seg;
   __shared__ uint32_t s_first[kSegCache];
+  __shared__ uint32_t s_heads[2048 / 32];  // the duplicate-aware epilogue's group starts (a tile holds <= 2048 keys)
   const int t = threadIdx.x;
   const bool cached = seg_cache_fill<kByStile0>(segs, sbeg, send, s_first);
   uint32_t r = 0;
@@ -307,16 +309,16 @@ __global__ void __launch_bounds__(NTH, BSORT_K4_MIN_CTAS * 256 / NTH) k_tile_sor
     __syncthreads();
     const Segment sg = segs[s_seg];
     __syncthreads();
-    switch (width_of_len(sg.L)) {
-      case 1: sort_supertile<1, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd); break;
-      case 2: sort_supertile<2, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd); break;
+    switch (sg.W) {
+      case 1: sort_supertile<1, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd, s_heads); break;
+      case 2: sort_supertile<2, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd, s_heads); break;
       case 4:
         if constexpr (kptn<4, NTH>() >= 1)
-          sort_supertile<4, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd);
+          sort_supertile<4, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd, s_heads);
         break;
       default:  // (launches with 8-word keys use 256 threads)
         if constexpr (kptn<8, NTH>() >= 1)
-          sort_supertile<8, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd);
+          sort_supertile<8, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd, s_heads);
         break;
     }
   }

@@ -47,8 +47,9 @@ def test_small_wait_limit_gives_timeout_or_exact(bsort_gpu, oracle_mod, synth_mo
     data = _doc(synth_mod, 3 << 20, 501)  # 192 chunks of K1; buckets that need merge passes
     exp = oracle_mod.stable(data, nthreads=8)
     outcomes = []
-    for limit in (1, 2, 16, 256):
-        with bsort_gpu.Context(wait_limit=limit) as c:
+    for limit, tune in ((1, None), (2, None), (16, "dedupe=2"), (256, None), (256, "dedupe=2"), (4096, "dedupe=2")):
+        # (dedupe=2: the duplicate-aware sort, whose hash inserts wait on each other)
+        with bsort_gpu.Context(wait_limit=limit, tune_table=tune) as c:
             for _ in range(2):  # the same context twice: it stays usable after a timeout
                 try:
                     r = c.text(data)

@@ -31,7 +31,7 @@ def assert_same_dev(dev, exp, label=""):
     assert np.array_equal(dev["stream"].cpu().numpy(), exp["stream"]), label
 
 
-@pytest.fixture(scope="module", params=["dedupe=1", "dedupe=0"])
+@pytest.fixture(scope="module", params=["dedupe=2", "dedupe=0"])
 def ctx(bsort_gpu, request):
     """A context with the duplicate-aware sort of the large buckets (the
     default) and one with merge passes instead: every test runs on both."""

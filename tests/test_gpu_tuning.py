@@ -20,7 +20,7 @@ TABLES = ["k4_lanes=2,2,2,2 piped_min=1 dedupe=0", "k4_lanes=8,8,8,8 piped_min=1
           "k4_runs=1 piped_min=1 dedupe=0", "k4_runs=2 k4_streams=0 dedupe=0", "k4_runs=4 dedupe=0",
           "k4_runs_small=16 dedupe=0", "k4_runs_small=16 k4_streams=0 k4_lanes=8,8,8,8",
           "k4_threads=512,512,512,512", "k4_threads=512,256,512,256 k4_lanes=8,2,2,4 k4_runs_small=16",
-          "k4_runs=1 piped_min=1 dedupe=1", "k4_runs=8 k4_runs_small=8 dedupe=1", "k4_streams=0 dedupe=1"]
+          "k4_runs=1 piped_min=1 dedupe=2", "k4_runs=8 k4_runs_small=8 dedupe=2", "k4_streams=0 dedupe=2"]
 
 
 def threshold_doc(W):
