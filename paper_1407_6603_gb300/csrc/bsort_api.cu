@@ -185,7 +185,7 @@ struct bsort_ctx {
   // the duplicate-aware sort: hash tables (stamped with the call's generation
   // `gen`, so never cleared between calls), the distinct-key arrays and their
   // ping-pong partner, the second layout, merge scratch and count prefixes
-  DevBuf htab, uA, uB, plan2, samples2, jobs2, pre, ssum, tfirst;
+  DevBuf htab, uA, uB, plan2, samples2, jobs2, pre, ssum, tfirst, icnt;
   HostBuf h_plan2, h_ucnt;
   uint32_t gen = 0;
   cudaEvent_t dedupe_ev = nullptr;  // the distinct-key counts reached the host
@@ -990,10 +990,31 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   std::vector<uint8_t>& group = c->groupv;
   group.clear();
   uint64_t big_tiles = 0;  // merge tiles of the buckets that need merge passes
+  const uint32_t order = c->cfg.order;
   for (uint32_t d = 0; d < ndocs; ++d) {
     if (c->doc_status[d] != BSORT_OK) continue;
     const uint32_t* h = h_hist + (size_t)d * kHist;
     uint32_t word_before = h_wbase[d] + d, byte_before = h_lbase[d];
+    if (order == BSORT_ORDER_WHOLE) {
+      // one bucket of every word of the document, keys zero-padded to its
+      // longest word; the words are emitted from the sorted keys afterwards
+      const uint32_t n = h_wbase[d + 1] - h_wbase[d];
+      if (n) {
+        Segment sg{};
+        sg.n = n;
+        sg.L = std::min(h_maxlen[d], (uint32_t)kHist - 1);
+        sg.doc = d;
+        sg.out_word = word_before;
+        sg.stream_off = byte_before;
+        sg.doc_stream0 = h_lbase[d];
+        sg.W = (uint32_t)key_width(c->codec, sg.L);
+        sg.flags = kSegKeysOut;
+        const uint8_t gi = group_of(sg, big_tiles);
+        cand.push_back(sg);
+        group.push_back(gi);
+      }
+      continue;
+    }
     for (uint32_t L = 1, Lmax = std::min(h_maxlen[d], (uint32_t)kHist - 1); L <= Lmax; ++L) {
       const uint32_t n = h[L];
       if (n) {
@@ -1022,7 +1043,10 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   std::vector<uint32_t>& dd_seg = c->dd_seg;  // candidate index of each such bucket
   dd_seg.clear();
   const uint64_t piped_tiles = (uint64_t)c->tune.piped_min * c->sm_count * merge_piped_ctas_per_sm();
-  if (c->tune.dedupe == 2 || (c->tune.dedupe == 1 && big_tiles >= piped_tiles))
+  // (the buckets of the other orders: the whole order's words have mixed
+  // lengths, which the expansion does not handle; the length order sorts nothing)
+  if (order <= BSORT_ORDER_FOLDED &&
+      (c->tune.dedupe == 2 || (c->tune.dedupe == 1 && big_tiles >= piped_tiles)))
     for (uint32_t i = 0; i < nseg; ++i)
       if (group[i] < 4) {
         cand[i].flags = kSegDedupe | ((uint32_t)dd_seg.size() << 8);
@@ -1038,7 +1062,8 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   const size_t cursor_bytes = align_up(4ull * (std::max<uint32_t>(nseg, 1) + 4), 256);
   const size_t ucnt_bytes = align_up(4ull * std::max<uint32_t>(ndd, 1), 256);
   const size_t ins_bytes = align_up(sizeof(DedupeIns) * std::max<uint32_t>(ndd, 1), 256);
-  const size_t plan_bytes = seg_bytes + lookup_bytes + cursor_bytes + ucnt_bytes + ins_bytes;
+  const size_t var_bytes = order == BSORT_ORDER_WHOLE ? align_up(sizeof(VarDesc) * std::max<uint32_t>(nseg, 1), 256) : 0;
+  const size_t plan_bytes = seg_bytes + lookup_bytes + cursor_bytes + ucnt_bytes + ins_bytes + var_bytes;
   GROW_HOST(c->h_plan, plan_bytes, "layout");
   Segment* const segs = hptr<Segment>(c->h_plan);
   uint32_t* const lookup = hptr<uint32_t>(c->h_plan, seg_bytes);
@@ -1051,8 +1076,18 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   uint64_t htab_words = 0, uniq_words = 0;
   std::vector<uint32_t>& dd_pos = c->dd_pos;  // table position of each duplicate-aware bucket
   dd_pos.assign(ndd, 0);
+  VarDesc* const vdesc = hptr<VarDesc>(c->h_plan, plan_bytes - var_bytes);
+  uint32_t max_doc_words = 0;
   for (uint32_t i = 0; i < nseg; ++i) {
     Segment& sg = segs[i];
+    if (order == BSORT_ORDER_WHOLE) {  // every length of the document goes to its one bucket
+      for (uint32_t L = 1; L <= sg.L; ++L)
+        if (h_hist[(size_t)sg.doc * kHist + L]) lookup[(size_t)sg.doc * kHist + L] = i;
+      vdesc[i] = VarDesc{sg.key_off, sg.n, sg.W, sg.final_buf, h_lbase[sg.doc + 1] - h_lbase[sg.doc], sg.out_word,
+                         sg.stream_off, sg.doc_stream0, 0u};
+      max_doc_words = std::max(max_doc_words, sg.n);
+      continue;
+    }
     lookup[(size_t)sg.doc * kHist + sg.L] = i;
     if (sg.flags & kSegDedupe) {
       const uint32_t di = seg_dedupe_index(sg);
@@ -1072,8 +1107,9 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
 
   // ---- upload the layout, size the key and output buffers ----
   GROW(c->plan, plan_bytes, "layout");
-  GROW(c->keysA, 8 * std::max<uint64_t>(p1.key_words, 16), "keys");
-  GROW(c->keysB, 8 * std::max<uint64_t>(p1.key_words, 16), "keys");
+  const uint64_t key_words = order == BSORT_ORDER_LENGTH ? 16 : std::max<uint64_t>(p1.key_words, 16);
+  GROW(c->keysA, 8 * key_words, "keys");
+  GROW(c->keysB, 8 * key_words, "keys");
   GROW(c->samples, 8 * std::max<uint64_t>(p1.smp_words, 16), "merge samples");
   GROW(c->counts, 8ull * ndocs * kHist, "counts");
   GROW(c->offsets, 4ull * ((uint64_t)n_total + ndocs), "offsets");
@@ -1114,16 +1150,26 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   for (int g = 0; g < kGroups; ++g) key_bytes_all += p1.kb[g];
   const uint32_t grid_cap = (uint32_t)c->sm_count * 16;
   const EmitOut eo{dptr<uint8_t>(c->stream), dptr<uint32_t>(c->offsets), c->cfg.want_offsets, c->codec};
+  if (order == BSORT_ORDER_LENGTH) GROW(c->icnt, 4ull * kHist * std::max<uint32_t>(items, 1), "length counts");
   {
     // K3 also writes each document's counts and closing offset, so it runs
-    // even when no document has a word
+    // even when no document has a word (and, for the length order, only that)
     const uint32_t count_grid = std::min<uint32_t>((ndocs * kHist + kWordThreads - 1) / kWordThreads, grid_cap);
-    const uint32_t grid = std::max<uint32_t>(std::max(items, count_grid), 1u);
+    const uint32_t grid = std::max<uint32_t>(std::max(order == BSORT_ORDER_LENGTH ? 0u : items, count_grid), 1u);
     LAUNCH(kScatter,
            (double)s_total + 4.0 * n_total + key_bytes_all + (4.0 + 8.0) * kHist * ndocs + (off_bytes ? 12.0 : 0.0) * ndocs,
            launch_scatter(dptr<uint32_t>(c->starts), dptr<uint8_t>(c->letters), d_wbase, d_lbase, d_item0, ndocs,
-                          items, grid, lookup_dev, segs_dev, cursor_dev, kA, d_hist, dptr<uint64_t>(c->counts), eo, st),
+                          items, grid, lookup_dev, segs_dev, cursor_dev, kA, d_hist, dptr<uint64_t>(c->counts), eo,
+                          order != BSORT_ORDER_LENGTH, st),
            "K3 scatter");
+  }
+  if (order == BSORT_ORDER_LENGTH) {
+    // no sort: every word's place follows from the per-block length counts
+    LAUNCH(kEmit, (double)s_total + 4.0 * n_total + (double)n_total * (off_bytes ? 4.0 : 0.0) + s_total,
+           launch_length_order(dptr<uint32_t>(c->starts), dptr<uint8_t>(c->letters), d_wbase, d_item0, ndocs, items,
+                               lookup_dev, segs_dev, dptr<uint32_t>(c->icnt), eo, st),
+           "length order");
+    return BSORT_OK;
   }
   // K4, K5, K6 of the buckets.  The first K4 launch (on the call's stream)
   // sorts the buckets that need merge passes: for the duplicate-aware sort,
@@ -1150,6 +1196,14 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   for (size_t i = 0; i < joined.size(); ++i) {
     CK(cudaEventRecord(c->join_ev[i], joined[i]), "join");
     CK(cudaStreamWaitEvent(st, c->join_ev[i], 0), "join");
+  }
+  if (order == BSORT_ORDER_WHOLE && nseg) {
+    // the words of the whole-text order, from the sorted keys
+    GROW(c->ssum, 4 * std::max<uint64_t>((uint64_t)nseg * var_slices(max_doc_words), 16), "letter prefixes");
+    LAUNCH(kEmit, (double)key_bytes_all + (double)s_total + (double)n_total * (off_bytes ? 4.0 : 0.0),
+           launch_var_emit(dptr<VarDesc>(c->plan, plan_bytes - var_bytes), nseg, max_doc_words, kA, kB, c->codec,
+                           dptr<uint32_t>(c->ssum), d_sticky, eo, st),
+           "whole-text emit");
   }
   return BSORT_OK;
 }
@@ -1235,7 +1289,7 @@ bsort_status bsort_create(bsort_ctx** out, const bsort_config* cfg) {
   if (conf.wait_limit == 0) conf.wait_limit = kDefaultWaitLimit;
   conf.want_offsets = conf.want_offsets ? 1 : 0;
   conf.profile = conf.profile ? 1 : 0;
-  if (conf.order > BSORT_ORDER_FOLDED || conf.key_pack > BSORT_KEYS_LETTERS6) return BSORT_E_INVAL;
+  if (conf.order > BSORT_ORDER_LENGTH || conf.key_pack > BSORT_KEYS_LETTERS6) return BSORT_E_INVAL;
   Tune tune;
   if (!parse_tune(conf.tune_table, tune)) return BSORT_E_INVAL;
   int dev = conf.device;
@@ -1290,7 +1344,7 @@ void bsort_destroy(bsort_ctx* c) {
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
   for (DevBuf* b : {&c->sticky, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB,
                     &c->counts, &c->offsets, &c->stream, &c->jobs, &c->samples, &c->htab, &c->uA, &c->uB, &c->plan2,
-                    &c->samples2, &c->jobs2, &c->pre, &c->ssum, &c->tfirst})
+                    &c->samples2, &c->jobs2, &c->pre, &c->ssum, &c->tfirst, &c->icnt})
     if (b->p) cudaFree(b->p);
   for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets,
                      &c->h_stream, &c->h_flag, &c->h_plan2, &c->h_ucnt})

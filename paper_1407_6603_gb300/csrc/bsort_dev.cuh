@@ -182,6 +182,15 @@ struct ExpandDesc {
 constexpr uint32_t kExpandTileWords = 2048;
 // words per output tile of the expansion for keys of W u64 words
 __host__ __device__ inline uint32_t expand_tile(uint32_t W) { return kExpandTileWords / W; }
+// The whole-text order's emission: per document, its bucket of every word
+// sorted with zero-padded keys (kept in the key buffer final_buf names).
+struct VarDesc {
+  uint64_t key_off;
+  uint32_t n, W, final_buf;
+  uint32_t letters;  // the document's letters: what the words' lengths must add up to
+  uint32_t out_word, stream_off, doc_stream0;
+  uint32_t pad;
+};
 // Where K4's hash inserts go (one call's tables, arrays and counters).
 struct DedupeOut {
   const DedupeIns* ins;
@@ -450,10 +459,12 @@ cudaError_t launch_tokenize1p(const uint8_t* in, const DocDesc* docs, DocDesc do
                               uint8_t* scratch, uint8_t* letters, uint32_t* starts, uint32_t* hist,
                               uint32_t* doc_maxlen, uint32_t* doc_wbase, uint32_t* doc_lbase, uint32_t* doc_item0, Meta* meta,
                               Meta* sticky, uint32_t l_cap, uint64_t wait_limit, HostMeta hm, cudaStream_t st);
+// pack = false: only the counts and closing offsets, no keys (the length order).
 cudaError_t launch_scatter(const uint32_t* starts, const uint8_t* letters, const uint32_t* doc_wbase,
                            const uint32_t* doc_lbase, const uint32_t* doc_item0, uint32_t ndocs, uint32_t items,
                            uint32_t grid, const uint32_t* seg_lookup, const Segment* segs, uint32_t* cursor,
-                           uint64_t* keys, const uint32_t* hist, uint64_t* counts, EmitOut eo, cudaStream_t st);
+                           uint64_t* keys, const uint32_t* hist, uint64_t* counts, EmitOut eo, bool pack,
+                           cudaStream_t st);
 cudaError_t launch_tile_sort(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
                              uint32_t grid, uint64_t* keys, Meta* meta, uint64_t wait_limit, cudaStream_t st);
 cudaError_t launch_merge_pass(int W, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t tiles,
@@ -509,6 +520,17 @@ struct ExpandCaps {
 cudaError_t launch_expand(const ExpandDesc* ed, uint32_t nbuckets, uint32_t max_U, uint32_t max_tiles,
                           const uint64_t* uA, const uint64_t* uB, uint32_t* pre, uint32_t* ssum, uint32_t* tfirst,
                           EmitOut eo, Meta* meta, ExpandCaps caps, cudaStream_t st);
+// The length order (Table 1): words grouped by length in input order, from
+// the word starts, the letters and the (document, length) buckets' places;
+// icnt holds items x 256 counts.
+cudaError_t launch_length_order(const uint32_t* starts, const uint8_t* letters, const uint32_t* doc_wbase,
+                                const uint32_t* doc_item0, uint32_t ndocs, uint32_t items, const uint32_t* seg_lookup,
+                                const Segment* segs, uint32_t* icnt, EmitOut eo, cudaStream_t st);
+// The whole-text order's words from nb documents' sorted zero-padded keys
+// (max_n: the most words of one document); ssum holds nb x var_slices(max_n).
+cudaError_t launch_var_emit(const VarDesc* vd, uint32_t nb, uint32_t max_n, const uint64_t* kA, const uint64_t* kB,
+                            uint32_t codec, uint32_t* ssum, Meta* meta, EmitOut eo, cudaStream_t st);
+size_t var_slices(uint32_t max_n);
 // Entries of the slice sums launch_expand needs per bucket (buffer ssum holds
 // nbuckets x expand_slices(max_U)); tfirst holds one entry per output tile.
 size_t expand_slices(uint32_t max_U);

@@ -261,10 +261,11 @@ __global__ void __launch_bounds__(kSortThreads) k_emit(const Segment* __restrict
 cudaError_t launch_scatter(const uint32_t* starts, const uint8_t* letters, const uint32_t* doc_wbase,
                            const uint32_t* doc_lbase, const uint32_t* doc_item0, uint32_t ndocs, uint32_t items,
                            uint32_t grid, const uint32_t* seg_lookup, const Segment* segs, uint32_t* cursor,
-                           uint64_t* keys, const uint32_t* hist, uint64_t* counts, EmitOut eo, cudaStream_t st) {
+                           uint64_t* keys, const uint32_t* hist, uint64_t* counts, EmitOut eo, bool pack,
+                           cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
-  k_scatter<<<grid, kWordThreads, 0, st>>>(starts, letters, doc_wbase, doc_lbase, doc_item0, ndocs, items, seg_lookup,
-                                           segs, cursor, keys, hist, counts, eo, eo.codec);
+  k_scatter<<<grid, kWordThreads, 0, st>>>(starts, letters, doc_wbase, doc_lbase, doc_item0, ndocs, pack ? items : 0u,
+                                           seg_lookup, segs, cursor, keys, hist, counts, eo, eo.codec);
   return cudaGetLastError();
 }
 

@@ -4,7 +4,12 @@
   the result must be the ASCII order's, byte for byte.
 * order=ORDER_FOLDED: alphabetic order with case ignored, ties in ASCII
   order, per length bucket; compared with the oracle's folded order.
-Each runs with the duplicate-aware sort forced on (dedupe=2) and off.
+* order=ORDER_WHOLE: every word of a document in ASCII order, a word before
+  the longer words it begins (one bucket per document, zero-padded keys),
+  with byte and six-bit keys.
+* order=ORDER_LENGTH: length buckets in input order (no sort at all).
+Each runs with the duplicate-aware sort forced on (dedupe=2) and off; the
+whole and length orders never use it, so there both must agree anyway.
 """
 import random
 
@@ -15,7 +20,8 @@ from test_gpu_parity import assert_same, assert_same_dev
 
 pytestmark = pytest.mark.gpu
 
-MODES = [("letters6", dict(key_pack=1), 0), ("folded", dict(order=1), 1), ("folded6", dict(order=1, key_pack=1), 1)]
+MODES = [("letters6", dict(key_pack=1), 0), ("folded", dict(order=1), 1), ("folded6", dict(order=1, key_pack=1), 1),
+         ("whole", dict(order=2), 2), ("whole6", dict(order=2, key_pack=1), 2), ("length", dict(order=3), 3)]
 
 
 @pytest.fixture(scope="module", params=[(m, t) for m in MODES for t in ("dedupe=2", "dedupe=0")],
@@ -87,6 +93,18 @@ def test_orders_batch(octx, oracle_mod, synth_mod):
     assert st == 0
     for i, d in enumerate(docs):
         assert_same(rs[i], expect(oracle_mod, d, order), f"doc {i}")
+
+
+def test_orders_prefixes_and_duplicates(octx, oracle_mod):
+    """Words that begin other words, many copies of few spellings, and
+    documents of one word or one length."""
+    c, order = octx
+    rng = random.Random(7)
+    stems = [b"a", b"ab", b"abc", b"abcdefgh", b"abcdefghi", b"abcdefghij", b"abcdefghijk", b"B", b"Ba", b"z" * 17]
+    words = [rng.choice(stems) + (b"" if rng.random() < 0.6 else bytes(rng.choice(b"aZ") for _ in range(rng.randint(1, 9))))
+             for _ in range(30_000)]
+    for data in (b" ".join(words), b"single", b"same same same SAME", b"abc abd abe ab a"):
+        assert_same(c.text(data), expect(oracle_mod, data, order))
 
 
 def test_letters6_is_the_ascii_result(bsort_gpu, synth_mod):
