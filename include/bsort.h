@@ -253,8 +253,11 @@ bsort_status bsort_device_finish(bsort_ctx* ctx, void* stream);
 typedef struct {
   const char* name;   /* kernel family: "tokenize", "scatter", "tile_sort", "merge_pass",
                          "merge_cut" (the tile cuts of a pipelined merge pass), "emit";
-                         and "host_gap", the device time of the call's one host round trip (the
-                         length counts read back, the bucket layout copied in) (static string) */
+                         "dedupe" (the duplicate-aware sort's hash aggregation of the large
+                         buckets) and "expand" (its expansion of the sorted distinct words);
+                         and "host_gap", the device time of the call's host round trips (the
+                         length counts read back and the bucket layout copied in; with the
+                         duplicate-aware sort, also its distinct-key counts) (static string) */
   uint64_t launches;  /* launches since the last read */
   double ms;          /* summed device time of those launches (0 when profiling is off) */
   double bytes;       /* summed algorithmic bytes of those launches */

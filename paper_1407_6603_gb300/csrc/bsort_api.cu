@@ -145,12 +145,12 @@ struct MetaLayout {
   }
 };
 
-enum Kind { kTokenize, kScatter, kTileSort, kMerge, kMergeCut, kEmit, kHostGap, kExpand, kKinds };
+enum Kind { kTokenize, kScatter, kTileSort, kMerge, kMergeCut, kEmit, kHostGap, kExpand, kDedupe, kKinds };
 // host_gap is no kernel: the device time between counts reaching the host and
 // the first launch after the layout built from them (the call's round trips:
 // the length counts, and the distinct-key counts of the duplicate-aware sort)
 const char* const kKindName[kKinds] = {"tokenize", "scatter",  "tile_sort", "merge_pass",
-                                       "merge_cut", "emit",     "host_gap",  "expand"};
+                                       "merge_cut", "emit",     "host_gap",  "expand", "dedupe"};
 
 struct ProfRec {
   int kind;
@@ -182,12 +182,14 @@ struct bsort_ctx {
   HostBuf h_sticky;
   DevBuf in, docs, meta, starts, letters, plan, keysA, keysB, counts, offsets, stream, jobs, samples;
   HostBuf h_in, h_docs, h_meta, h_plan, h_counts, h_offsets, h_stream;
-  // the duplicate-aware sort: hash tables (stamped with the call's generation
-  // `gen`, so never cleared between calls), the distinct-key arrays and their
-  // ping-pong partner, the second layout, merge scratch and count prefixes
-  DevBuf htab, uA, uB, plan2, samples2, jobs2, pre, ssum, tfirst, icnt;
+  // the duplicate-aware sort: hash tables (all slots zero between calls: each
+  // call's claims are undone on the device; htab_clean says whether that is
+  // known to hold, else the next call clears them), the distinct-key arrays
+  // and their ping-pong partner, the second layout, merge scratch and count
+  // prefixes
+  DevBuf htab, dcnt, uA, uB, plan2, samples2, jobs2, pre, ssum, tfirst, icnt;
   HostBuf h_plan2, h_ucnt;
-  uint32_t gen = 0;
+  bool htab_clean = false;
   cudaEvent_t dedupe_ev = nullptr;  // the distinct-key counts reached the host
   std::vector<uint32_t> dd_seg, dd_pos;
   std::vector<Segment> segv2;
@@ -488,6 +490,10 @@ struct SortPlan {
   double ob[kGroups] = {};
   uint32_t etile = 0, wtiles[2] = {}, wpasses[2] = {}, mtiles[4] = {}, mpasses[4] = {};
   uint64_t jobs_total = 0, job_at[4] = {};
+  // the duplicate-aware sort's buckets (groups 0..3 marked kSegDedupe): the
+  // hash-aggregation launch covers [dd_beg, dd_end) in dd_units units
+  uint32_t dd_units = 0, dd_beg = 0, dd_end = 0;
+  double dd_bytes = 0;
   uint32_t gb(int g) const { return pbeg[pos_of[g]]; }      // first segment of group g
   uint32_t ge(int g) const { return pbeg[pos_of[g] + 1]; }  // one past its last
 };
@@ -541,15 +547,23 @@ void plan_sorts(const bsort_ctx* c, const std::vector<Segment>& cand, const std:
     }
   }
   // K4 launches: cluster size, its own group, and the table range it covers
-  // (the merge-pass groups too, for the cluster size that makes their runs)
+  // (the merge-pass groups too, for the cluster size that makes their runs,
+  // unless they go to the duplicate-aware sort's own launch)
+  bool dd = false;
+  for (uint32_t i = 0; i < p.nseg; ++i) dd |= group[i] < 4 && (cand[i].flags & kSegDedupe);
+  const bool runs_in_k4 = !dd;
   for (K4Launch& l : p.k4) {
     if (l.gc < 0) {
-      l.sbeg = p.runs == l.cluster ? p.gb(0) : 0u;
-      l.send = p.runs == l.cluster ? p.ge(4) : 0u;
+      l.sbeg = p.runs == l.cluster && runs_in_k4 ? p.gb(0) : 0u;
+      l.send = p.runs == l.cluster && runs_in_k4 ? p.ge(4) : 0u;
     } else {
-      l.sbeg = l.cluster == p.runs ? p.gb(0) : p.gb(l.gc);
+      l.sbeg = l.cluster == p.runs && runs_in_k4 ? p.gb(0) : p.gb(l.gc);
       l.send = p.ge(l.gc);
     }
+  }
+  if (dd) {
+    p.dd_beg = p.gb(0);
+    p.dd_end = p.ge(4);
   }
   auto out_bytes = [&](const Segment& sg) {  // a bucket's output: its letters and offsets
     return (sg.flags & kSegKeysOut) ? 8.0 * sg.W * sg.n : (double)sg.n * (sg.L + off_bytes);
@@ -567,6 +581,11 @@ void plan_sorts(const bsort_ctx* c, const std::vector<Segment>& cand, const std:
     if (gi >= 10) {  // only the wide keys go through K6
       sg.etile0 = p.etile;
       p.etile += (sg.n + tile_of_width(W) - 1) / tile_of_width(W);
+    }
+    if (gi < 4 && (sg.flags & kSegDedupe)) {  // the hash-aggregation units
+      sg.stile0 = p.dd_units;
+      p.dd_units += (sg.n + dedupe_unit_keys(W) - 1) / dedupe_unit_keys(W);
+      p.dd_bytes += 8.0 * W * sg.n;
     }
     if (gi < 4) {
       // Every bucket of the group gets its merge tiles, also one that needs
@@ -627,7 +646,8 @@ bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, 
     if (ra != rb) return ra;
     return p.k4[a].levels > p.k4[b].levels;
   });
-  const bool small_work = p.ge(9) > p.gb(9) || n4 > 1;  // the warp sort, or more than one K4 launch
+  // the warp sort, or more than one launch of K4 and the hash aggregation
+  const bool small_work = p.ge(9) > p.gb(9) || n4 + (p.dd_units ? 1 : 0) > 1;
   const bool side = side_ok && small_work && c->tune.k4_streams;
   if (side) CK(cudaEventRecord(c->fork_ev, st), "fork");
   int used = 0;
@@ -638,10 +658,25 @@ bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, 
     return sx;
   };
   bool first_done = false;
+  if (p.dd_units) {
+    // the duplicate-aware sort's buckets first, on the call's stream: the
+    // distinct-key counts are read back right after it
+    Trace tr_(c, st, kDedupe, p.dd_bytes);
+    c->htab_clean = false;  // until the launches that also undo the claims are enqueued
+    CK(tr_.done(launch_dedupe_hash(d_segs, p.dd_beg, p.dd_end, p.dd_units, c->sm_count, kA, dd, p.dd_end - p.dd_beg,
+                                   d_sticky, c->cfg.wait_limit, st)),
+       "duplicate-aware hash aggregation");
+    c->htab_clean = true;
+    if (after_first_k4) {
+      const bsort_status s = after_first_k4();
+      if (s != BSORT_OK) return s;
+    }
+    first_done = true;
+  }
   for (int q = 0; q < n4; ++q) {
     const K4Launch& l = p.k4[k4_order[q]];
     cudaStream_t sx = st;
-    if (q > 0 && side) {
+    if ((q > 0 || p.dd_units) && side) {
       sx = side_stream();
       CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
     }
@@ -649,9 +684,9 @@ bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, 
     tr_.variant = (uint32_t)l.cluster;
     const int cls = l.cluster == 1 ? 0 : l.cluster == 2 ? 1 : l.cluster == 4 ? 2 : 3;  // 16 as 8
     CK(tr_.done(launch_tile_sort2(l.cluster, c->tune.k4_lanes[cls], c->tune.k4_threads[cls], d_segs, l.sbeg, l.send,
-                                  l.supertiles, c->sm_count, l.max_w, kA, eo, d_sticky, c->cfg.wait_limit, dd, sx)),
+                                  l.supertiles, c->sm_count, l.max_w, kA, eo, d_sticky, c->cfg.wait_limit, sx)),
        "K4 tile_sort");
-    if (q == 0 && after_first_k4) {
+    if (q == 0 && !first_done && after_first_k4) {
       const bsort_status s = after_first_k4();
       if (s != BSORT_OK) return s;
       first_done = true;
@@ -855,7 +890,7 @@ bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* i
   const Segment* segs2_dev = dptr<Segment>(c->plan2);
   uint32_t* barrier2 = dptr<uint32_t>(c->plan2, seg_bytes);
   std::vector<cudaStream_t> none;
-  const DedupeOut no_dd{nullptr, nullptr, nullptr, nullptr, 0};
+  const DedupeOut no_dd{nullptr, nullptr, nullptr, nullptr, nullptr};
   bsort_status s = launch_sorts(c, p2, segs2, segs2_dev, dptr<uint64_t>(c->uA), dptr<uint64_t>(c->uB),
                                 dptr<uint64_t>(c->samples2), c->jobs2, barrier2, eo, no_dd, st, false, none, {});
   if (s != BSORT_OK) return s;
@@ -965,6 +1000,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
                 hm->err_timeout ? "a bounded device wait of the tokenize kernel ran out (the call's outputs are not valid)"
                                 : "a bounded device wait ran out (injected by BSORT_FAULT=timeout)");
   if (hm->err_prev) {
+    c->htab_clean = false;
     CK(cudaMemsetAsync(d_sticky, 0, sizeof(Meta), st), "clear timeout flag");
     return fail(c, BSORT_E_TIMEOUT,
                 "a bounded device wait of the sort kernels ran out in an earlier device call on this context, "
@@ -1073,7 +1109,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   const uint64_t off_bytes = c->cfg.want_offsets ? 4 : 0;
   SortPlan p1;
   plan_sorts(c, cand, group, big_tiles, false, off_bytes, segs, p1);
-  uint64_t htab_words = 0, uniq_words = 0;
+  uint64_t htab_words = 0, uniq_words = 0, cnt_words = 0;
   std::vector<uint32_t>& dd_pos = c->dd_pos;  // table position of each duplicate-aware bucket
   dd_pos.assign(ndd, 0);
   VarDesc* const vdesc = hptr<VarDesc>(c->h_plan, plan_bytes - var_bytes);
@@ -1101,6 +1137,8 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       htab_words += (1ull << d.hbits) * (W + 1);
       d.uniq_off = uniq_words;
       uniq_words += align_up((size_t)sg.n * d.Wp, 16);
+      d.cnt_off = cnt_words;
+      if (W == 1) cnt_words += align_up((size_t)sg.n, 16);
       dd_pos[di] = i;
     }
   }
@@ -1114,21 +1152,23 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   GROW(c->counts, 8ull * ndocs * kHist, "counts");
   GROW(c->offsets, 4ull * ((uint64_t)n_total + ndocs), "offsets");
   GROW(c->stream, (size_t)s_total + 16, "stream");
-  DedupeOut ddo{nullptr, nullptr, nullptr, nullptr, 0};
+  DedupeOut ddo{nullptr, nullptr, nullptr, nullptr, nullptr};
   if (ndd) {
     const void* old_tab = c->htab.p;
+    const void* old_cnt = c->dcnt.p;
     GROW(c->htab, 8 * htab_words, "hash tables");
+    GROW(c->dcnt, 8 * std::max<uint64_t>(cnt_words, 16), "distinct-key counts");
     GROW(c->uA, 8 * std::max<uint64_t>(uniq_words, 16), "distinct keys");
     GROW(c->uB, 8 * std::max<uint64_t>(uniq_words, 16), "distinct keys");
-    if (c->htab.p != old_tab || ++c->gen == 0) {
-      // a new table (or a generation counter that wrapped): every slot must
-      // carry a generation that no call uses, 0
+    // a new table or count array, or ones an earlier call may have left dirty
+    if (c->htab.p != old_tab || c->dcnt.p != old_cnt || !c->htab_clean) {
       CK(cudaMemsetAsync(c->htab.p, 0, c->htab.cap, st), "clear hash tables");
-      c->gen = 1;
+      CK(cudaMemsetAsync(c->dcnt.p, 0, c->dcnt.cap, st), "clear distinct-key counts");
+      c->htab_clean = true;
     }
     ddo = DedupeOut{dptr<DedupeIns>(c->plan, seg_bytes + lookup_bytes + cursor_bytes + ucnt_bytes),
                     dptr<uint64_t>(c->htab), dptr<uint64_t>(c->uA),
-                    dptr<uint32_t>(c->plan, seg_bytes + lookup_bytes + cursor_bytes), c->gen};
+                    dptr<uint32_t>(c->plan, seg_bytes + lookup_bytes + cursor_bytes), dptr<uint64_t>(c->dcnt)};
   }
   CK(cudaMemcpyAsync(c->plan.p, c->h_plan.p, plan_bytes, cudaMemcpyHostToDevice, st), "copy layout");
   Segment* const segs_dev = dptr<Segment>(c->plan);
@@ -1239,6 +1279,7 @@ bsort_status read_back(bsort_ctx* c, cudaStream_t st, size_t off_base, size_t st
   for (size_t i = 0; i < (size_t)ndocs * kHist; ++i) hc[i] = (i % kHist) ? hh[i] : 0;
   CK(cudaStreamSynchronize(st), "wait for results");
   if (hs->err_timeout || hs->err_internal) {
+    c->htab_clean = false;  // (a failed check may have left a claimed slot behind)
     CK(cudaMemsetAsync(c->sticky.p, 0, sizeof(Meta), st), "clear timeout flag");
     CK(cudaStreamSynchronize(st), "clear timeout flag");
     if (!hs->err_timeout)
@@ -1343,7 +1384,7 @@ void bsort_destroy(bsort_ctx* c) {
   cudaSetDevice(c->device);
   if (c->own_stream) cudaStreamSynchronize(c->own_stream);
   for (DevBuf* b : {&c->sticky, &c->in, &c->docs, &c->meta, &c->starts, &c->letters, &c->plan, &c->keysA, &c->keysB,
-                    &c->counts, &c->offsets, &c->stream, &c->jobs, &c->samples, &c->htab, &c->uA, &c->uB, &c->plan2,
+                    &c->counts, &c->offsets, &c->stream, &c->jobs, &c->samples, &c->htab, &c->dcnt, &c->uA, &c->uB, &c->plan2,
                     &c->samples2, &c->jobs2, &c->pre, &c->ssum, &c->tfirst, &c->icnt})
     if (b->p) cudaFree(b->p);
   for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets,
@@ -1641,6 +1682,7 @@ bsort_status bsort_device_finish(bsort_ctx* c, void* stream) {
   CK(cudaMemcpyAsync(hs, c->sticky.p, sizeof(Meta), cudaMemcpyDeviceToHost, st), "read status");
   CK(cudaStreamSynchronize(st), "wait for the device work");
   if (hs->err_timeout || hs->err_internal) {
+    c->htab_clean = false;  // (a failed check may have left a claimed slot behind)
     CK(cudaMemsetAsync(c->sticky.p, 0, sizeof(Meta), st), "clear timeout flag");
     CK(cudaStreamSynchronize(st), "clear timeout flag");
     if (!hs->err_timeout) return fail(c, BSORT_E_CUDA, "a consistency check of the sort kernels failed");

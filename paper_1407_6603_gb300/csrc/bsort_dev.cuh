@@ -149,18 +149,21 @@ struct Segment {
 static_assert(sizeof(Segment) == 80, "a segment is five 16-byte words");
 // Segment flags.  kSegKeysOut: the sorted keys stay in the key buffer (final_buf)
 // instead of being emitted as words (the distinct-word arrays of the
-// duplicate-aware sort).  kSegDedupe: K4 sorts the bucket's runs and hands each
-// run's distinct keys, with their multiplicities, to the bucket's hash table.
+// duplicate-aware sort).  kSegDedupe: the hash aggregation kernel (not K4)
+// hands the bucket's distinct keys, with their multiplicities, to the
+// bucket's hash table.
 constexpr uint32_t kSegKeysOut = 1u, kSegDedupe = 2u;
 __host__ __device__ inline uint32_t seg_dedupe_index(const Segment& s) { return s.flags >> 8; }
 
 // Duplicate-aware sort (an option of the sort phase; the result is the same):
 // a bucket's distinct keys are collected in a hash table with their counts,
-// sorted, and expanded by their counts.  Per bucket, for K4's hash inserts:
+// sorted, and expanded by their counts.  Per bucket, for the hash inserts:
 struct DedupeIns {
   uint64_t htab_off;  // first u64 word of the bucket's table: 2^hbits slots of 1 + W words
   uint64_t uniq_off;  // first u64 word of its distinct-key array: entries of Wp words
-                      // (the key's W words, its count, zeros), at most n entries
+                      // (the key's W words, its count, zeros; while the inserts run, the
+                      // slot index after the key or after the count), at most n entries
+  uint64_t cnt_off;   // one-word keys: first of its n words of the count array
   uint32_t hbits;
   uint32_t Wp;        // next_pow2(W + 1)
   uint32_t n;         // the bucket's words: the array's capacity in entries
@@ -191,13 +194,13 @@ struct VarDesc {
   uint32_t out_word, stream_off, doc_stream0;
   uint32_t pad;
 };
-// Where K4's hash inserts go (one call's tables, arrays and counters).
+// Where the hash inserts go (one call's tables, arrays and counters).
 struct DedupeOut {
   const DedupeIns* ins;
-  uint64_t* htab;
+  uint64_t* htab;  // every slot zero between calls
   uint64_t* uniq;
   uint32_t* ucnt;  // distinct keys per bucket so far (zeroed per call)
-  uint32_t gen;    // the call's generation: slots stamped with another are empty
+  uint64_t* dcnt;  // one-word keys' counts by distinct-key index (zero between calls)
 };
 
 // One output tile of a pipelined merge pass (K5), as the cut kernel leaves it:
@@ -474,18 +477,27 @@ cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, 
 // K4 with clusters of `cluster` CTAs of `threads` (256, or 512 when no key
 // of the launch is wider than 4 words) and `lanes` (2, 4 or 8) lanes per
 // odd-even transposition group.
+// The duplicate-aware sort's hash aggregation of segments [sbeg, send) (each
+// marked kSegDedupe, with stile0 its first unit of dedupe_unit_keys(W) keys,
+// `units` in all): every distinct key of a unit goes to its bucket's table
+// with its count; then the `ndd` buckets' distinct-key arrays are completed
+// and their tables' claimed slots zeroed.
+uint32_t dedupe_unit_keys(uint32_t W);
+cudaError_t launch_dedupe_hash(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t units, uint32_t sm_count,
+                               const uint64_t* keys, DedupeOut o, uint32_t ndd, Meta* meta, uint64_t wait_limit,
+                               cudaStream_t st);
 cudaError_t launch_tile_sort2(int cluster, int lanes, int threads, const Segment* segs, uint32_t sbeg, uint32_t send,
                               uint32_t supertiles, int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
-                              uint64_t wait_limit, DedupeOut dd, cudaStream_t st);
+                              uint64_t wait_limit, cudaStream_t st);
 cudaError_t launch_tile_sort2_g2(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                                  int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
-                                 uint64_t wait_limit, DedupeOut dd, cudaStream_t st);
+                                 uint64_t wait_limit, cudaStream_t st);
 cudaError_t launch_tile_sort2_g4(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                                  int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
-                                 uint64_t wait_limit, DedupeOut dd, cudaStream_t st);
+                                 uint64_t wait_limit, cudaStream_t st);
 cudaError_t launch_tile_sort2_g8(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                                  int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
-                                 uint64_t wait_limit, DedupeOut dd, cudaStream_t st);
+                                 uint64_t wait_limit, cudaStream_t st);
 // Merge passes pass0 .. pass0 + npass - 1 (keys between kA and kB, pass p
 // reading kA when p is even); npass > 1 makes one cooperative launch whose
 // passes are separated by grid barriers counted on *barrier (zeroed).

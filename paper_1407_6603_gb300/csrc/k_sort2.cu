@@ -521,12 +521,12 @@ cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, 
 
 cudaError_t launch_tile_sort2(int cluster, int lanes, int threads, const Segment* segs, uint32_t sbeg, uint32_t send,
                               uint32_t supertiles, int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
-                              uint64_t wait_limit, DedupeOut dd, cudaStream_t st) {
+                              uint64_t wait_limit, cudaStream_t st) {
   if (supertiles == 0) return cudaSuccess;
   switch (lanes) {
-    case 2: return launch_tile_sort2_g2(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
-    case 4: return launch_tile_sort2_g4(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
-    case 8: return launch_tile_sort2_g8(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
+    case 2: return launch_tile_sort2_g2(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 4: return launch_tile_sort2_g4(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 8: return launch_tile_sort2_g8(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
     default: return cudaErrorInvalidValue;
   }
 }

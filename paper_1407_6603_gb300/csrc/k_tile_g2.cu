@@ -6,9 +6,9 @@ namespace bsort {
 
 cudaError_t launch_tile_sort2_g2(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                                  int max_grid, int max_width, uint64_t* keys, EmitOut eo, Meta* meta,
-                                 uint64_t wait_limit, DedupeOut dd, cudaStream_t st) {
+                                 uint64_t wait_limit, cudaStream_t st) {
   return tile_sort2_lanes<2>(cluster, threads, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit,
-                              dd, st);
+                              st);
 }
 
 }  // namespace bsort

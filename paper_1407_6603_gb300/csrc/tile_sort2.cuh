@@ -27,7 +27,6 @@
 #include <cooperative_groups.h>
 
 #include "bsort_dev.cuh"
-#include "dedupe.cuh"
 #include "sort_common.cuh"
 
 namespace cg = cooperative_groups;
@@ -223,7 +222,7 @@ __device__ uint64_t* cluster_merge(uint64_t* buf0, uint64_t* buf1, uint64_t* buf
 template <int W, int CL, int G, int NTH>
 __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint64_t* keys, uint64_t* buf0,
                                uint64_t* buf1, uint64_t* buf2, uint64_t* bar, uint32_t& phase, const EmitOut& eo,
-                               Meta* meta, uint64_t wait_limit, const DedupeOut& dd, uint32_t* s_heads) {
+                               Meta* meta, uint64_t wait_limit) {
   constexpr int KPT = kptn<W, NTH>();
   constexpr uint32_t T = NTH * KPT;
   constexpr uint32_t TW = T * W;
@@ -266,9 +265,6 @@ __device__ void sort_supertile(const Segment& sg, uint32_t st, uint32_t r, uint6
   if constexpr (CL > 1) res = cluster_merge<W, CL, NTH>(buf0, buf1, buf2, r);
   if (lost) {
     // nothing of this supertile is written
-  } else if (sg.flags & kSegDedupe) {  // its distinct keys and their counts to the bucket's table
-    rle_insert<W, NTH>([&](uint32_t i) { return kload<W>(res + padw(i * W)); }, cnt, sg, dd, s_heads, meta,
-                       wait_limit);
   } else if (sg.passes == 0 && !(sg.flags & kSegKeysOut)) {  // the bucket is sorted: its words go straight out
     emit_tile<NTH>(sg, (uint32_t)j0, cnt, [&](uint32_t j, uint32_t q) { return res[padw(j * W + q)]; }, eo);
   } else {  // a run of CL tiles for K5 (or, kSegKeysOut, the sorted keys in place)
@@ -281,7 +277,7 @@ template <int CL, int G, int NTH>
 __global__ void __launch_bounds__(NTH, BSORT_K4_MIN_CTAS * 256 / NTH) k_tile_sort2(const Segment* __restrict__ segs, uint32_t sbeg,
                                                            uint32_t send, uint32_t nst, uint32_t buf_words,
                                                            uint64_t* keys, EmitOut eo, Meta* meta,
-                                                           uint64_t wait_limit, DedupeOut dd) {
+                                                           uint64_t wait_limit) {
   extern __shared__ __align__(128) uint64_t sm[];
   uint64_t* buf0 = sm;
   uint64_t* buf1 = sm + buf_words;
@@ -289,7 +285,6 @@ __global__ void __launch_bounds__(NTH, BSORT_K4_MIN_CTAS * 256 / NTH) k_tile_sor
   __shared__ __align__(8) uint64_t bar;
   __shared__ uint32_t s_seg;
   __shared__ uint32_t s_first[kSegCache];
-  __shared__ uint32_t s_heads[2048 / 32];  // the duplicate-aware epilogue's group starts (a tile holds <= 2048 keys)
   const int t = threadIdx.x;
   const bool cached = seg_cache_fill<kByStile0>(segs, sbeg, send, s_first);
   uint32_t r = 0;
@@ -310,15 +305,15 @@ __global__ void __launch_bounds__(NTH, BSORT_K4_MIN_CTAS * 256 / NTH) k_tile_sor
     const Segment sg = segs[s_seg];
     __syncthreads();
     switch (sg.W) {
-      case 1: sort_supertile<1, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd, s_heads); break;
-      case 2: sort_supertile<2, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd, s_heads); break;
+      case 1: sort_supertile<1, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
+      case 2: sort_supertile<2, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit); break;
       case 4:
         if constexpr (kptn<4, NTH>() >= 1)
-          sort_supertile<4, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd, s_heads);
+          sort_supertile<4, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit);
         break;
       default:  // (launches with 8-word keys use 256 threads)
         if constexpr (kptn<8, NTH>() >= 1)
-          sort_supertile<8, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit, dd, s_heads);
+          sort_supertile<8, CL, G, NTH>(sg, st, r, keys, buf0, buf1, buf2, &bar, phase, eo, meta, wait_limit);
         break;
     }
   }
@@ -327,7 +322,7 @@ __global__ void __launch_bounds__(NTH, BSORT_K4_MIN_CTAS * 256 / NTH) k_tile_sor
 template <int CL, int G, int NTH>
 cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t nst, int max_grid,
                           int max_width, uint64_t* keys, const EmitOut& eo, Meta* meta, uint64_t wait_limit,
-                          const DedupeOut& dd, cudaStream_t st) {
+                          cudaStream_t st) {
   (void)max_width;
   const uint32_t buf_words = padded_words(2048u);
   const size_t smem = (size_t)(CL > 1 ? 3 : 1) * buf_words * 8;
@@ -367,8 +362,7 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
   }
   const uint32_t ncl = nst < (uint32_t)clusters * 2u ? nst : (uint32_t)clusters * 2u;
   cfg.gridDim = dim3(ncl * CL, 1, 1);
-  return cudaLaunchKernelEx(&cfg, k_tile_sort2<CL, G, NTH>, segs, sbeg, send, nst, buf_words, keys, eo, meta, wait_limit,
-                            dd);
+  return cudaLaunchKernelEx(&cfg, k_tile_sort2<CL, G, NTH>, segs, sbeg, send, nst, buf_words, keys, eo, meta, wait_limit);
 }
 
 // All cluster sizes and CTA sizes for one lane count G (each K4 translation
@@ -376,13 +370,13 @@ cudaError_t tile_sort2_cl(const Segment* segs, uint32_t sbeg, uint32_t send, uin
 template <int G, int NTH>
 cudaError_t tile_sort2_cls(int cluster, const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t supertiles,
                            int max_grid, int max_width, uint64_t* keys, const EmitOut& eo, Meta* meta,
-                           uint64_t wait_limit, const DedupeOut& dd, cudaStream_t st) {
+                           uint64_t wait_limit, cudaStream_t st) {
   switch (cluster) {
-    case 1: return tile_sort2_cl<1, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
-    case 2: return tile_sort2_cl<2, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
-    case 4: return tile_sort2_cl<4, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
-    case 8: return tile_sort2_cl<8, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
-    case 16: return tile_sort2_cl<16, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, dd, st);
+    case 1: return tile_sort2_cl<1, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 2: return tile_sort2_cl<2, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 4: return tile_sort2_cl<4, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 8: return tile_sort2_cl<8, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
+    case 16: return tile_sort2_cl<16, G, NTH>(segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta, wait_limit, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -390,12 +384,12 @@ cudaError_t tile_sort2_cls(int cluster, const Segment* segs, uint32_t sbeg, uint
 template <int G>
 cudaError_t tile_sort2_lanes(int cluster, int threads, const Segment* segs, uint32_t sbeg, uint32_t send,
                              uint32_t supertiles, int max_grid, int max_width, uint64_t* keys, const EmitOut& eo,
-                             Meta* meta, uint64_t wait_limit, const DedupeOut& dd, cudaStream_t st) {
+                             Meta* meta, uint64_t wait_limit, cudaStream_t st) {
   if (threads == 512 && max_width <= 4)
     return tile_sort2_cls<G, 512>(cluster, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta,
-                                  wait_limit, dd, st);
+                                  wait_limit, st);
   return tile_sort2_cls<G, 256>(cluster, segs, sbeg, send, supertiles, max_grid, max_width, keys, eo, meta,
-                                wait_limit, dd, st);
+                                wait_limit, st);
 }
 
 }  // namespace

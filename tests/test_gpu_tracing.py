@@ -5,7 +5,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-FAMILIES = {"tokenize", "scatter", "tile_sort", "merge_pass", "merge_cut", "emit", "host_gap", "expand"}
+FAMILIES = {"tokenize", "scatter", "tile_sort", "merge_pass", "merge_cut", "emit", "host_gap", "expand", "dedupe"}
 
 
 def test_profile_and_timeline(bsort_gpu, synth_mod):
