@@ -4,14 +4,14 @@
 // length bucket; equal words are byte-identical, so a bucket's sorted words
 // are its distinct words in order, each repeated as often as it occurs.  This
 // kernel finds the distinct words and their counts without sorting the
-// bucket: each unit of 4096 key words (4096 / W keys of one bucket) is
+// bucket: each unit of 2048 key words (2048 / W keys of one bucket) is
 // aggregated in shared memory, then every distinct key of the unit is added
 // with its count to the bucket's hash table in global memory (dedupe.cuh).
 // The distinct keys are sorted and expanded afterwards (k_dedupe.cu).
 //
 // Per unit (one CTA at a time, units strided over a persistent grid):
 //   1. the unit's keys are copied into shared memory (cp.async, 16 bytes a
-//      copy: a bucket's keys start 128-byte aligned and a unit is 32 KiB);
+//      copy: a bucket's keys start 128-byte aligned and a unit is 16 KiB);
 //   2. an open-addressing table of 2 * keys slots (one u32 each: empty, or
 //      the index of the slot's first key in the high half and the count of
 //      its copies in the low half) takes every key: an empty slot is claimed
@@ -28,8 +28,8 @@ namespace bsort {
 namespace {
 
 constexpr int kHaThreads = 256;
-constexpr uint32_t kHaUnitWords = 4096;          // key words per unit (32 KiB)
-constexpr uint32_t kHaSlots = 2 * kHaUnitWords;  // table slots for W = 1 (32 KiB)
+constexpr uint32_t kHaUnitWords = 2048;          // key words per unit (16 KiB)
+constexpr uint32_t kHaSlots = 2 * kHaUnitWords;  // table slots for W = 1 (16 KiB)
 constexpr uint32_t kHaEmpty = 0xFFFFFFFFu;
 constexpr size_t kHaSmem = 8 * kHaUnitWords + 4 * kHaSlots;
 static_assert(kHaUnitWords <= 0xFFFFu, "a slot's key index and count are 16 bits each");
@@ -117,7 +117,7 @@ __device__ void hash_unit(const uint64_t* __restrict__ g, uint32_t cnt, const Se
   __syncthreads();  // the keys and the table are read: the next unit may fill them
 }
 
-__global__ void __launch_bounds__(kHaThreads) k_dedupe_hash(const Segment* __restrict__ segs, uint32_t sbeg,
+__global__ void __launch_bounds__(kHaThreads, 4) k_dedupe_hash(const Segment* __restrict__ segs, uint32_t sbeg,
                                                             uint32_t send, uint32_t units,
                                                             const uint64_t* __restrict__ keys, DedupeOut o,
                                                             Meta* meta, uint64_t wait_limit) {
@@ -208,7 +208,10 @@ cudaError_t launch_dedupe_hash(const Segment* segs, uint32_t sbeg, uint32_t send
     return cudaFuncSetAttribute(k_dedupe_hash, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHaSmem);
   });
   if (e != cudaSuccess) return e;
-  const uint32_t cap = sm_count * 3u;  // 3 CTAs of 64 KiB (+ the segment cache) per SM
+  // 4 CTAs per SM (registers bound it; 32 KiB of shared memory each): the
+  // global inserts are latency-bound, so more warps in flight beat larger
+  // units (which would leave fewer distinct keys to insert)
+  const uint32_t cap = sm_count * 4u;
   k_dedupe_hash<<<units < cap ? units : cap, kHaThreads, kHaSmem, st>>>(segs, sbeg, send, units, keys, o, meta,
                                                                          wait_limit);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
