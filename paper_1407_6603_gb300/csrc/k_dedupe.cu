@@ -11,7 +11,8 @@
 //                   and the entry holding each output tile's first word
 //   k_expand_words  per bucket and output tile: each word's entry (a binary
 //                   search of the tile's prefix entries, staged in shared
-//                   memory), then its letters and offset
+//                   memory), then its offset, and its letters into a shared
+//                   copy of the tile's bytes, which go out as 16-byte stores
 #include "bsort_dev.cuh"
 #include "sort_common.cuh"
 
@@ -164,19 +165,28 @@ __device__ __forceinline__ uint32_t last_le(const uint32_t* pr, uint32_t lo, uin
   return lo;
 }
 
+// Bytes of one output tile's letters, staged in shared memory: T keys of W
+// words hold at most (2048 / W) * floor(64 W / 6) <= 21845 letters (six-bit
+// and case-folded keys spend 6 bits a letter, bytes 8), plus 15 bytes of
+// alignment shift.
+constexpr uint32_t kExpandStage = 21888;
+
 // The words of bucket blockIdx.y, one output tile of T = kExpandTileWords / W
 // at a time (tiles strided over blockIdx.x): word w0 + j of tile k is a copy
 // of entry u(j), the last u with pre[u] <= w0 + j.  The entries from the one
 // holding the tile's first word to the one holding the next tile's first
 // word (every one between covers a word of the tile: at most T + 1 of them)
 // have their prefix staged in shared memory; each thread finds its words'
-// entries there and writes the words' letters (big-endian in the key words)
-// and offsets.
+// entries there, writes their offsets, and writes their letters into a
+// shared-memory copy of the tile's stream bytes, shifted by the destination's
+// offset within 16 bytes; the tile's bytes then go out as aligned 16-byte
+// stores (byte stores only at the two ragged ends).
 __global__ void __launch_bounds__(kExThreads) k_expand_words(const ExpandDesc* __restrict__ ed, uint32_t nb,
                                                              const uint64_t* uA, const uint64_t* uB,
                                                              const uint32_t* pre, const uint32_t* tfirst, EmitOut eo,
                                                              Meta* meta, ExpandCaps caps) {
   __shared__ uint32_t s_pre[kExpandTileWords + 1];
+  __shared__ __align__(16) uint8_t s_out[kExpandStage];
   if (blockIdx.y >= nb) return;
   const ExpandDesc d = ed[blockIdx.y];
   if (!desc_ok(d, caps)) return;  // reported by the prefix kernels
@@ -198,17 +208,34 @@ __global__ void __launch_bounds__(kExThreads) k_expand_words(const ExpandDesc* _
     }
     for (uint32_t k = threadIdx.x; k <= ub - ua; k += kExThreads) s_pre[k] = pr[ua + k];
     __syncthreads();
+    uint8_t* const dst = eo.stream + d.stream_off + (size_t)w0 * d.L;
+    const uint32_t nbytes = cnt * d.L;
+    const uint32_t sh = (uint32_t)((uintptr_t)dst & 15u);
+    const bool staged = sh + nbytes <= kExpandStage;  // (always, for keys of at most 8 words)
     for (uint32_t j = threadIdx.x; j < cnt; j += kExThreads) {
       const uint32_t w = w0 + j;
       const uint64_t* e = P + (uint64_t)(ua + last_le(s_pre, 0, ub - ua, w)) * d.Wp;
-      uint8_t* out = eo.stream + d.stream_off + (size_t)w * d.L;
+      uint8_t* out = staged ? s_out + sh + j * d.L : dst + (size_t)j * d.L;
       for (uint32_t q = 0; q * 8 < d.L; ++q) {
         const uint64_t a = ascii8(eo.codec, d.L, [&](uint32_t x) { return e[x]; }, q);
         for (uint32_t b = 0; b < 8 && q * 8 + b < d.L; ++b) out[q * 8 + b] = (uint8_t)(a >> (56 - 8 * b));
       }
       if (eo.want_offsets) eo.offsets[d.out_word + w] = d.stream_off - d.doc_stream0 + w * d.L;
     }
-    __syncthreads();  // s_pre is read: the next tile may fill it
+    __syncthreads();
+    if (staged) {
+      // dst + head is 16-byte aligned, and so is s_out + sh + head
+      const uint32_t head = min(nbytes, (16u - sh) & 15u);
+      const uint32_t chunks = (nbytes - head) >> 4;
+      const uint32_t tail0 = head + 16u * chunks;
+      for (uint32_t c = threadIdx.x; c < chunks; c += kExThreads)
+        *reinterpret_cast<uint4*>(dst + head + 16u * c) = *reinterpret_cast<const uint4*>(s_out + sh + head + 16u * c);
+      for (uint32_t k = threadIdx.x; k < head + (nbytes - tail0); k += kExThreads) {
+        const uint32_t o = k < head ? k : tail0 + (k - head);
+        dst[o] = s_out[sh + o];
+      }
+      __syncthreads();  // s_out and s_pre are read: the next tile may fill them
+    }
   }
 }
 
