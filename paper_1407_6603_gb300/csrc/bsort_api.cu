@@ -800,9 +800,9 @@ bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, 
 // The duplicate-aware sort's second half, once K4 has filled the hash tables
 // of the `ndd` buckets marked kSegDedupe (table positions in c->dd_pos): reads
 // how many distinct keys each bucket has, sorts every bucket's distinct-key
-// array (entries of key + count, kSegKeysOut: the same K4 / K5 kernels, all
-// on the call's stream), then expands the sorted arrays into the buckets'
-// words.  The counts' read-back is the call's second round trip.
+// array (entries of key + count, kSegKeysOut: the same K4 / K5 kernels, on
+// the side streams as the first sorts), then expands the sorted arrays into
+// the buckets' words.  The counts' read-back is the call's second round trip.
 bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* ins, uint32_t ndd,
                            const uint32_t* h_ucnt, const EmitOut& eo, cudaStream_t st) {
   cudaEvent_t gap_a = nullptr;
@@ -889,11 +889,18 @@ bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* i
   }
   const Segment* segs2_dev = dptr<Segment>(c->plan2);
   uint32_t* barrier2 = dptr<uint32_t>(c->plan2, seg_bytes);
-  std::vector<cudaStream_t> none;
+  // (the distinct-key sorts use the side streams too: the tile sorts of the
+  // size classes, and the merge chains of the key widths, overlap; they are
+  // joined back before the expansion)
+  std::vector<cudaStream_t> joined2;
   const DedupeOut no_dd{nullptr, nullptr, nullptr, nullptr, nullptr};
   bsort_status s = launch_sorts(c, p2, segs2, segs2_dev, dptr<uint64_t>(c->uA), dptr<uint64_t>(c->uB),
-                                dptr<uint64_t>(c->samples2), c->jobs2, barrier2, eo, no_dd, st, false, none, {});
+                                dptr<uint64_t>(c->samples2), c->jobs2, barrier2, eo, no_dd, st, true, joined2, {});
   if (s != BSORT_OK) return s;
+  for (size_t i = 0; i < joined2.size(); ++i) {
+    CK(cudaEventRecord(c->join_ev[i], joined2[i]), "join");
+    CK(cudaStreamWaitEvent(st, c->join_ev[i], 0), "join");
+  }
   const ExpandCaps caps{std::min(c->uA.cap, c->uB.cap) / 8, c->pre.cap / 4, c->stream.cap, c->offsets.cap / 4,
                         c->tfirst.cap / 4};
   LAUNCH(kExpand, moved,
