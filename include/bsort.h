@@ -345,19 +345,26 @@ bsort_status bsort_context_config(const bsort_ctx* ctx, bsort_config* out);
  * admitted as soon as a worker and enough budget are free.  bsort_poll()
  * hands out finished requests: their tags, their results (HOST pointers,
  * outs[i].status per request) and, when latency_ns is not NULL, the time from
- * submission to completion.  The results of one poll stay valid until the
- * next bsort_poll on the context, bsort_serve_stop + restart, or
- * bsort_destroy.  Each result equals what bsort_text returns for the document
- * alone.
+ * submission to completion.  Each result equals what bsort_text returns for
+ * the document alone.  Results are not copied: they point into the
+ * page-locked buffers their batch was read back into, which stay held until
+ * every result of that batch has been passed to bsort_result_release(ctx,
+ * &out) (the server then writes a later batch into them).  So each polled
+ * result stays valid until it is released, or until bsort_serve_start
+ * restarts the server or bsort_destroy; release every result once it has
+ * been used, or the server keeps allocating new buffers.
  *
- * Threads: bsort_submit and bsort_poll may run on two different threads (one
- * producer, one consumer); no other call on the context may run meanwhile.
+ * Threads: bsort_submit may run on several threads at once (producers),
+ * bsort_poll on one other thread (the consumer), and bsort_result_release of
+ * polled results on any threads, all at the same time; no other call on the
+ * context may run meanwhile.
  * bsort_serve_stop() finishes the queued requests and stops the workers;
- * finished results stay pollable.  bsort_destroy() stops a running server.
+ * finished results stay pollable (and, once polled, valid until released).
+ * bsort_destroy() stops a running server and frees every result.
  */
 typedef struct {
   uint64_t hbm_budget;      /* device bytes the in-flight requests may use (0 = 64 GiB) */
-  uint32_t workers;         /* batches in flight at once, 1..16 (0 = 2) */
+  uint32_t workers;         /* batches in flight at once, 1..16 (0 = 4) */
   uint32_t max_batch_docs;  /* requests per batch (0 = 1024) */
 } bsort_serve_config;
 

@@ -267,13 +267,26 @@ def bsort_submit(h, data, tag: int) -> int:
     return int(load().bsort_submit(h, a.ctypes.data if a.size else None, a.size, tag))
 
 
-def bsort_poll(h, max_results: int = 256, want_offsets: bool = True) -> list:
-    """Finished requests: [(tag, Result, latency_ns)], results copied out."""
+def bsort_poll(h, max_results: int = 256, want_offsets: bool = True, copy: bool = True) -> list:
+    """Finished requests: [(tag, result, latency_ns)].  copy=True: the results
+    are copied out and released at once.  copy=False: each result is a
+    ViewResult over the server's page-locked buffers, valid until it is passed
+    to bsort_result_release (Context.release), which must follow."""
     tags = (ctypes.c_uint64 * max_results)()
     outs = (bsort_result * max_results)()
     lat = (ctypes.c_uint64 * max_results)()
-    k = int(load().bsort_poll(h, tags, outs, lat, max_results))
-    return [(int(tags[i]), _host_result(outs[i], want_offsets), int(lat[i])) for i in range(k)]
+    lib = load()
+    k = int(lib.bsort_poll(h, tags, outs, lat, max_results))
+    got = []
+    for i in range(k):
+        r = bsort_result.from_buffer_copy(outs[i])
+        if copy:
+            res = _host_result(r, want_offsets)
+            lib.bsort_result_release(h, ctypes.byref(r))
+        else:
+            res = ViewResult(r, want_offsets)
+        got.append((int(tags[i]), res, int(lat[i])))
+    return got
 
 
 def bsort_serve_pending(h) -> int:
@@ -323,9 +336,10 @@ def _host_array(ptr, ctype, count, dtype, copy: bool) -> np.ndarray:
 
 
 class ViewResult:
-    """A host result whose arrays are views of the context's page-locked
-    buffers, made on first access; valid until the next call on the context
-    (the C ABI's own lifetime).  Same fields as Result."""
+    """A host result whose arrays are views of page-locked buffers, made on
+    first access: the context's (valid until the next call on the context) or,
+    from poll(copy=False), the server's (valid until Context.release).  Same
+    fields as Result."""
 
     __slots__ = ("_r", "_want_offsets", "max_len", "n_words", "stream_bytes", "status", "_cache")
 
@@ -539,8 +553,13 @@ class Context:
     def submit(self, data, tag: int) -> int:
         return bsort_submit(self._h, data, tag)
 
-    def poll(self, max_results: int = 256) -> list:
-        return bsort_poll(self._h, max_results, self.want_offsets)
+    def poll(self, max_results: int = 256, copy: bool = True) -> list:
+        return bsort_poll(self._h, max_results, self.want_offsets, copy)
+
+    def release(self, res) -> None:
+        """Ends a served result's hold on the server's buffers (a ViewResult
+        from poll(copy=False)); its arrays must not be used afterwards."""
+        bsort_result_release(self._h, res._r)
 
     def serve_pending(self) -> int:
         return bsort_serve_pending(self._h)

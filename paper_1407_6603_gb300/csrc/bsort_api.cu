@@ -1699,8 +1699,37 @@ bsort_status bsort_device_finish(bsort_ctx* c, void* stream) {
 }
 
 void bsort_result_release(bsort_ctx* c, bsort_result* res) {
-  (void)c;
-  if (res) std::memset(res, 0, sizeof(*res));
+  if (!res) return;
+  if (c) bsort_serve_release(c, res);  // a served result: its batch's buffers may be reused
+  std::memset(res, 0, sizeof(*res));
 }
 
 }  // extern "C"
+
+struct bsort_host_out {
+  HostBuf counts, offsets, stream;
+};
+
+bsort_host_out* bsort_take_result_buffers(bsort_ctx* c) {
+  bsort_host_out* b = new bsort_host_out{c->h_counts, c->h_offsets, c->h_stream};
+  c->h_counts = HostBuf{};
+  c->h_offsets = HostBuf{};
+  c->h_stream = HostBuf{};
+  return b;
+}
+
+void bsort_give_result_buffers(bsort_ctx* c, bsort_host_out* b) {
+  for (HostBuf* h : {&c->h_counts, &c->h_offsets, &c->h_stream})
+    if (h->p) cudaFreeHost(h->p);
+  c->h_counts = b->counts;
+  c->h_offsets = b->offsets;
+  c->h_stream = b->stream;
+  delete b;
+}
+
+void bsort_free_result_buffers(bsort_host_out* b) {
+  if (!b) return;
+  for (HostBuf* h : {&b->counts, &b->offsets, &b->stream})
+    if (h->p) cudaFreeHost(h->p);
+  delete b;
+}

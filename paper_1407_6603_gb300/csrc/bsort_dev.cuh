@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bsort.h"
+
 namespace bsort {
 
 constexpr int kHist = 256;                  // histogram bins: lengths 0..255
@@ -424,6 +426,16 @@ __device__ __forceinline__ uint32_t seg_find_warp(const Segment* segs, uint32_t 
 // Stops the serving loop of a context, if it runs one (bsort_serve.cu).
 struct bsort_ctx;
 void bsort_serve_shutdown(const struct bsort_ctx* ctx);
+// The serving loop's hand-over of result buffers (bsort_api.cu): a context's
+// page-locked result buffers (counts, offsets, stream) move out of it, with
+// the results of its last call in them, and a set of earlier buffers moves
+// back in for reuse; the context allocates new ones when it has none.
+struct bsort_host_out;
+struct bsort_host_out* bsort_take_result_buffers(struct bsort_ctx* ctx);
+void bsort_give_result_buffers(struct bsort_ctx* ctx, struct bsort_host_out* b);
+void bsort_free_result_buffers(struct bsort_host_out* b);
+// Ends the hold of a served result (bsort_serve.cu); false if it holds none.
+bool bsort_serve_release(const struct bsort_ctx* ctx, const bsort_result* res);
 namespace bsort {
 
 // Runs `set` (kernel attribute calls and the like) once per device for the

@@ -10,6 +10,12 @@
 // requests that arrive during a batch are admitted as soon as a worker and
 // enough of the budget are free, and the workers' batches overlap on the
 // device.  Every result is the one bsort_text gives for the document alone.
+//
+// Results are not copied: a batch's page-locked result buffers leave the
+// worker's context with the results in them (bsort_take_result_buffers) and
+// stay held until every result of the batch has been released
+// (bsort_result_release, from any thread); they then go back to the worker,
+// whose next batch writes into them.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -21,6 +27,7 @@
 #include <vector>
 
 #include "bsort.h"
+#include "bsort_dev.cuh"
 
 namespace {
 
@@ -38,13 +45,25 @@ struct Request {
   Clock::time_point submitted;
 };
 
+struct Worker;
+
+// A batch's result buffers and how many of its results still hold them.
+struct BatchHold {
+  bsort_host_out* bufs;
+  uint32_t refs;
+  Worker* owner;
+};
+
 struct Done {
   uint64_t tag;
-  bsort_result res;  // pointers into the vectors below
-  std::vector<uint64_t> counts;
-  std::vector<uint32_t> offsets;
-  std::vector<uint8_t> stream;
+  bsort_result res;  // pointers into its batch's buffers (none for a failed document)
+  BatchHold* hold;   // null when res points nowhere
   uint64_t latency_ns;
+};
+
+struct Worker {
+  bsort_ctx* ctx = nullptr;
+  std::vector<bsort_host_out*> free_bufs;  // released result buffers, for the next batch
 };
 
 struct Server {
@@ -52,12 +71,12 @@ struct Server {
   std::condition_variable cv_work, cv_space;
   std::deque<Request> queue;
   std::deque<Done> done;
-  std::vector<Done> polled;  // results handed out by the last poll, kept until the next one
+  std::unordered_map<const void*, BatchHold*> handed;  // polled results not yet released, by counts pointer
   uint64_t budget = 0, in_flight = 0;
   uint32_t max_docs = 0;
   bool stop = false;
   bool want_offsets = true;
-  std::vector<bsort_ctx*> ctxs;
+  std::vector<Worker*> workers;
   std::vector<std::thread> threads;
 };
 
@@ -70,23 +89,37 @@ Server* server_of(const bsort_ctx* c) {
   return it == g_servers.end() ? nullptr : it->second;
 }
 
-void copy_result(const bsort_result& r, Done& d, bool want_offsets) {
-  d.res = r;
-  if (r.status != BSORT_OK || !r.counts) {
-    d.res.counts = nullptr;
-    d.res.offsets = nullptr;
-    d.res.stream = nullptr;
-    return;
+// Ends one result's hold on its batch's buffers (under s->mu); the last one
+// gives them back to the worker that filled them, or frees them once the
+// workers are gone.
+void unhold(Server* s, BatchHold* h) {
+  if (--h->refs == 0) {
+    if (s->stop)
+      bsort_free_result_buffers(h->bufs);
+    else
+      h->owner->free_bufs.push_back(h->bufs);
+    delete h;
   }
-  d.counts.assign(r.counts, r.counts + r.max_len + 1);
-  if (want_offsets && r.offsets) d.offsets.assign(r.offsets, r.offsets + r.n_words + 1);
-  d.stream.assign(r.stream, r.stream + r.stream_bytes);
-  d.res.counts = d.counts.data();
-  d.res.offsets = d.offsets.empty() ? nullptr : d.offsets.data();
-  d.res.stream = d.stream.data();
 }
 
-void worker_loop(Server* s, bsort_ctx* ctx) {
+// Frees every result not yet released, polled or not (the server is stopped).
+void free_results(Server* s) {
+  std::vector<BatchHold*> holds;
+  for (Done& d : s->done)
+    if (d.hold) holds.push_back(d.hold);
+  for (auto& kv : s->handed) holds.push_back(kv.second);
+  std::sort(holds.begin(), holds.end());
+  holds.erase(std::unique(holds.begin(), holds.end()), holds.end());
+  for (BatchHold* h : holds) {
+    bsort_free_result_buffers(h->bufs);
+    delete h;
+  }
+  s->done.clear();
+  s->handed.clear();
+}
+
+void worker_loop(Server* s, Worker* wk) {
+  bsort_ctx* ctx = wk->ctx;
   std::vector<Request> batch;
   std::vector<const uint8_t*> ptrs;
   std::vector<size_t> lens;
@@ -125,25 +158,50 @@ void worker_loop(Server* s, bsort_ctx* ctx) {
       ptrs[i] = batch[i].bytes.data();
       lens[i] = batch[i].bytes.size();
     }
+    {  // result buffers released since the last batch, if any, to write into
+      bsort_host_out* reuse = nullptr;
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (!wk->free_bufs.empty()) {
+          reuse = wk->free_bufs.back();
+          wk->free_bufs.pop_back();
+        }
+      }
+      if (reuse) bsort_give_result_buffers(ctx, reuse);
+    }
     const bsort_status st = bsort_batch(ctx, ptrs.data(), lens.data(), batch.size(), outs.data());
+    BatchHold* hold = new BatchHold{bsort_take_result_buffers(ctx), 0, wk};
     std::vector<Done> finished(batch.size());
     const Clock::time_point now = Clock::now();
     for (size_t i = 0; i < batch.size(); ++i) {
       Done& d = finished[i];
       d.tag = batch[i].tag;
+      d.hold = nullptr;
       if (st != BSORT_OK && outs[i].status == BSORT_OK && outs[i].counts == nullptr) {
         // the whole call failed (not one document): report the call's status
         // (every document that succeeded, empty ones included, has counts)
         std::memset(&d.res, 0, sizeof(d.res));
         d.res.status = st;
       } else {
-        copy_result(outs[i], d, s->want_offsets);
+        d.res = outs[i];
+        if (d.res.status != BSORT_OK || !d.res.counts) {
+          d.res.counts = nullptr;
+          d.res.offsets = nullptr;
+          d.res.stream = nullptr;
+        } else {
+          d.hold = hold;
+          ++hold->refs;
+        }
       }
       d.latency_ns = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(now - batch[i].submitted).count();
     }
     {
       std::lock_guard<std::mutex> lk(s->mu);
       s->in_flight -= foot;
+      if (hold->refs == 0) {  // no result points into the buffers
+        wk->free_bufs.push_back(hold->bufs);
+        delete hold;
+      }
       for (Done& d : finished) s->done.push_back(std::move(d));
     }
     s->cv_space.notify_all();
@@ -159,8 +217,15 @@ void stop_server(Server* s) {
   s->cv_space.notify_all();
   for (std::thread& t : s->threads) t.join();
   s->threads.clear();
-  for (bsort_ctx* c : s->ctxs) bsort_destroy(c);
-  s->ctxs.clear();
+  // the finished results stay (their buffers are their own) until released
+  // or until the server is dropped
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (Worker* w : s->workers) {
+    for (bsort_host_out* b : w->free_bufs) bsort_free_result_buffers(b);
+    bsort_destroy(w->ctx);
+    delete w;
+  }
+  s->workers.clear();
 }
 
 }  // namespace
@@ -176,6 +241,10 @@ void bsort_serve_shutdown(const bsort_ctx* ctx) {
     g_servers.erase(it);
   }
   stop_server(s);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    free_results(s);
+  }
   delete s;
 }
 
@@ -184,7 +253,7 @@ extern "C" {
 void bsort_serve_config_default(bsort_serve_config* cfg) {
   if (!cfg) return;
   cfg->hbm_budget = 64ull << 30;
-  cfg->workers = 2;
+  cfg->workers = 4;
   cfg->max_batch_docs = 1024;
 }
 
@@ -194,7 +263,7 @@ bsort_status bsort_serve_start(bsort_ctx* ctx, const bsort_serve_config* cfg) {
   bsort_serve_config_default(&conf);
   if (cfg) conf = *cfg;
   if (conf.hbm_budget == 0) conf.hbm_budget = 64ull << 30;
-  if (conf.workers == 0) conf.workers = 2;
+  if (conf.workers == 0) conf.workers = 4;
   if (conf.max_batch_docs == 0) conf.max_batch_docs = 1024;
   if (conf.workers > 16) return BSORT_E_INVAL;
   if (Server* old = server_of(ctx)) {
@@ -216,13 +285,18 @@ bsort_status bsort_serve_start(bsort_ctx* ctx, const bsort_serve_config* cfg) {
     bsort_ctx* w = nullptr;
     const bsort_status st = bsort_create(&w, &wc);
     if (st != BSORT_OK) {
-      for (bsort_ctx* c : s->ctxs) bsort_destroy(c);
+      for (Worker* x : s->workers) {
+        bsort_destroy(x->ctx);
+        delete x;
+      }
       delete s;
       return st;
     }
-    s->ctxs.push_back(w);
+    Worker* x = new Worker();
+    x->ctx = w;
+    s->workers.push_back(x);
   }
-  for (bsort_ctx* w : s->ctxs) s->threads.emplace_back(worker_loop, s, w);
+  for (Worker* w : s->workers) s->threads.emplace_back(worker_loop, s, w);
   std::lock_guard<std::mutex> lk(g_servers_mu);
   g_servers[ctx] = s;
   return BSORT_OK;
@@ -251,18 +325,15 @@ size_t bsort_poll(bsort_ctx* ctx, uint64_t* tags, bsort_result* outs, uint64_t* 
   Server* s = server_of(ctx);
   if (!s || !tags || !outs) return 0;
   std::lock_guard<std::mutex> lk(s->mu);
-  s->polled.clear();  // results of the previous poll are released here
   size_t k = 0;
   while (k < max && !s->done.empty()) {
-    s->polled.push_back(std::move(s->done.front()));
+    Done& d = s->done.front();
+    tags[k] = d.tag;
+    outs[k] = d.res;
+    if (latency_ns) latency_ns[k] = d.latency_ns;
+    if (d.hold) s->handed[d.res.counts] = d.hold;  // held until bsort_result_release
     s->done.pop_front();
     ++k;
-  }
-  for (size_t i = 0; i < k; ++i) {
-    Done& d = s->polled[i];
-    tags[i] = d.tag;
-    outs[i] = d.res;
-    if (latency_ns) latency_ns[i] = d.latency_ns;
   }
   return k;
 }
@@ -294,3 +365,16 @@ bsort_status bsort_serve_stop(bsort_ctx* ctx) {
 }
 
 }  // extern "C"
+
+bool bsort_serve_release(const bsort_ctx* ctx, const bsort_result* res) {
+  if (!res || !res->counts) return false;
+  Server* s = server_of(ctx);
+  if (!s) return false;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->handed.find(res->counts);
+  if (it == s->handed.end()) return false;
+  BatchHold* h = it->second;
+  s->handed.erase(it);
+  unhold(s, h);
+  return true;
+}

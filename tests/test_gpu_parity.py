@@ -372,6 +372,58 @@ def test_serving_results_equal_alone(bsort_gpu, oracle_mod, synth_mod):
         assert lat[i] > 0
 
 
+def test_serving_views_held_until_released(bsort_gpu, oracle_mod, synth_mod):
+    """Results polled as views of the server's buffers (no copy) stay intact
+    across later polls and batches until released, also when released out of
+    order from other threads; released buffers go back to the workers, whose
+    later batches write into them; results still held survive serve_stop."""
+    import threading
+    import time
+
+    docs = [synth_mod.batch_doc(*s) for s in synth_mod.batch_shapes(48)]
+    with bsort_gpu.Context() as c:
+        c.serve_start(hbm_budget=1 << 30, workers=2, max_batch_docs=4)
+        for i, d in enumerate(docs):
+            assert c.submit(d, i) == 0
+        held = {}
+        deadline = time.time() + 120
+        while len(held) < len(docs) and time.time() < deadline:
+            for tag, res, _ in c.poll(5, copy=False):
+                held[tag] = res
+            time.sleep(0.001)
+        assert sorted(held) == list(range(len(docs)))
+        # every view still matches after all the polls; release half of them
+        # from two threads, in scrambled order
+        for i, d in enumerate(docs):
+            assert_same(held[i], oracle_mod.stable(d, nthreads=8), f"held request {i}")
+        first = [t for t in range(len(docs)) if t % 2 == 0]
+        random.Random(5).shuffle(first)
+        ths = [threading.Thread(target=lambda ts: [c.release(held.pop(t)) for t in ts], args=(first[k::2],))
+               for k in range(2)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        # more batches now reuse the released buffers; the views still held
+        # must not change
+        for i, d in enumerate(docs):
+            assert c.submit(d, 1000 + i) == 0
+        again = {}
+        deadline = time.time() + 120
+        while len(again) < len(docs) and time.time() < deadline:
+            for tag, res, _ in c.poll(8):  # copied out and released at once
+                again[tag] = res
+            time.sleep(0.001)
+        c.serve_stop()
+        for i, d in enumerate(docs):
+            exp = oracle_mod.stable(d, nthreads=8)
+            assert_same(again[1000 + i], exp, f"second round {i}")
+            if i in held:
+                assert_same(held[i], exp, f"still held {i}")
+        for t in list(held):
+            c.release(held.pop(t))
+
+
 def test_serving_rejects_over_budget(bsort_gpu):
     with bsort_gpu.Context() as c:
         c.serve_start(hbm_budget=1 << 20, workers=1)
