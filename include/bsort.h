@@ -364,7 +364,7 @@ bsort_status bsort_context_config(const bsort_ctx* ctx, bsort_config* out);
  */
 typedef struct {
   uint64_t hbm_budget;      /* device bytes the in-flight requests may use (0 = 64 GiB) */
-  uint32_t workers;         /* batches in flight at once, 1..16 (0 = 4) */
+  uint32_t workers;         /* batches in flight at once, 1..16 (0 = 2) */
   uint32_t max_batch_docs;  /* requests per batch (0 = 1024) */
 } bsort_serve_config;
 
@@ -376,6 +376,13 @@ bsort_status bsort_serve_start(bsort_ctx* ctx, const bsort_serve_config* cfg);
 /* Errors: BSORT_E_INVAL (not serving, NULL bytes), BSORT_E_TOO_LARGE (1 GiB or more,
  * or more than the whole budget), BSORT_E_BUSY (stopping). */
 bsort_status bsort_submit(bsort_ctx* ctx, const uint8_t* bytes, size_t len, uint64_t tag);
+
+/* bsort_submit without the copy: the server reads the caller's bytes, which
+ * must stay valid and unchanged until the request's result has been polled.
+ * Page-locked bytes are read by the copy engine in place (no host copy at
+ * all); pageable ones are copied by the worker that takes the request.
+ * Errors as bsort_submit. */
+bsort_status bsort_submit_borrowed(bsort_ctx* ctx, const uint8_t* bytes, size_t len, uint64_t tag);
 
 /* Writes up to max finished requests; returns how many. */
 size_t bsort_poll(bsort_ctx* ctx, uint64_t* tags, bsort_result* outs, uint64_t* latency_ns, size_t max);

@@ -13,6 +13,7 @@ takes a CUDA tensor and the current torch stream).
 from __future__ import annotations
 
 import ctypes
+import threading
 import os
 from dataclasses import dataclass
 
@@ -125,6 +126,8 @@ def load(path: str | None = None):
     lib.bsort_serve_start.argtypes = [ctx_p, ctypes.POINTER(bsort_serve_config)]
     lib.bsort_submit.restype = ctypes.c_int
     lib.bsort_submit.argtypes = [ctx_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64]
+    lib.bsort_submit_borrowed.restype = ctypes.c_int
+    lib.bsort_submit_borrowed.argtypes = [ctx_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint64]
     lib.bsort_poll.restype = ctypes.c_size_t
     lib.bsort_poll.argtypes = [ctx_p, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(bsort_result),
                                ctypes.POINTER(ctypes.c_uint64), ctypes.c_size_t]
@@ -265,6 +268,13 @@ def bsort_serve_start(h, hbm_budget: int = 0, workers: int = 0, max_batch_docs: 
 def bsort_submit(h, data, tag: int) -> int:
     a = _as_u8(data)
     return int(load().bsort_submit(h, a.ctypes.data if a.size else None, a.size, tag))
+
+
+def bsort_submit_borrowed(h, data, tag: int) -> int:
+    """data (a uint8 array) must stay alive and unchanged until the request's
+    result is polled (Context.submit(borrow=True) keeps the reference)."""
+    a = _as_u8(data)
+    return int(load().bsort_submit_borrowed(h, a.ctypes.data if a.size else None, a.size, tag))
 
 
 def bsort_poll(h, max_results: int = 256, want_offsets: bool = True, copy: bool = True) -> list:
@@ -441,12 +451,15 @@ class Context:
         self._tune = tune_table.encode() if tune_table is not None else None
         cfg.tune_table = self._tune
         self.want_offsets = want_offsets
+        self._borrowed = {}  # tag -> array of a borrowed request not yet polled
+        self._borrow_lock = threading.Lock()
         self._h = bsort_create(cfg)
 
     def close(self) -> None:
         if getattr(self, "_h", None):
             bsort_destroy(self._h)
             self._h = None
+        self._borrowed = {}
 
     def __del__(self):
         self.close()
@@ -550,11 +563,28 @@ class Context:
     def serve_start(self, hbm_budget: int = 0, workers: int = 0, max_batch_docs: int = 0) -> None:
         bsort_serve_start(self._h, hbm_budget, workers, max_batch_docs)
 
-    def submit(self, data, tag: int) -> int:
-        return bsort_submit(self._h, data, tag)
+    def submit(self, data, tag: int, borrow: bool = False) -> int:
+        """Queues a document.  borrow=True: no copy; the array (page-locked
+        ones are read in place by the copy engine) is kept referenced here
+        until its tag's result is polled."""
+        if not borrow:
+            return bsort_submit(self._h, data, tag)
+        a = _as_u8(data)
+        with self._borrow_lock:
+            self._borrowed[tag] = a
+        st = bsort_submit_borrowed(self._h, a, tag)
+        if st != BSORT_OK:
+            with self._borrow_lock:
+                self._borrowed.pop(tag, None)
+        return st
 
     def poll(self, max_results: int = 256, copy: bool = True) -> list:
-        return bsort_poll(self._h, max_results, self.want_offsets, copy)
+        got = bsort_poll(self._h, max_results, self.want_offsets, copy)
+        if self._borrowed:
+            with self._borrow_lock:
+                for tag, _, _ in got:
+                    self._borrowed.pop(tag, None)
+        return got
 
     def release(self, res) -> None:
         """Ends a served result's hold on the server's buffers (a ViewResult

@@ -1536,16 +1536,29 @@ bsort_status bsort_batch(bsort_ctx* c, const uint8_t* const* docs, const size_t*
         CK(cudaMemcpyAsync(c->in.p, c->h_in.p, rb, cudaMemcpyHostToDevice, st), "copy input");
       }
     } else {
-      GROW_HOST(c->h_in, bytes + 16, "input staging");
       GROW(c->in, bytes + 16, "input");
+      bool all_pinned = true;
+      for (size_t i = g0; i < g1 && all_pinned; ++i) all_pinned = !lens[i] || host_pinned(docs[i], lens[i]);
       uint64_t pos = 0;
-      for (uint32_t i = 0; i < nd; ++i) {
-        offs[i] = pos;
-        ls[i] = lens[g0 + i];
-        if (ls[i]) std::memcpy(hptr<uint8_t>(c->h_in, pos), docs[g0 + i], ls[i]);
-        pos += align_up(ls[i], 16);
+      if (all_pinned) {  // every document page-locked: the copy engine reads each in place
+        for (uint32_t i = 0; i < nd; ++i) {
+          offs[i] = pos;
+          ls[i] = lens[g0 + i];
+          if (ls[i])
+            CK(cudaMemcpyAsync(dptr<uint8_t>(c->in, pos), docs[g0 + i], ls[i], cudaMemcpyHostToDevice, st),
+               "copy input");
+          pos += align_up(ls[i], 16);
+        }
+      } else {  // gathered into the staging buffer, then one copy
+        GROW_HOST(c->h_in, bytes + 16, "input staging");
+        for (uint32_t i = 0; i < nd; ++i) {
+          offs[i] = pos;
+          ls[i] = lens[g0 + i];
+          if (ls[i]) std::memcpy(hptr<uint8_t>(c->h_in, pos), docs[g0 + i], ls[i]);
+          pos += align_up(ls[i], 16);
+        }
+        if (bytes) CK(cudaMemcpyAsync(c->in.p, c->h_in.p, bytes, cudaMemcpyHostToDevice, st), "copy input");
       }
-      if (bytes) CK(cudaMemcpyAsync(c->in.p, c->h_in.p, bytes, cudaMemcpyHostToDevice, st), "copy input");
     }
     s = run_path(c, dptr<uint8_t>(c->in), offs.data(), ls.data(), nd, st);
     if (s != BSORT_OK) return s;
@@ -1725,6 +1738,13 @@ void bsort_give_result_buffers(bsort_ctx* c, bsort_host_out* b) {
   c->h_offsets = b->offsets;
   c->h_stream = b->stream;
   delete b;
+}
+
+bsort_status bsort_reserve_result_buffers(bsort_ctx* c, uint64_t bytes, uint64_t ndocs) {
+  GROW_HOST(c->h_counts, 8ull * kHist * std::max<uint64_t>(ndocs, 1), "counts");
+  GROW_HOST(c->h_offsets, 4ull * (bytes / 2 + 2 * ndocs + 1), "offsets");
+  GROW_HOST(c->h_stream, bytes + 16, "stream");
+  return BSORT_OK;
 }
 
 void bsort_free_result_buffers(bsort_host_out* b) {

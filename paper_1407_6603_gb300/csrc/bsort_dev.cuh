@@ -434,6 +434,11 @@ struct bsort_host_out;
 struct bsort_host_out* bsort_take_result_buffers(struct bsort_ctx* ctx);
 void bsort_give_result_buffers(struct bsort_ctx* ctx, struct bsort_host_out* b);
 void bsort_free_result_buffers(struct bsort_host_out* b);
+// Grows the context's result buffers to what a bsort_batch of `ndocs`
+// documents of `bytes` bytes in all can need (at most: every byte a letter,
+// every second one a word), so that the call reallocates none of them:
+// freeing page-locked memory waits for the whole device.
+bsort_status bsort_reserve_result_buffers(struct bsort_ctx* ctx, uint64_t bytes, uint64_t ndocs);
 // Ends the hold of a served result (bsort_serve.cu); false if it holds none.
 bool bsort_serve_release(const struct bsort_ctx* ctx, const bsort_result* res);
 namespace bsort {

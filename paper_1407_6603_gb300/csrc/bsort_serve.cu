@@ -40,7 +40,9 @@ uint64_t footprint(uint64_t len) { return 16 * len + (64u << 10); }
 
 struct Request {
   uint64_t tag;
-  std::vector<uint8_t> bytes;
+  std::vector<uint8_t> bytes;   // the document's copy (bsort_submit)
+  const uint8_t* ptr = nullptr;  // or the caller's own bytes (bsort_submit_borrowed)
+  size_t len = 0;
   uint64_t foot;
   Clock::time_point submitted;
 };
@@ -155,8 +157,8 @@ void worker_loop(Server* s, Worker* wk) {
     lens.resize(batch.size());
     outs.assign(batch.size(), bsort_result{});
     for (size_t i = 0; i < batch.size(); ++i) {
-      ptrs[i] = batch[i].bytes.data();
-      lens[i] = batch[i].bytes.size();
+      ptrs[i] = batch[i].ptr ? batch[i].ptr : batch[i].bytes.data();
+      lens[i] = batch[i].ptr ? batch[i].len : batch[i].bytes.size();
     }
     {  // result buffers released since the last batch, if any, to write into
       bsort_host_out* reuse = nullptr;
@@ -168,6 +170,11 @@ void worker_loop(Server* s, Worker* wk) {
         }
       }
       if (reuse) bsort_give_result_buffers(ctx, reuse);
+      // sized for the whole batch now, so that the call grows none of them
+      // (a regrowth frees page-locked memory, which waits for the device)
+      uint64_t bytes = 0;
+      for (size_t i = 0; i < batch.size(); ++i) bytes += lens[i];
+      bsort_reserve_result_buffers(ctx, bytes, batch.size());  // (a failure surfaces in the call)
     }
     const bsort_status st = bsort_batch(ctx, ptrs.data(), lens.data(), batch.size(), outs.data());
     BatchHold* hold = new BatchHold{bsort_take_result_buffers(ctx), 0, wk};
@@ -253,7 +260,7 @@ extern "C" {
 void bsort_serve_config_default(bsort_serve_config* cfg) {
   if (!cfg) return;
   cfg->hbm_budget = 64ull << 30;
-  cfg->workers = 4;
+  cfg->workers = 2;
   cfg->max_batch_docs = 1024;
 }
 
@@ -263,7 +270,7 @@ bsort_status bsort_serve_start(bsort_ctx* ctx, const bsort_serve_config* cfg) {
   bsort_serve_config_default(&conf);
   if (cfg) conf = *cfg;
   if (conf.hbm_budget == 0) conf.hbm_budget = 64ull << 30;
-  if (conf.workers == 0) conf.workers = 4;
+  if (conf.workers == 0) conf.workers = 2;
   if (conf.max_batch_docs == 0) conf.max_batch_docs = 1024;
   if (conf.workers > 16) return BSORT_E_INVAL;
   if (Server* old = server_of(ctx)) {
@@ -302,13 +309,18 @@ bsort_status bsort_serve_start(bsort_ctx* ctx, const bsort_serve_config* cfg) {
   return BSORT_OK;
 }
 
-bsort_status bsort_submit(bsort_ctx* ctx, const uint8_t* bytes, size_t len, uint64_t tag) {
+static bsort_status submit_request(bsort_ctx* ctx, const uint8_t* bytes, size_t len, uint64_t tag, bool borrow) {
   Server* s = server_of(ctx);
   if (!s || (!bytes && len)) return BSORT_E_INVAL;
   if ((uint64_t)len >= (1ull << 30)) return BSORT_E_TOO_LARGE;
   Request r;
   r.tag = tag;
-  r.bytes.assign(bytes, bytes + len);
+  if (borrow) {
+    r.ptr = len ? bytes : nullptr;
+    r.len = len;
+  } else {
+    r.bytes.assign(bytes, bytes + len);
+  }
   r.foot = footprint(len);
   if (r.foot > s->budget) return BSORT_E_TOO_LARGE;
   r.submitted = Clock::now();
@@ -319,6 +331,14 @@ bsort_status bsort_submit(bsort_ctx* ctx, const uint8_t* bytes, size_t len, uint
   }
   s->cv_work.notify_one();
   return BSORT_OK;
+}
+
+bsort_status bsort_submit(bsort_ctx* ctx, const uint8_t* bytes, size_t len, uint64_t tag) {
+  return submit_request(ctx, bytes, len, tag, false);
+}
+
+bsort_status bsort_submit_borrowed(bsort_ctx* ctx, const uint8_t* bytes, size_t len, uint64_t tag) {
+  return submit_request(ctx, bytes, len, tag, true);
 }
 
 size_t bsort_poll(bsort_ctx* ctx, uint64_t* tags, bsort_result* outs, uint64_t* latency_ns, size_t max) {

@@ -424,6 +424,43 @@ def test_serving_views_held_until_released(bsort_gpu, oracle_mod, synth_mod):
             c.release(held.pop(t))
 
 
+def test_serving_borrowed_inputs(bsort_gpu, oracle_mod, synth_mod):
+    """Requests submitted without a copy: page-locked documents (read in place
+    by the copy engine, back to back or scattered by the submission order) and
+    pageable ones, mixed with copied submissions; every result equals the
+    oracle's, and the context drops its references once the results are
+    polled."""
+    import time
+
+    docs = [synth_mod.batch_doc(*s) for s in synth_mod.batch_shapes(36)]
+    docs[5] = np.zeros(0, np.uint8)
+    pinned = bsort_gpu.pack_host(docs)
+    order = list(range(len(docs)))
+    random.Random(9).shuffle(order)
+    with bsort_gpu.Context() as c:
+        c.serve_start(hbm_budget=1 << 30, workers=2, max_batch_docs=6)
+        for k, i in enumerate(order):
+            mode = k % 3
+            if mode == 0:
+                assert c.submit(pinned[i], i, borrow=True) == 0
+            elif mode == 1:
+                assert c.submit(np.array(docs[i]), i, borrow=True) == 0
+            else:
+                assert c.submit(docs[i], i) == 0
+        got = {}
+        deadline = time.time() + 120
+        while len(got) < len(docs) and time.time() < deadline:
+            for tag, res, _ in c.poll(7):
+                got[tag] = res
+            time.sleep(0.001)
+        c.serve_stop()
+        assert not c._borrowed
+    assert sorted(got) == list(range(len(docs)))
+    for i, d in enumerate(docs):
+        assert got[i].status == 0
+        assert_same(got[i], oracle_mod.stable(d, nthreads=8), f"request {i}")
+
+
 def test_serving_rejects_over_budget(bsort_gpu):
     with bsort_gpu.Context() as c:
         c.serve_start(hbm_budget=1 << 20, workers=1)
