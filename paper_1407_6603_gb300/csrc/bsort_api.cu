@@ -1740,11 +1740,21 @@ void bsort_give_result_buffers(bsort_ctx* c, bsort_host_out* b) {
   delete b;
 }
 
+// (the result buffers a batch of ndocs documents of `bytes` bytes can need)
+static uint64_t need_counts(uint64_t ndocs) { return 8ull * kHist * std::max<uint64_t>(ndocs, 1); }
+static uint64_t need_offsets(uint64_t bytes, uint64_t ndocs) { return 4ull * (bytes / 2 + 2 * ndocs + 1); }
+static uint64_t need_stream(uint64_t bytes) { return bytes + 16; }
+
 bsort_status bsort_reserve_result_buffers(bsort_ctx* c, uint64_t bytes, uint64_t ndocs) {
-  GROW_HOST(c->h_counts, 8ull * kHist * std::max<uint64_t>(ndocs, 1), "counts");
-  GROW_HOST(c->h_offsets, 4ull * (bytes / 2 + 2 * ndocs + 1), "offsets");
-  GROW_HOST(c->h_stream, bytes + 16, "stream");
+  GROW_HOST(c->h_counts, need_counts(ndocs), "counts");
+  GROW_HOST(c->h_offsets, need_offsets(bytes, ndocs), "offsets");
+  GROW_HOST(c->h_stream, need_stream(bytes), "stream");
   return BSORT_OK;
+}
+
+bool bsort_result_buffers_fit(const bsort_host_out* b, uint64_t bytes, uint64_t ndocs) {
+  return b->counts.cap >= need_counts(ndocs) && b->offsets.cap >= need_offsets(bytes, ndocs) &&
+         b->stream.cap >= need_stream(bytes);
 }
 
 void bsort_free_result_buffers(bsort_host_out* b) {

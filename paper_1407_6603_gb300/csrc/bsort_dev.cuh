@@ -439,6 +439,8 @@ void bsort_free_result_buffers(struct bsort_host_out* b);
 // every second one a word), so that the call reallocates none of them:
 // freeing page-locked memory waits for the whole device.
 bsort_status bsort_reserve_result_buffers(struct bsort_ctx* ctx, uint64_t bytes, uint64_t ndocs);
+// Whether a set of result buffers is already large enough for such a batch.
+bool bsort_result_buffers_fit(const struct bsort_host_out* b, uint64_t bytes, uint64_t ndocs);
 // Ends the hold of a served result (bsort_serve.cu); false if it holds none.
 bool bsort_serve_release(const struct bsort_ctx* ctx, const bsort_result* res);
 namespace bsort {

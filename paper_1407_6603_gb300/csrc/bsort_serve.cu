@@ -160,20 +160,25 @@ void worker_loop(Server* s, Worker* wk) {
       ptrs[i] = batch[i].ptr ? batch[i].ptr : batch[i].bytes.data();
       lens[i] = batch[i].ptr ? batch[i].len : batch[i].bytes.size();
     }
-    {  // result buffers released since the last batch, if any, to write into
+    {
+      // result buffers to write into: a set released since an earlier batch
+      // that is large enough for this one, else new ones (sized for the
+      // whole batch before the call, so that the call grows none of them).
+      // A set is never regrown or freed while serving: freeing page-locked
+      // memory waits for the whole device, which would stall every worker.
+      uint64_t bytes = 0;
+      for (size_t i = 0; i < batch.size(); ++i) bytes += lens[i];
       bsort_host_out* reuse = nullptr;
       {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (!wk->free_bufs.empty()) {
-          reuse = wk->free_bufs.back();
-          wk->free_bufs.pop_back();
-        }
+        for (size_t i = wk->free_bufs.size(); i-- > 0;)
+          if (bsort_result_buffers_fit(wk->free_bufs[i], bytes, batch.size())) {
+            reuse = wk->free_bufs[i];
+            wk->free_bufs.erase(wk->free_bufs.begin() + (long)i);
+            break;
+          }
       }
       if (reuse) bsort_give_result_buffers(ctx, reuse);
-      // sized for the whole batch now, so that the call grows none of them
-      // (a regrowth frees page-locked memory, which waits for the device)
-      uint64_t bytes = 0;
-      for (size_t i = 0; i < batch.size(); ++i) bytes += lens[i];
       bsort_reserve_result_buffers(ctx, bytes, batch.size());  // (a failure surfaces in the call)
     }
     const bsort_status st = bsort_batch(ctx, ptrs.data(), lens.data(), batch.size(), outs.data());
