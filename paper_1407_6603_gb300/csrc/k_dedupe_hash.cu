@@ -88,25 +88,43 @@ __device__ void hash_unit(const uint64_t* __restrict__ g, uint32_t cnt, const Se
   const uint32_t di = seg_dedupe_index(sg);
   const DedupeIns d = o.ins[di];
   if constexpr (W == 1) {
-    // four slots a round per thread: the first probes' loads of the global
-    // table are issued together, then each insert goes on from its own
+    // Each warp first packs the occupied slots of its eighth of the table to
+    // the front of that eighth (in place: a packed position never passes the
+    // slot it comes from, and the warp reads each round of 32 slots before
+    // it writes), then its lanes take the packed distinct keys four at a
+    // time: the first probes' loads of the global table are issued together,
+    // then each insert goes on from its own.  (Taking the slots as they lie,
+    // about half of each round's four would be empty.)
+    const uint32_t lane = t & 31u;
+    const uint32_t per = slots / (kHaThreads / 32);
+    uint32_t* list = s_tab + (t >> 5) * per;
+    uint32_t n = 0;
+    for (uint32_t b = 0; b < per; b += 32) {
+      const uint32_t v = list[b + lane];
+      const bool occ = v != kHaEmpty;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, occ);
+      if (occ) list[n + (uint32_t)__popc(m & ((1u << lane) - 1u))] = v;
+      n += (uint32_t)__popc(m);
+    }
+    __syncwarp();
     const uint64_t* gtab = o.htab + d.htab_off;
-    for (uint32_t h0 = t; h0 < slots; h0 += 4 * kHaThreads) {
-      uint64_t k[4], gi[4], seen[4], seen_u[4];
-      uint32_t c[4];
+    for (uint32_t q0 = 0; q0 * 32 < n; q0 += 4) {
+      uint64_t seen[4], seen_u[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const uint32_t h = h0 + j * kHaThreads;
-        const uint32_t v = h < slots ? s_tab[h] : kHaEmpty;
-        c[j] = v == kHaEmpty ? 0u : (v & 0xFFFFu);  // an occupied slot counts at least one copy
-        k[j] = c[j] ? s_keys[v >> 16] : 0ull;
-        gi[j] = c[j] ? first_slot1(k[j], d) : 0ull;
+        const uint32_t i = (q0 + j) * 32 + lane;
         seen[j] = seen_u[j] = 0ull;
-        if (c[j]) ld_relaxed_pair(gtab + 2 * gi[j], seen[j], seen_u[j]);
+        if (i < n) ld_relaxed_pair(gtab + 2 * first_slot1(s_keys[list[i] >> 16], d), seen[j], seen_u[j]);
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (c[j]) insert1_from(k[j], c[j], gi[j], seen[j], seen_u[j], d, di, o, meta, wait_limit);
+      for (int j = 0; j < 4; ++j) {
+        const uint32_t i = (q0 + j) * 32 + lane;
+        if (i < n) {
+          const uint32_t v = list[i];
+          const uint64_t k = s_keys[v >> 16];
+          insert1_from(k, v & 0xFFFFu, first_slot1(k, d), seen[j], seen_u[j], d, di, o, meta, wait_limit);
+        }
+      }
     }
   } else {
     for (uint32_t h = t; h < slots; h += kHaThreads) {

@@ -526,13 +526,17 @@ def test_batch_4096_full(bsort_gpu, oracle_mod, synth_mod):
     assert bad == [], f"documents differing from the oracle: {bad[:20]}"
 
 
-@pytest.mark.parametrize("case", ["one_word", "two_words", "hot_and_cold", "all_distinct_wide"])
+@pytest.mark.parametrize("case", ["one_word", "two_words", "hot_and_cold", "all_distinct_wide", "hot_and_cold_wide"])
 def test_duplicate_aware_extremes(ctx, oracle_mod, case):
     """Large buckets at the extremes of repetition: one word repeated 3M
     times (one distinct key whose count spans every tile), two words, a few
-    hot words among many cold ones, and distinct words of 33..64 letters
-    (keys of 8 words, whose distinct-key entries take the 16-word sort)."""
-    rng = np.random.default_rng({"one_word": 1, "two_words": 2, "hot_and_cold": 3, "all_distinct_wide": 4}[case])
+    hot words among many cold ones, distinct words of 33..64 letters (keys of
+    8 words, whose distinct-key entries take the 16-word sort), and hot and
+    cold words of 12 and 24 letters (keys of 2 and 4 words, whose table
+    slots publish their key after a claim, so that readers of a hot word wait
+    for it)."""
+    rng = np.random.default_rng({"one_word": 1, "two_words": 2, "hot_and_cold": 3, "all_distinct_wide": 4,
+                                 "hot_and_cold_wide": 5}[case])
     if case == "one_word":
         data = b"hello " * 3_000_000
     elif case == "two_words":
@@ -543,6 +547,15 @@ def test_duplicate_aware_extremes(ctx, oracle_mod, case):
         words = [bytes(r) for r in cold] + [b"zzzzzz"] * 300_000 + [b"aaaaaa"] * 100_000 + [b"mmmmmm"] * 17
         order = rng.permutation(len(words))
         data = b"\n".join(words[i] for i in order)
+    elif case == "hot_and_cold_wide":
+        words = []
+        for L in (12, 24):
+            alpha = np.frombuffer(b"abcdefghijklmnopqrstuvwxyzABC", np.uint8)
+            hot = [bytes(rng.choice(alpha, size=L)) for _ in range(5)]
+            cold = rng.choice(alpha, size=(120_000, L))
+            words += [bytes(r) for r in cold] + [hot[i] for i in rng.integers(0, 5, size=80_000)]
+        order = rng.permutation(len(words))
+        data = b" ".join(words[i] for i in order)
     else:
         lens = rng.integers(33, 37, size=60_000)  # four buckets of about 15,000 words
         words = [bytes(rng.choice(np.frombuffer(b"abcdefghijklmnopqrstuvwxyz", np.uint8), size=L)) for L in lens]
