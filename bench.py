@@ -53,7 +53,7 @@ FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCE = {
     "tokenize": "k_tokenize1p.cu", "scatter": "k_scatter.cu", "emit": "k_scatter.cu",
     "tile_sort": "k_sort2.cu", "merge_pass": "k_sort2.cu", "merge_cut": "k_sort2.cu", "expand": "k_dedupe.cu",
-    "dedupe": "k_dedupe_hash.cu",
+    "dedupe": "k_dedupe_hash.cu", "layout": "k_layout.cu",
 }
 
 

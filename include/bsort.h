@@ -191,8 +191,9 @@ bsort_status bsort_text(bsort_ctx* ctx, const uint8_t* bytes, size_t len, bsort_
  * (any alignment) to len bytes; it must stay unchanged until the work
  * enqueued on `stream` has finished.  `stream` is a cudaStream_t (NULL = the
  * legacy default stream).
- * The call enqueues the whole path on `stream` and waits only for the length
- * histogram, which fixes the bucket layout; it returns with the scalar fields
+ * The call enqueues the whole path on `stream` and waits only for the summary
+ * of the bucket layout (computed on the device from the length histograms),
+ * which fixes the later launches' sizes; it returns with the scalar fields
  * of *out filled and with DEVICE pointers in counts, offsets and stream, whose
  * contents are complete once `stream` reaches the point of return (for
  * example after cudaStreamSynchronize(stream)).
@@ -253,12 +254,14 @@ bsort_status bsort_device_finish(bsort_ctx* ctx, void* stream);
 typedef struct {
   const char* name;   /* kernel family: "tokenize", "scatter", "tile_sort", "merge_pass",
                          "merge_cut" (the tile cuts of a pipelined merge pass), "emit";
+                         "layout" (the bucket layout: one segment per (document, length) from
+                         the length histograms, ordered by the kernels that sort them);
                          "dedupe" (the duplicate-aware sort's hash aggregation of the large
                          buckets) and "expand" (its expansion of the sorted distinct words);
                          and "host_gap", the device time of the call's host round trips (the
-                         length counts read back and the bucket layout copied in; with the
+                         layout's summary read back, until the next launch; with the
                          duplicate-aware sort, also its distinct-key counts) (static string) */
-  uint64_t launches;  /* launches since the last read */
+  uint64_t launches;  /* kernel launches since the last read */
   double ms;          /* summed device time of those launches (0 when profiling is off) */
   double bytes;       /* summed algorithmic bytes of those launches */
   double key_levels;  /* sort kernels: summed key-levels, each key counted once per doubling of the
@@ -280,6 +283,9 @@ typedef struct {
   uint32_t stream;    /* 0: the call's stream; 1..5: the side streams of the tile sorts, 6..9: those of the merge chains */
   uint32_t variant;   /* tile_sort: CTAs per cluster (0: the one-warp sort of tiny buckets);
                          merge_pass / merge_cut: key width in u64 words; else 0 */
+  uint32_t kernels;   /* kernels the launch comprises (layout: 3, dedupe: 2, expand: up to 4, the
+                         length order and the whole-text emit: 3; host_gap: 0; else 1) */
+  uint32_t reserved;
 } bsort_trace_rec;
 
 /* Writes up to `max` traced launches, in launch order, into out[] (waiting for

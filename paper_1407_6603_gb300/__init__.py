@@ -52,7 +52,8 @@ class bsort_kernel_stat(ctypes.Structure):
 
 class bsort_trace_rec(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char_p), ("start_ms", ctypes.c_double), ("end_ms", ctypes.c_double),
-                ("bytes", ctypes.c_double), ("stream", ctypes.c_uint32), ("variant", ctypes.c_uint32)]
+                ("bytes", ctypes.c_double), ("stream", ctypes.c_uint32), ("variant", ctypes.c_uint32),
+                ("kernels", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class bsort_result(ctypes.Structure):
@@ -244,7 +245,7 @@ def bsort_trace_read(h) -> list[tuple[str, float, float, float, int]]:
     if n < 0:
         raise BsortError(BSORT_E_CUDA, "bsort_trace_read failed")
     return [(arr[i].name.decode(), arr[i].start_ms, arr[i].end_ms, arr[i].bytes, int(arr[i].stream),
-             int(arr[i].variant)) for i in range(n)]
+             int(arr[i].variant), int(arr[i].kernels)) for i in range(n)]
 
 
 def bsort_launch_count(h) -> int:

@@ -40,12 +40,6 @@ struct HostBuf {
 // ceil(log2(n)) for n >= 1 (0 for n <= 1)
 double ceil_log2(uint64_t n) { return n <= 1 ? 0.0 : (double)(64 - __builtin_clzll(n - 1)); }
 
-uint32_t merge_passes(uint64_t n, uint64_t tile) {
-  uint32_t p = 0;
-  while ((tile << p) < n) ++p;
-  return p;
-}
-
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Tuning chosen per bucket-size class (see bsort_config.tune_table).  The
@@ -127,11 +121,13 @@ bool parse_tune(const char* text, Tune& t) {
   return true;
 }
 
-// Layout of the device "meta" region, read back in one copy after K2.
 // The meta region: what K1 leaves for the host (read back in one copy of
-// `total` bytes), then K1's look-back scratch; one memset clears both.
+// `total` bytes), then K1's look-back scratch and K2's work area (its
+// accumulators, its summary, the merge chains' barrier counters); one memset
+// clears all three.
 struct MetaLayout {
-  size_t meta = 0, wbase = 0, lbase = 0, item0 = 0, maxlen = 0, hist = 0, total = 0, scratch = 0, cleared = 0;
+  size_t meta = 0, wbase = 0, lbase = 0, item0 = 0, maxlen = 0, hist = 0, total = 0, scratch = 0, layout = 0,
+         cleared = 0;
   void set(uint32_t ndocs, uint32_t chunks) {
     meta = 0;
     wbase = meta + align_up(sizeof(Meta), 128);
@@ -141,16 +137,17 @@ struct MetaLayout {
     hist = maxlen + align_up(ndocs * 4ull, 128);
     total = hist + (size_t)ndocs * kHist * 4;
     scratch = align_up(total, 256);
-    cleared = scratch + tokenize1p_scratch_bytes(chunks);
+    layout = align_up(scratch + tokenize1p_scratch_bytes(chunks), 256);
+    cleared = layout + sizeof(LayoutWork);
   }
 };
 
-enum Kind { kTokenize, kScatter, kTileSort, kMerge, kMergeCut, kEmit, kHostGap, kExpand, kDedupe, kKinds };
+enum Kind { kTokenize, kScatter, kTileSort, kMerge, kMergeCut, kEmit, kHostGap, kExpand, kDedupe, kLayout, kKinds };
 // host_gap is no kernel: the device time between counts reaching the host and
 // the first launch after the layout built from them (the call's round trips:
 // the length counts, and the distinct-key counts of the duplicate-aware sort)
 const char* const kKindName[kKinds] = {"tokenize", "scatter",  "tile_sort", "merge_pass",
-                                       "merge_cut", "emit",     "host_gap",  "expand", "dedupe"};
+                                       "merge_cut", "emit",     "host_gap",  "expand", "dedupe", "layout"};
 
 struct ProfRec {
   int kind;
@@ -158,6 +155,7 @@ struct ProfRec {
   double bytes;
   uint32_t stream;   // 0: the call's stream; 1.. the side streams
   uint32_t variant;  // tile sort: CTAs per cluster (0: warp sort); merge: key width
+  uint32_t kernels;  // kernels the traced call launched
 };
 
 }  // namespace
@@ -181,27 +179,25 @@ struct bsort_ctx {
   DevBuf sticky;  // a Meta kept across calls: err_timeout of bounded device waits
   HostBuf h_sticky;
   DevBuf in, docs, meta, starts, letters, plan, keysA, keysB, counts, offsets, stream, jobs, samples;
-  HostBuf h_in, h_docs, h_meta, h_plan, h_counts, h_offsets, h_stream;
+  HostBuf h_in, h_docs, h_meta, h_lay, h_counts, h_offsets, h_stream;
   // the duplicate-aware sort: hash tables (all slots zero between calls: each
   // call's claims are undone on the device; htab_clean says whether that is
   // known to hold, else the next call clears them), the distinct-key arrays
   // and their ping-pong partner, the second layout, merge scratch and count
   // prefixes
   DevBuf htab, dcnt, uA, uB, plan2, samples2, jobs2, pre, ssum, tfirst, icnt;
-  HostBuf h_plan2, h_ucnt;
+  HostBuf h_plan2, h_ucnt, h_dd;  // h_dd: the duplicate-aware buckets' segments and descriptors
   bool htab_clean = false;
   cudaEvent_t dedupe_ev = nullptr;  // the distinct-key counts reached the host
-  std::vector<uint32_t> dd_seg, dd_pos;
   std::vector<Segment> segv2;
   std::vector<uint8_t> groupv2;
-  HostBuf h_flag;     // K1 raises it once its copy of a small meta region is in h_meta
-  uint32_t seq = 0;   // the value it raises it to: one per call
+  HostBuf h_flag;     // word 0: K1 raises it once its copy of a small meta region is in h_meta;
+                      // word 8: K2 raises it once its summary is in h_lay
+  uint32_t seq = 0;   // the value they are raised to: one per call
 
   // results of the last run (host view)
   MetaLayout ml;
   uint32_t ndocs = 0;
-  std::vector<Segment> segv;
-  std::vector<uint8_t> groupv;
   std::vector<uint32_t> doc_status;
 
   // tracing
@@ -342,6 +338,7 @@ struct Trace {
   double bytes;
   double levels;
   uint32_t variant = 0;
+  uint32_t kernels = 1;  // kernels the traced call launches
   cudaEvent_t a = nullptr;
   Trace(bsort_ctx* c_, cudaStream_t st_, int kind_, double bytes_, double levels_ = 0.0)
       : c(c_), st(st_), kind(kind_), bytes(bytes_), levels(levels_) {
@@ -352,8 +349,8 @@ struct Trace {
   }
   cudaError_t done(cudaError_t e) {
     if (e != cudaSuccess) return e;
-    c->launches += 1;
-    c->kind_launches[kind] += 1;
+    c->launches += kernels;
+    c->kind_launches[kind] += kernels;
     c->kind_bytes[kind] += bytes;
     c->kind_levels[kind] += levels;
     if (a) {
@@ -363,7 +360,7 @@ struct Trace {
         uint32_t sx = 0;
         for (int i = 0; i < bsort_ctx::kSide; ++i)
           if (st == c->side[i]) sx = (uint32_t)i + 1;
-        c->recs.push_back(ProfRec{kind, a, b, bytes, sx, variant});
+        c->recs.push_back(ProfRec{kind, a, b, bytes, sx, variant, kernels});
       }
     }
     return e;
@@ -373,6 +370,13 @@ struct Trace {
 #define LAUNCH(kind, bytes, call, what)                 \
   do {                                                  \
     Trace tr_(c, st, (kind), (double)(bytes));          \
+    CK(tr_.done(call), what);                           \
+  } while (0)
+// the same for a call that launches nk kernels
+#define LAUNCHK(kind, bytes, nk, call, what)            \
+  do {                                                  \
+    Trace tr_(c, st, (kind), (double)(bytes));          \
+    tr_.kernels = (nk);                                 \
     CK(tr_.done(call), what);                           \
   } while (0)
 
@@ -426,47 +430,27 @@ cudaError_t spin_wait(cudaEvent_t ev) {
 }
 
 // ---- sort planning and launching ----
-// Shared by the (document, length) buckets and, for the duplicate-aware sort,
-// by the arrays of their distinct keys.
-//
-// Groups (T = one K4 tile of the bucket's key width; table order below):
-//   0..3  W = 1, 2, 4, 8 and more than 8T keys: K4 into runs of k4_runs or
-//         k4_runs_small tiles, then K5 merge passes (one launch per pass and
-//         width), or, marked kSegDedupe, K4's hash inserts; group 4 unused
-//   5     (4T, 8T] keys: K4 in clusters of 8        6   (2T, 4T]: clusters of 4
-//   7     (T, 2T]: clusters of 2                      8   (32 KPT, T]: single CTAs
-//   9     at most 32 lanes x KPT keys: one warp each
-//   10,11 keys of 16 / 32 words (65..128 / 129..255 letters): the narrow-tile
-//         kernels of k_sort.cu
-constexpr int kGroups = 12;
+// The (document, length) buckets are laid out by K2 on the device
+// (k_layout.cu); the host builds the launch plan from K2's summary
+// (plan_from_summary).  The duplicate-aware sort's second phase, the arrays
+// of the buckets' distinct keys (a handful of buckets, known only after the
+// hash aggregation), is laid out here by plan_sorts, by the same groups
+// (sort_group) and table order (table_order).
 
 uint8_t group_of(Segment& sg, uint64_t& big_tiles) {
   const uint32_t n = sg.n;
   const int W = (int)sg.W;
-  const uint32_t T = W >= 16 ? 0u : tile2_keys(W);
+  const int gi = sort_group(n, W);
   sg.run0 = n;
   sg.passes = 0;
-  uint8_t gi;
-  if (W >= 16) {
-    gi = W == 16 ? 10 : 11;
+  if (gi >= 10) {
     sg.run0 = (uint32_t)tile_of_width(W);
     sg.passes = merge_passes(n, sg.run0);
-  } else if (n <= warp_keys(W)) {
-    gi = 9;
-  } else if (n <= T) {
-    gi = 8;
-  } else if (n <= 2 * T) {
-    gi = 7;
-  } else if (n <= 4 * T) {
-    gi = 6;
-  } else if (n <= (uint32_t)kSuperCluster * T) {
-    gi = 5;
-  } else {  // needs merge passes: runs and passes are set by plan_sorts
-    gi = (uint8_t)class_of_width(W);
+  } else if (gi < 4) {  // needs merge passes: runs and passes are set by plan_sorts
     big_tiles += (n + merge2_keys(W) - 1) / merge2_keys(W);
   }
   sg.final_buf = sg.passes & 1u;
-  return gi;
+  return (uint8_t)gi;
 }
 
 struct K4Launch {
@@ -494,6 +478,11 @@ struct SortPlan {
   // hash-aggregation launch covers [dd_beg, dd_end) in dd_units units
   uint32_t dd_units = 0, dd_beg = 0, dd_end = 0;
   double dd_bytes = 0;
+  // the tags' figures of the launches that are not per K4 launch: key-levels
+  // of the warp sort and the wide keys' tile sorts (groups 9..11), bytes per
+  // merge pass (groups 0..3, then 10 and 11)
+  double lev[kGroups] = {};
+  double moved[6][kMovedPasses] = {};
   uint32_t gb(int g) const { return pbeg[pos_of[g]]; }      // first segment of group g
   uint32_t ge(int g) const { return pbeg[pos_of[g] + 1]; }  // one past its last
 };
@@ -519,14 +508,7 @@ void plan_sorts(const bsort_ctx* c, const std::vector<Segment>& cand, const std:
   // before the one whose cluster size makes their runs, so that every K4
   // launch and every width's merge chain covers one contiguous range; then
   // the warp sort and the wide keys.
-  int n_ord = 0;
-  for (int gc : {5, 6, 7, 8}) {
-    if (kSuperCluster >> (gc - 5) == p.runs || (p.runs > kSuperCluster && gc == 5))
-      for (int g = 0; g < 5; ++g) p.order[n_ord++] = g;
-    p.order[n_ord++] = gc;
-  }
-  for (int g : {9, 10, 11}) p.order[n_ord++] = g;
-  for (int q = 0; q < kGroups; ++q) p.pos_of[p.order[q]] = q;
+  table_order((uint32_t)p.runs, p.order, p.pos_of);
   for (int q = 0; q < kGroups; ++q) p.pbeg[q + 1] = p.pbeg[q] + group_n[p.order[q]];
   {  // stable counting sort of the candidates by table position
     uint32_t at[kGroups];
@@ -616,6 +598,16 @@ void plan_sorts(const bsort_ctx* c, const std::vector<Segment>& cand, const std:
       sg.tile0 = p.wtiles[gi - 10];
       p.wtiles[gi - 10] += (sg.n + sg.run0 - 1) / sg.run0;
       p.wpasses[gi - 10] = std::max(p.wpasses[gi - 10], sg.passes);
+      p.lev[gi] += (double)sg.n * ceil_log2(std::min<uint64_t>(sg.n, sg.run0));
+    } else if (gi == 9) {
+      p.lev[gi] += (double)sg.n * ceil_log2(sg.n);
+    }
+    const int mg = gi < 4 ? gi : gi >= 10 ? gi - 6 : -1;
+    for (uint32_t q = 0; mg >= 0 && q < sg.passes && q < (uint32_t)kMovedPasses; ++q) {
+      // keys in; keys out, or the words at the bucket's last pass
+      const double kw = 8.0 * W * sg.n;
+      const bool words = gi < 4 && q + 1 == sg.passes && !(sg.flags & kSegKeysOut);
+      p.moved[mg][q] += kw + (words ? (double)sg.n * (sg.L + off_bytes) : kw);
     }
   }
   for (int g = 0; g < 4; ++g)
@@ -625,7 +617,66 @@ void plan_sorts(const bsort_ctx* c, const std::vector<Segment>& cand, const std:
     }
 }
 
-bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, const Segment* d_segs, uint64_t* kA,
+// The plan of the (document, length) buckets from K2's summary: the same
+// fields plan_sorts fills, from K2's per-group totals.
+void plan_from_summary(const bsort_ctx* c, const LayoutSummary& S, SortPlan& p) {
+  p.nseg = S.nseg;
+  p.runs = (int)S.runs;
+  table_order(S.runs, p.order, p.pos_of);
+  for (int q = 0; q < kGroups; ++q) p.pbeg[q + 1] = p.pbeg[q] + S.group_n[p.order[q]];
+  const bool dd = S.dd != 0;
+  for (K4Launch& l : p.k4) {
+    const bool runs_here = l.cluster == p.runs && !dd;
+    if (l.gc < 0) {
+      l.sbeg = runs_here ? p.gb(0) : 0u;
+      l.send = runs_here ? p.ge(4) : 0u;
+    } else {
+      l.sbeg = runs_here ? p.gb(0) : p.gb(l.gc);
+      l.send = p.ge(l.gc);
+    }
+    // its groups: the merge-pass groups when its clusters make their runs, and its own
+    for (int g = 0; g < kGroups; ++g) {
+      const bool mine = (g < 4 && runs_here) || g == l.gc;
+      if (!mine) continue;
+      l.supertiles += (uint32_t)S.tot[g][kColStile];
+      l.max_w = std::max(l.max_w, (int)S.max_w[g]);
+      l.key_bytes += (double)S.k4_bytes[g];
+      l.levels += (double)S.levels[g];
+    }
+  }
+  if (dd) {
+    p.dd_beg = p.gb(0);
+    p.dd_end = p.ge(4);
+    for (int g = 0; g < 4; ++g) p.dd_units += (uint32_t)S.tot[g][kColStile];
+    p.dd_bytes = (double)S.dd_bytes;
+  }
+  for (int g = 0; g < kGroups; ++g) {
+    p.key_words += S.tot[g][kColKeyw];
+    p.kb[g] = (double)S.kb[g];
+    p.ob[g] = (double)S.ob[g];
+    p.lev[g] = g >= 9 ? (double)S.levels[g] : 0.0;
+  }
+  for (int g = 0; g < 4; ++g) {
+    p.smp_words += S.tot[g][kColSmp];
+    p.mtiles[g] = (uint32_t)S.tot[g][kColTile];
+    p.mpasses[g] = S.max_passes[g];
+  }
+  for (int i = 0; i < 2; ++i) {
+    p.wtiles[i] = (uint32_t)S.tot[10 + i][kColTile];
+    p.wpasses[i] = S.max_passes[10 + i];
+  }
+  p.etile = p.wtiles[0] + p.wtiles[1];
+  for (int m = 0; m < 6; ++m)
+    for (int q = 0; q < kMovedPasses; ++q) p.moved[m][q] = (double)S.moved[m][q];
+  const uint32_t piped_grid = (uint32_t)(c->sm_count * merge_piped_ctas_per_sm());
+  for (int g = 0; g < 4; ++g)
+    if (p.mpasses[g] && p.mtiles[g] >= c->tune.piped_min * piped_grid) {
+      p.job_at[g] = p.jobs_total;
+      p.jobs_total += p.mtiles[g] + 1;  // and the end sentinel
+    }
+}
+
+bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* d_segs, uint64_t* kA,
                           uint64_t* kB, uint64_t* samples, DevBuf& jobs, uint32_t* barrier_dev, const EmitOut& eo,
                           const DedupeOut& dd, cudaStream_t st, bool side_ok, std::vector<cudaStream_t>& joined,
                           const std::function<bsort_status()>& after_first_k4) {
@@ -662,6 +713,7 @@ bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, 
     // the duplicate-aware sort's buckets first, on the call's stream: the
     // distinct-key counts are read back right after it
     Trace tr_(c, st, kDedupe, p.dd_bytes);
+    tr_.kernels = 2;  // the aggregation, then the tables' completion
     c->htab_clean = false;  // until the launches that also undo the claims are enqueued
     CK(tr_.done(launch_dedupe_hash(d_segs, p.dd_beg, p.dd_end, p.dd_units, c->sm_count, kA, dd, p.dd_end - p.dd_beg,
                                    d_sticky, c->cfg.wait_limit, st)),
@@ -699,18 +751,13 @@ bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, 
   if (p.ge(9) > p.gb(9)) {
     cudaStream_t sx = side_stream();
     if (side) CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
-    double levels = 0;
-    for (uint32_t i = p.gb(9); i < p.ge(9); ++i) levels += (double)segs[i].n * ceil_log2(segs[i].n);
-    Trace tr_(c, sx, kTileSort, (double)p.kb[9] + p.ob[9], levels);
+    Trace tr_(c, sx, kTileSort, (double)p.kb[9] + p.ob[9], p.lev[9]);
     CK(tr_.done(launch_warp_sort(d_segs, p.gb(9), p.ge(9), kA, eo, sx)), "K4 warp_sort");
   }
   for (int g = 10; g < 12; ++g) {
     const uint32_t tiles = p.wtiles[g - 10];
     if (!tiles) continue;
-    double levels = 0;
-    for (uint32_t k = p.gb(g); k < p.ge(g); ++k)
-      levels += (double)segs[k].n * ceil_log2(std::min<uint64_t>(segs[k].n, segs[k].run0));
-    Trace tr_(c, st, kTileSort, 2.0 * p.kb[g], levels);
+    Trace tr_(c, st, kTileSort, 2.0 * p.kb[g], p.lev[g]);
     tr_.variant = 1;
     CK(tr_.done(launch_tile_sort(g == 10 ? 16 : 32, d_segs, p.gb(g), p.ge(g), tiles, std::min(tiles, grid_cap), kA,
                                  d_sticky, c->cfg.wait_limit, st)),
@@ -729,7 +776,6 @@ bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, 
     if (p.mpasses[g]) ++chains;
   const bool chain_side = side_ok && chains > 1;
   if (chain_side) CK(cudaEventRecord(c->fork_ev, st), "fork");
-  const uint64_t off_bytes = c->cfg.want_offsets ? 4 : 0;
   for (int g = 0; g < 4; ++g) {
     if (!p.mpasses[g]) continue;
     const int W = width_of_class(g);
@@ -739,16 +785,7 @@ bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, 
       joined.push_back(sx);
       CK(cudaStreamWaitEvent(sx, c->fork_ev, 0), "fork");
     }
-    auto moved_in = [&](uint32_t pass) {  // keys in, then keys out or, at a bucket's last pass, its words
-      double moved = 0;
-      for (uint32_t i = p.gb(g); i < p.ge(g); ++i) {
-        const Segment& sg = segs[i];
-        if (sg.passes <= pass) continue;
-        const bool words = sg.passes == pass + 1 && !(sg.flags & kSegKeysOut);
-        moved += 8.0 * W * sg.n + (words ? (double)sg.n * (sg.L + off_bytes) : 8.0 * W * sg.n);
-      }
-      return moved;
-    };
+    auto moved_in = [&](uint32_t pass) { return pass < (uint32_t)kMovedPasses ? p.moved[g][pass] : 0.0; };
     if (p.mtiles[g] >= c->tune.piped_min * piped_grid) {
       for (uint32_t pass = 0; pass < p.mpasses[g]; ++pass) {
         const uint64_t* src = (pass & 1) ? kB : kA;
@@ -780,9 +817,7 @@ bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, 
     const int W = g == 10 ? 16 : 32;
     const uint32_t tiles = p.wtiles[g - 10];
     for (uint32_t pass = 0; pass < p.wpasses[g - 10]; ++pass) {
-      double moved = 0;
-      for (uint32_t i = p.gb(g); i < p.ge(g); ++i)
-        if (segs[i].passes > pass) moved += 16.0 * W * segs[i].n;
+      const double moved = pass < (uint32_t)kMovedPasses ? p.moved[g - 6][pass] : 0.0;
       LAUNCH(kMerge, moved,
              launch_merge_pass(W, d_segs, p.gb(g), p.ge(g), tiles, std::min(tiles, grid_cap), pass, (pass & 1) ? kB : kA,
                                (pass & 1) ? kA : kB, st),
@@ -797,13 +832,14 @@ bsort_status launch_sorts(bsort_ctx* c, const SortPlan& p, const Segment* segs, 
   return BSORT_OK;
 }
 
-// The duplicate-aware sort's second half, once K4 has filled the hash tables
-// of the `ndd` buckets marked kSegDedupe (table positions in c->dd_pos): reads
+// The duplicate-aware sort's second half, once the hash aggregation has
+// filled the tables of the `ndd` buckets marked kSegDedupe (dd_segs: host
+// copies of their segments, in dedupe-index order; ins: their descriptors): reads
 // how many distinct keys each bucket has, sorts every bucket's distinct-key
 // array (entries of key + count, kSegKeysOut: the same K4 / K5 kernels, on
 // the side streams as the first sorts), then expands the sorted arrays into
 // the buckets' words.  The counts' read-back is the call's second round trip.
-bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* ins, uint32_t ndd,
+bsort_status sort_distinct(bsort_ctx* c, const Segment* dd_segs, const DedupeIns* ins, uint32_t ndd,
                            const uint32_t* h_ucnt, const EmitOut& eo, cudaStream_t st) {
   cudaEvent_t gap_a = nullptr;
   if (c->cfg.profile) {
@@ -851,7 +887,7 @@ bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* i
   for (uint32_t di = 0; di < ndd; ++di) {
     if (where[di] == kNoSegment) continue;
     const Segment& u = segs2[where[di]];
-    const Segment& b = segs[c->dd_pos[di]];
+    const Segment& b = dd_segs[di];
     ExpandDesc& e = ed[ne++];
     e = ExpandDesc{};
     e.uniq_off = ins[di].uniq_off;
@@ -883,7 +919,7 @@ bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* i
     cudaEvent_t gap_b = next_event(c);
     if (gap_b) {
       cudaEventRecord(gap_b, st);
-      c->recs.push_back(ProfRec{kHostGap, gap_a, gap_b, 0.0, 0u, 0u});
+      c->recs.push_back(ProfRec{kHostGap, gap_a, gap_b, 0.0, 0u, 0u, 0u});
       c->kind_launches[kHostGap] += 1;
     }
   }
@@ -894,7 +930,7 @@ bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* i
   // joined back before the expansion)
   std::vector<cudaStream_t> joined2;
   const DedupeOut no_dd{nullptr, nullptr, nullptr, nullptr, nullptr};
-  bsort_status s = launch_sorts(c, p2, segs2, segs2_dev, dptr<uint64_t>(c->uA), dptr<uint64_t>(c->uB),
+  bsort_status s = launch_sorts(c, p2, segs2_dev, dptr<uint64_t>(c->uA), dptr<uint64_t>(c->uB),
                                 dptr<uint64_t>(c->samples2), c->jobs2, barrier2, eo, no_dd, st, true, joined2, {});
   if (s != BSORT_OK) return s;
   for (size_t i = 0; i < joined2.size(); ++i) {
@@ -903,7 +939,7 @@ bsort_status sort_distinct(bsort_ctx* c, const Segment* segs, const DedupeIns* i
   }
   const ExpandCaps caps{std::min(c->uA.cap, c->uB.cap) / 8, c->pre.cap / 4, c->stream.cap, c->offsets.cap / 4,
                         c->tfirst.cap / 4};
-  LAUNCH(kExpand, moved,
+  LAUNCHK(kExpand, moved, ne == 0 ? 0u : max_tiles == 0 ? 3u : 4u,
          launch_expand(dptr<ExpandDesc>(c->plan2, seg_bytes + barrier_bytes), ne, max_U, max_tiles,
                        dptr<uint64_t>(c->uA), dptr<uint64_t>(c->uB), dptr<uint32_t>(c->pre), dptr<uint32_t>(c->ssum),
                        dptr<uint32_t>(c->tfirst), eo, dptr<Meta>(c->sticky), caps, st),
@@ -921,7 +957,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   // ---- documents and chunks ----
   GROW_HOST(c->h_docs, sizeof(DocDesc) * ndocs, "document table");
   DocDesc* hd = hptr<DocDesc>(c->h_docs);
-  uint64_t chunks = 0, total_len = 0, words_bound = 0;
+  uint64_t chunks = 0, total_len = 0, words_bound = 0, seg_bound = 0;
   for (uint32_t i = 0; i < ndocs; ++i) {
     if (lens[i] >= (1ull << 32))
       return fail(c, BSORT_E_TOO_LARGE, "document of 2^32 bytes or more (offsets are 32-bit)");
@@ -932,41 +968,88 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     total_len += lens[i];
     const uint64_t wb = lens[i] / 2 + 1;
     words_bound += wb;
+    seg_bound += std::min<uint64_t>(wb, kMaxLen);  // a bucket per length with words
   }
   if (total_len >= (1ull << 32))
     return fail(c, BSORT_E_TOO_LARGE, "2^32 bytes or more in one pass (positions are 32-bit)");
   c->ml.set(ndocs, (uint32_t)chunks);
   const MetaLayout& ml = c->ml;
+  const uint32_t order = c->cfg.order;
   GROW(c->docs, sizeof(DocDesc) * ndocs, "document table");
   GROW(c->meta, ml.cleared, "meta");
   GROW(c->starts, 4 * (words_bound + 1), "word starts");
   GROW(c->letters, total_len + 16, "stripped letters");
   GROW_HOST(c->h_meta, ml.total, "meta");
+  GROW_HOST(c->h_lay, sizeof(LayoutSummary), "layout summary");
   Meta* d_meta = dptr<Meta>(c->meta, ml.meta);
   Meta* d_sticky = dptr<Meta>(c->sticky);
   uint32_t* d_wbase = dptr<uint32_t>(c->meta, ml.wbase);
   uint32_t* d_lbase = dptr<uint32_t>(c->meta, ml.lbase);
   uint32_t* d_item0 = dptr<uint32_t>(c->meta, ml.item0);
   uint32_t* d_hist = dptr<uint32_t>(c->meta, ml.hist);
+  LayoutWork* d_work = dptr<LayoutWork>(c->meta, ml.layout);
+
+  // The table K2 writes, sized by bounds known before the counts: a bucket
+  // per (document, length) with words (the whole-text order: per document);
+  // a duplicate-aware bucket holds more than 2048 words.
+  const uint32_t seg_cap = (uint32_t)std::max<uint64_t>(order == BSORT_ORDER_WHOLE ? ndocs : seg_bound, 1);
+  const uint32_t dd_cap = (uint32_t)std::max<uint64_t>(std::min<uint64_t>(seg_cap, words_bound / 2048 + 1), 1);
+  const size_t seg_bytes = align_up(sizeof(Segment) * (size_t)seg_cap, 256);
+  const size_t lookup_bytes = align_up(4ull * std::max<uint32_t>(ndocs, 1) * kHist, 256);
+  const size_t cursor_bytes = align_up(4ull * seg_cap, 256);
+  const size_t ucnt_bytes = align_up(4ull * dd_cap, 256);
+  const size_t ins_bytes = align_up(sizeof(DedupeIns) * (size_t)dd_cap, 256);
+  const size_t var_bytes = order == BSORT_ORDER_WHOLE ? align_up(sizeof(VarDesc) * (size_t)seg_cap, 256) : 0;
+  const size_t blk_bytes = align_up(8 * layout_scratch_words(ndocs), 256);
+  size_t at = 0;
+  const size_t at_segs = at;
+  at += seg_bytes;
+  const size_t at_lookup = at;
+  at += lookup_bytes;
+  const size_t at_cursor = at;
+  at += cursor_bytes;
+  const size_t at_ucnt = at;
+  at += ucnt_bytes;
+  const size_t at_ins = at;
+  at += ins_bytes;
+  const size_t at_var = at;
+  at += var_bytes;
+  const size_t at_blk = at;
+  at += blk_bytes;
+  GROW(c->plan, at, "layout");
+  Segment* const segs_dev = dptr<Segment>(c->plan, at_segs);
+  uint32_t* const lookup_dev = dptr<uint32_t>(c->plan, at_lookup);
+  uint32_t* const cursor_dev = dptr<uint32_t>(c->plan, at_cursor);
+  uint32_t* const ucnt_dev = dptr<uint32_t>(c->plan, at_ucnt);
+  DedupeIns* const ins_dev = dptr<DedupeIns>(c->plan, at_ins);
+  VarDesc* const var_dev = dptr<VarDesc>(c->plan, at_var);
+  uint32_t* const barrier_dev = d_work->barrier;  // one per key width, cleared with meta
 
   // A small meta region (up to 64 KB: about 60 documents) reaches the host
-  // from K1's last CTA directly, without a copy of its own.
+  // from K1's last CTA directly, without a copy of its own; K2's summary
+  // always does (from its last CTA of K2b).
   // (Page-locked host memory is mapped at the same address on the device
   // with unified addressing; where it is not mapped the copy path is taken.)
-  bool meta_direct = ml.total <= 65536;
-  HostMeta hmeta{nullptr, 0, nullptr, 0};
-  if (meta_direct) {
+  bool meta_direct = ml.total <= 65536, lay_direct = true;
+  HostMeta hmeta{nullptr, 0, nullptr, 0}, hlay{nullptr, 0, nullptr, 0};
+  {
     GROW_HOST(c->h_flag, 64, "flag");
     void* dm = nullptr;
+    void* dl = nullptr;
     void* df = nullptr;
     if (cudaHostGetDevicePointer(&dm, c->h_meta.p, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer(&dl, c->h_lay.p, 0) != cudaSuccess ||
         cudaHostGetDevicePointer(&df, c->h_flag.p, 0) != cudaSuccess) {
       cudaGetLastError();
-      meta_direct = false;
+      meta_direct = lay_direct = false;
     } else {
-      if (++c->seq == 0) ++c->seq;  // 0: the flag's value before any call
-      __atomic_store_n(hptr<uint32_t>(c->h_flag), 0u, __ATOMIC_RELEASE);
-      hmeta = HostMeta{static_cast<uint4*>(dm), (uint32_t)(ml.total / 16), static_cast<uint32_t*>(df), c->seq};
+      if (++c->seq == 0) ++c->seq;  // 0: the flags' value before any call
+      uint32_t* hf = hptr<uint32_t>(c->h_flag);
+      __atomic_store_n(hf, 0u, __ATOMIC_RELEASE);
+      __atomic_store_n(hf + 8, 0u, __ATOMIC_RELEASE);
+      uint32_t* df32 = static_cast<uint32_t*>(df);
+      if (meta_direct) hmeta = HostMeta{static_cast<uint4*>(dm), (uint32_t)(ml.total / 16), df32, c->seq};
+      hlay = HostMeta{static_cast<uint4*>(dl), (uint32_t)(sizeof(LayoutSummary) / 16), df32 + 8, c->seq};
     }
   }
   // one document travels as a kernel argument; more as a table
@@ -984,22 +1067,45 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
                            d_meta, d_sticky, c->cfg.l_cap, c->cfg.wait_limit, hmeta, st),
          "K1 tokenize");
   if (!meta_direct) CK(cudaMemcpyAsync(c->h_meta.p, c->meta.p, ml.total, cudaMemcpyDeviceToHost, st), "read counts");
+  // K2: the bucket layout, from K1's histograms.  Its tag: the histograms
+  // read (three times) and the lookup written; the segments written are added
+  // once their number is known.
+  {
+    LayoutParams lp{};
+    lp.ndocs = ndocs;
+    lp.order = order;
+    lp.codec = c->codec;
+    lp.off_bytes = c->cfg.want_offsets ? 4u : 0u;
+    lp.k4_runs = (uint32_t)c->tune.k4_runs;
+    lp.k4_runs_small = (uint32_t)c->tune.k4_runs_small;
+    lp.dedupe = (uint32_t)c->tune.dedupe;
+    lp.piped_tiles = (uint64_t)c->tune.piped_min * c->sm_count * merge_piped_ctas_per_sm();
+    lp.seg_cap = seg_cap;
+    lp.dd_cap = dd_cap;
+    const LayoutOut lo{segs_dev, lookup_dev, cursor_dev, ucnt_dev, ins_dev, var_dev, dptr<uint64_t>(c->plan, at_blk)};
+    Trace tr_(c, st, kLayout, 4.0 * kHist * ndocs * 4);
+    tr_.kernels = 3;
+    CK(tr_.done(launch_layout(lp, d_hist, d_wbase, d_lbase, dptr<uint32_t>(c->meta, ml.maxlen), d_work, lo, hlay, st)),
+       "K2 layout");
+  }
+  if (!lay_direct)
+    CK(cudaMemcpyAsync(c->h_lay.p, &d_work->s, sizeof(LayoutSummary), cudaMemcpyDeviceToHost, st), "read layout summary");
   cudaEvent_t gap_a = nullptr;
   if (c->cfg.profile) {
     gap_a = next_event(c);
     if (gap_a) cudaEventRecord(gap_a, st);
   }
   CK(cudaEventRecord(c->counts_ev, st), "counts event");
-  if (meta_direct)
-    CK(flag_wait(hptr<uint32_t>(c->h_flag), hmeta.seq, c->counts_ev), "wait for counts");
-  else
+  if (lay_direct) {
+    CK(flag_wait(hptr<uint32_t>(c->h_flag) + 8, hlay.seq, c->counts_ev), "wait for the layout");
+    if (meta_direct) CK(flag_wait(hptr<uint32_t>(c->h_flag), hmeta.seq, c->counts_ev), "wait for counts");
+  } else {
     CK(spin_wait(c->counts_ev), "wait for counts");
+  }
 
   const Meta* hm = hptr<Meta>(c->h_meta, ml.meta);
-  const uint32_t* h_wbase = hptr<uint32_t>(c->h_meta, ml.wbase);
-  const uint32_t* h_lbase = hptr<uint32_t>(c->h_meta, ml.lbase);
   const uint32_t* h_hist = hptr<uint32_t>(c->h_meta, ml.hist);
-  const uint32_t* h_maxlen = hptr<uint32_t>(c->h_meta, ml.maxlen);
+  const LayoutSummary& S = *hptr<LayoutSummary>(c->h_lay);
   // K1's own bounded waits (this call), then the sort kernels' waits of an
   // earlier device call whose status nobody collected (bsort_device_finish)
   if (hm->err_timeout || fault_on("timeout"))
@@ -1013,145 +1119,44 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
                 "a bounded device wait of the sort kernels ran out in an earlier device call on this context, "
                 "whose outputs were not valid (bsort_device_finish reports it in time)");
   }
-  const uint32_t n_total = hm->n_total, s_total = hm->s_total, items = hm->items_total;
-  {
-    // K1 reads the input and writes the letters and the word starts
-    const double k1 = (double)total_len + s_total + 4.0 * n_total;
-    c->kind_bytes[kTokenize] += k1;
-    for (auto it = c->recs.rbegin(); it != c->recs.rend(); ++it)
-      if (it->kind == kTokenize) {
-        it->bytes += k1;
-        break;
-      }
+  if (S.seg_over) {
+    CK(cudaStreamSynchronize(st), "layout");
+    return fail(c, BSORT_E_CUDA, "the bucket layout exceeded its table (a consistency check failed)");
   }
-
-  // ---- bucket layout: one segment per (document, length) ----
+  const uint32_t n_total = hm->n_total, s_total = hm->s_total, items = hm->items_total;
+  const uint32_t nseg = S.nseg;
+  {
+    // K1 reads the input and writes the letters and the word starts; K2
+    // writes the segments
+    const double k1 = (double)total_len + s_total + 4.0 * n_total;
+    const double k2 = (double)sizeof(Segment) * nseg;
+    c->kind_bytes[kTokenize] += k1;
+    c->kind_bytes[kLayout] += k2;
+    bool t1 = false, t2 = false;
+    for (auto it = c->recs.rbegin(); it != c->recs.rend() && !(t1 && t2); ++it) {
+      if (it->kind == kTokenize && !t1) {
+        it->bytes += k1;
+        t1 = true;
+      } else if (it->kind == kLayout && !t2) {
+        it->bytes += k2;
+        t2 = true;
+      }
+    }
+  }
   for (uint32_t d = 0; d < ndocs; ++d)
     if (h_hist[(size_t)d * kHist] != 0) c->doc_status[d] = BSORT_E_WORD_TOO_LONG;
-  std::vector<Segment>& cand = c->segv;
-  cand.clear();
-  std::vector<uint8_t>& group = c->groupv;
-  group.clear();
-  uint64_t big_tiles = 0;  // merge tiles of the buckets that need merge passes
-  const uint32_t order = c->cfg.order;
-  for (uint32_t d = 0; d < ndocs; ++d) {
-    if (c->doc_status[d] != BSORT_OK) continue;
-    const uint32_t* h = h_hist + (size_t)d * kHist;
-    uint32_t word_before = h_wbase[d] + d, byte_before = h_lbase[d];
-    if (order == BSORT_ORDER_WHOLE) {
-      // one bucket of every word of the document, keys zero-padded to its
-      // longest word; the words are emitted from the sorted keys afterwards
-      const uint32_t n = h_wbase[d + 1] - h_wbase[d];
-      if (n) {
-        Segment sg{};
-        sg.n = n;
-        sg.L = std::min(h_maxlen[d], (uint32_t)kHist - 1);
-        sg.doc = d;
-        sg.out_word = word_before;
-        sg.stream_off = byte_before;
-        sg.doc_stream0 = h_lbase[d];
-        sg.W = (uint32_t)key_width(c->codec, sg.L);
-        sg.flags = kSegKeysOut;
-        const uint8_t gi = group_of(sg, big_tiles);
-        cand.push_back(sg);
-        group.push_back(gi);
-      }
-      continue;
-    }
-    for (uint32_t L = 1, Lmax = std::min(h_maxlen[d], (uint32_t)kHist - 1); L <= Lmax; ++L) {
-      const uint32_t n = h[L];
-      if (n) {
-        Segment sg{};
-        sg.n = n;
-        sg.L = L;
-        sg.doc = d;
-        sg.out_word = word_before;
-        sg.stream_off = byte_before;
-        sg.doc_stream0 = h_lbase[d];
-        sg.W = (uint32_t)key_width(c->codec, L);
-        const uint8_t gi = group_of(sg, big_tiles);
-        cand.push_back(sg);
-        group.push_back(gi);
-      }
-      word_before += n;
-      byte_before += L * n;
-    }
-  }
-  const uint32_t nseg = (uint32_t)cand.size();
-  // The duplicate-aware sort takes the buckets that would need merge passes
-  // (keys of at most 8 words): K4 hands their sorted runs' distinct keys to a
-  // hash table per bucket instead of writing the runs back.  It pays on large
-  // inputs, whose merges would be pipelined (the same threshold); on smaller
-  // ones its second round trip and launches cost more than the merges save.
-  std::vector<uint32_t>& dd_seg = c->dd_seg;  // candidate index of each such bucket
-  dd_seg.clear();
-  const uint64_t piped_tiles = (uint64_t)c->tune.piped_min * c->sm_count * merge_piped_ctas_per_sm();
-  // (the buckets of the other orders: the whole order's words have mixed
-  // lengths, which the expansion does not handle; the length order sorts nothing)
-  if (order <= BSORT_ORDER_FOLDED &&
-      (c->tune.dedupe == 2 || (c->tune.dedupe == 1 && big_tiles >= piped_tiles)))
-    for (uint32_t i = 0; i < nseg; ++i)
-      if (group[i] < 4) {
-        cand[i].flags = kSegDedupe | ((uint32_t)dd_seg.size() << 8);
-        dd_seg.push_back(i);
-      }
-  const uint32_t ndd = (uint32_t)dd_seg.size();
-  // the layout is built in place in the page-locked upload buffer: segments,
-  // the (document, length) -> segment lookup, the zeroed slot cursors of K3
-  // and grid-barrier counters of the merge chains, the distinct-key counters
-  // and the hash-insert descriptors, which go to the device in one copy
-  const size_t seg_bytes = align_up(sizeof(Segment) * std::max<size_t>(nseg, 1), 256);
-  const size_t lookup_bytes = align_up(4ull * ndocs * kHist, 256);
-  const size_t cursor_bytes = align_up(4ull * (std::max<uint32_t>(nseg, 1) + 4), 256);
-  const size_t ucnt_bytes = align_up(4ull * std::max<uint32_t>(ndd, 1), 256);
-  const size_t ins_bytes = align_up(sizeof(DedupeIns) * std::max<uint32_t>(ndd, 1), 256);
-  const size_t var_bytes = order == BSORT_ORDER_WHOLE ? align_up(sizeof(VarDesc) * std::max<uint32_t>(nseg, 1), 256) : 0;
-  const size_t plan_bytes = seg_bytes + lookup_bytes + cursor_bytes + ucnt_bytes + ins_bytes + var_bytes;
-  GROW_HOST(c->h_plan, plan_bytes, "layout");
-  Segment* const segs = hptr<Segment>(c->h_plan);
-  uint32_t* const lookup = hptr<uint32_t>(c->h_plan, seg_bytes);
-  std::memset(lookup, 0xFF, 4ull * ndocs * kHist);  // kNoSegment
-  std::memset(hptr<char>(c->h_plan, seg_bytes + lookup_bytes), 0, cursor_bytes + ucnt_bytes);
-  DedupeIns* const ins = hptr<DedupeIns>(c->h_plan, seg_bytes + lookup_bytes + cursor_bytes + ucnt_bytes);
-  const uint64_t off_bytes = c->cfg.want_offsets ? 4 : 0;
   SortPlan p1;
-  plan_sorts(c, cand, group, big_tiles, false, off_bytes, segs, p1);
+  plan_from_summary(c, S, p1);
+  const uint32_t ndd = p1.dd_end - p1.dd_beg;
   uint64_t htab_words = 0, uniq_words = 0, cnt_words = 0;
-  std::vector<uint32_t>& dd_pos = c->dd_pos;  // table position of each duplicate-aware bucket
-  dd_pos.assign(ndd, 0);
-  VarDesc* const vdesc = hptr<VarDesc>(c->h_plan, plan_bytes - var_bytes);
-  uint32_t max_doc_words = 0;
-  for (uint32_t i = 0; i < nseg; ++i) {
-    Segment& sg = segs[i];
-    if (order == BSORT_ORDER_WHOLE) {  // every length of the document goes to its one bucket
-      for (uint32_t L = 1; L <= sg.L; ++L)
-        if (h_hist[(size_t)sg.doc * kHist + L]) lookup[(size_t)sg.doc * kHist + L] = i;
-      vdesc[i] = VarDesc{sg.key_off, sg.n, sg.W, sg.final_buf, h_lbase[sg.doc + 1] - h_lbase[sg.doc], sg.out_word,
-                         sg.stream_off, sg.doc_stream0, 0u};
-      max_doc_words = std::max(max_doc_words, sg.n);
-      continue;
-    }
-    lookup[(size_t)sg.doc * kHist + sg.L] = i;
-    if (sg.flags & kSegDedupe) {
-      const uint32_t di = seg_dedupe_index(sg);
-      const uint32_t W = sg.W;
-      DedupeIns& d = ins[di];
-      d = DedupeIns{};
-      d.hbits = (uint32_t)ceil_log2(2ull * sg.n);
-      d.Wp = 2 * W;
-      d.n = sg.n;
-      d.htab_off = htab_words;
-      htab_words += (1ull << d.hbits) * (W + 1);
-      d.uniq_off = uniq_words;
-      uniq_words += align_up((size_t)sg.n * d.Wp, 16);
-      d.cnt_off = cnt_words;
-      if (W == 1) cnt_words += align_up((size_t)sg.n, 16);
-      dd_pos[di] = i;
-    }
+  for (int g = 0; g < 4; ++g) {
+    htab_words += S.tot[g][kColHtab];
+    uniq_words += S.tot[g][kColUniq];
+    cnt_words += S.tot[g][kColDcnt];
   }
+  const uint64_t off_bytes = c->cfg.want_offsets ? 4 : 0;
 
-  // ---- upload the layout, size the key and output buffers ----
-  GROW(c->plan, plan_bytes, "layout");
+  // ---- size the key and output buffers ----
   const uint64_t key_words = order == BSORT_ORDER_LENGTH ? 16 : std::max<uint64_t>(p1.key_words, 16);
   GROW(c->keysA, 8 * key_words, "keys");
   GROW(c->keysB, 8 * key_words, "keys");
@@ -1173,28 +1178,21 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
       CK(cudaMemsetAsync(c->dcnt.p, 0, c->dcnt.cap, st), "clear distinct-key counts");
       c->htab_clean = true;
     }
-    ddo = DedupeOut{dptr<DedupeIns>(c->plan, seg_bytes + lookup_bytes + cursor_bytes + ucnt_bytes),
-                    dptr<uint64_t>(c->htab), dptr<uint64_t>(c->uA),
-                    dptr<uint32_t>(c->plan, seg_bytes + lookup_bytes + cursor_bytes), dptr<uint64_t>(c->dcnt)};
+    ddo = DedupeOut{ins_dev, dptr<uint64_t>(c->htab), dptr<uint64_t>(c->uA), ucnt_dev, dptr<uint64_t>(c->dcnt)};
   }
-  CK(cudaMemcpyAsync(c->plan.p, c->h_plan.p, plan_bytes, cudaMemcpyHostToDevice, st), "copy layout");
-  Segment* const segs_dev = dptr<Segment>(c->plan);
-  uint32_t* const lookup_dev = dptr<uint32_t>(c->plan, seg_bytes);
-  uint32_t* const cursor_dev = dptr<uint32_t>(c->plan, seg_bytes + lookup_bytes);
-  uint32_t* const barrier_dev = cursor_dev + std::max<uint32_t>(nseg, 1);  // one per key width
 
-  if (gap_a) {  // the round trip ends where the layout copy is enqueued
+  if (gap_a) {  // the round trip ends where the first launch after it is enqueued
     cudaEvent_t gap_b = next_event(c);
     if (gap_b) {
       cudaEventRecord(gap_b, st);
-      c->recs.push_back(ProfRec{kHostGap, gap_a, gap_b, 0.0, 0u, 0u});
+      c->recs.push_back(ProfRec{kHostGap, gap_a, gap_b, 0.0, 0u, 0u, 0u});
       c->kind_launches[kHostGap] += 1;
     }
   }
   uint64_t* kA = dptr<uint64_t>(c->keysA);
   uint64_t* kB = dptr<uint64_t>(c->keysB);
   uint64_t key_bytes_all = 0;
-  for (int g = 0; g < kGroups; ++g) key_bytes_all += p1.kb[g];
+  for (int g = 0; g < kGroups; ++g) key_bytes_all += (uint64_t)p1.kb[g];
   const uint32_t grid_cap = (uint32_t)c->sm_count * 16;
   const EmitOut eo{dptr<uint8_t>(c->stream), dptr<uint32_t>(c->offsets), c->cfg.want_offsets, c->codec};
   if (order == BSORT_ORDER_LENGTH) GROW(c->icnt, 4ull * kHist * std::max<uint32_t>(items, 1), "length counts");
@@ -1212,31 +1210,44 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   }
   if (order == BSORT_ORDER_LENGTH) {
     // no sort: every word's place follows from the per-block length counts
-    LAUNCH(kEmit, (double)s_total + 4.0 * n_total + (double)n_total * (off_bytes ? 4.0 : 0.0) + s_total,
+    LAUNCHK(kEmit, (double)s_total + 4.0 * n_total + (double)n_total * (off_bytes ? 4.0 : 0.0) + s_total,
+           items ? 3u : 0u,
            launch_length_order(dptr<uint32_t>(c->starts), dptr<uint8_t>(c->letters), d_wbase, d_item0, ndocs, items,
                                lookup_dev, segs_dev, dptr<uint32_t>(c->icnt), eo, st),
            "length order");
     return BSORT_OK;
   }
-  // K4, K5, K6 of the buckets.  The first K4 launch (on the call's stream)
-  // sorts the buckets that need merge passes: for the duplicate-aware sort,
-  // the distinct-key counts are read back right after it, while the other
-  // launches run on.
+  // K4, K5, K6 of the buckets.  The first launch on the call's stream sorts
+  // the buckets that need merge passes (or, for the duplicate-aware sort,
+  // aggregates them): the distinct-key counts, with the duplicate-aware
+  // buckets' segments and descriptors, are read back right after it, while
+  // the other launches run on.
   std::vector<cudaStream_t> joined;
-  uint32_t* h_ucnt = nullptr;
+  const uint32_t* h_ucnt = nullptr;
+  const Segment* h_ddseg = nullptr;
+  const DedupeIns* h_ins = nullptr;
   auto after_first = [&]() -> bsort_status {
     if (!ndd) return BSORT_OK;
+    const size_t sb = align_up(sizeof(Segment) * ndd, 64), ib = align_up(sizeof(DedupeIns) * ndd, 64);
+    GROW_HOST(c->h_dd, sb + ib, "duplicate-aware buckets");
     GROW_HOST(c->h_ucnt, 4ull * ndd, "distinct-key counts");
+    h_ddseg = hptr<Segment>(c->h_dd);
+    h_ins = hptr<DedupeIns>(c->h_dd, sb);
     h_ucnt = hptr<uint32_t>(c->h_ucnt);
-    CK(cudaMemcpyAsync(h_ucnt, ddo.ucnt, 4ull * ndd, cudaMemcpyDeviceToHost, st), "read distinct-key counts");
+    CK(cudaMemcpyAsync(hptr<Segment>(c->h_dd), segs_dev + p1.dd_beg, sizeof(Segment) * ndd, cudaMemcpyDeviceToHost, st),
+       "read duplicate-aware buckets");
+    CK(cudaMemcpyAsync(hptr<DedupeIns>(c->h_dd, sb), ins_dev, sizeof(DedupeIns) * ndd, cudaMemcpyDeviceToHost, st),
+       "read duplicate-aware buckets");
+    CK(cudaMemcpyAsync(hptr<uint32_t>(c->h_ucnt), ucnt_dev, 4ull * ndd, cudaMemcpyDeviceToHost, st),
+       "read distinct-key counts");
     CK(cudaEventRecord(c->dedupe_ev, st), "distinct-key counts event");
     return BSORT_OK;
   };
-  bsort_status s = launch_sorts(c, p1, segs, segs_dev, kA, kB, dptr<uint64_t>(c->samples), c->jobs, barrier_dev, eo,
-                                ddo, st, true, joined, after_first);
+  bsort_status s = launch_sorts(c, p1, segs_dev, kA, kB, dptr<uint64_t>(c->samples), c->jobs, barrier_dev, eo, ddo, st,
+                                true, joined, after_first);
   if (s != BSORT_OK) return s;
   if (ndd) {
-    s = sort_distinct(c, segs, ins, ndd, h_ucnt, eo, st);
+    s = sort_distinct(c, h_ddseg, h_ins, ndd, h_ucnt, eo, st);
     if (s != BSORT_OK) return s;
   }
   // the launches on side streams
@@ -1246,9 +1257,11 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
   }
   if (order == BSORT_ORDER_WHOLE && nseg) {
     // the words of the whole-text order, from the sorted keys
+    const uint32_t max_doc_words = S.max_doc_words;
     GROW(c->ssum, 4 * std::max<uint64_t>((uint64_t)nseg * var_slices(max_doc_words), 16), "letter prefixes");
-    LAUNCH(kEmit, (double)key_bytes_all + (double)s_total + (double)n_total * (off_bytes ? 4.0 : 0.0),
-           launch_var_emit(dptr<VarDesc>(c->plan, plan_bytes - var_bytes), nseg, max_doc_words, kA, kB, c->codec,
+    LAUNCHK(kEmit, (double)key_bytes_all + (double)s_total + (double)n_total * (off_bytes ? 4.0 : 0.0),
+           max_doc_words ? 3u : 0u,
+           launch_var_emit(var_dev, nseg, max_doc_words, kA, kB, c->codec,
                            dptr<uint32_t>(c->ssum), d_sticky, eo, st),
            "whole-text emit");
   }
@@ -1394,8 +1407,8 @@ void bsort_destroy(bsort_ctx* c) {
                     &c->counts, &c->offsets, &c->stream, &c->jobs, &c->samples, &c->htab, &c->dcnt, &c->uA, &c->uB, &c->plan2,
                     &c->samples2, &c->jobs2, &c->pre, &c->ssum, &c->tfirst, &c->icnt})
     if (b->p) cudaFree(b->p);
-  for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_plan, &c->h_counts, &c->h_offsets,
-                     &c->h_stream, &c->h_flag, &c->h_plan2, &c->h_ucnt})
+  for (HostBuf* b : {&c->h_sticky, &c->h_in, &c->h_docs, &c->h_meta, &c->h_lay, &c->h_counts, &c->h_offsets,
+                     &c->h_stream, &c->h_flag, &c->h_plan2, &c->h_ucnt, &c->h_dd})
     if (b->p) cudaFreeHost(b->p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
@@ -1641,7 +1654,7 @@ int bsort_trace_read(bsort_ctx* c, bsort_trace_rec* out, int max) {
         cudaGetLastError();
         return -1;
       }
-      out[k] = bsort_trace_rec{kKindName[r.kind], s, e, r.bytes, r.stream, r.variant};
+      out[k] = bsort_trace_rec{kKindName[r.kind], s, e, r.bytes, r.stream, r.variant, r.kernels, 0u};
     }
     ++k;
   }

@@ -4,7 +4,9 @@
 //   K1  tokenize      per 16 KiB chunk, one pass (decoupled look-back): the
 //                     stripped letter stream S, the S offset of every word
 //                     start, the per-document length histograms and bases
-//   -- host reads the histograms and lays out one segment per (doc, length)
+//   K2  layout        per document: one segment per (doc, length) with words,
+//                     placed in the table by the kernels that sort it; the
+//                     host reads back only a fixed-size summary (grid sizes)
 //   K3  scatter       per 2048-word block: each word packed into a big-endian
 //                     key of W u64 words, written to its segment
 //   K4  tile_sort     per tile: odd-even transposition sort, then merges
@@ -113,7 +115,7 @@ __host__ __device__ inline TokSum tok_combine(const TokSum& a, const TokSum& b) 
   return r;
 }
 
-// Device-written summary that the host reads after K2.
+// Device-written summary of K1 that the host reads back.
 struct Meta {
   uint32_t n_total;       // words over all documents
   uint32_t s_total;       // letters over all documents
@@ -126,9 +128,9 @@ struct Meta {
   uint32_t err_site;      // sticky: the first such check's site (kernel << 8 | place)
 };
 
-// One (document, length) bucket.  The host orders the table by the K4/K5
-// kernels that sort it (see run_path in bsort_api.cu), so that each launch
-// covers a contiguous range of it.
+// One (document, length) bucket.  K2 orders the table by the K4/K5 kernels
+// that sort it (table_order), so that each launch covers a contiguous range
+// of it.
 struct Segment {
   uint64_t key_off;     // first key, in u64 words, in both key buffers
   uint32_t n;           // words in the bucket
@@ -236,6 +238,59 @@ __host__ __device__ inline uint32_t tile2_keys(int W) { return (uint32_t)(W >= 1
 __host__ __device__ inline uint32_t merge2_keys(int W) { return (uint32_t)(256 * (W >= 8 ? 1 : 8 / W)); }
 // keys a single warp sorts on its own (32 lanes x keys per thread)
 __host__ __device__ inline uint32_t warp_keys(int W) { return (uint32_t)(32 * (W >= 8 ? 1 : 8 / W)); }
+
+// Sort groups of a bucket of n keys of W words (T = tile2_keys(W)):
+//   0..3  W = 1, 2, 4, 8 and more than 8T keys: K4 into runs, then K5 merge
+//         passes, or the duplicate-aware sort's hash aggregation; 4 unused
+//   5     (4T, 8T] keys: K4 in clusters of 8        6   (2T, 4T]: clusters of 4
+//   7     (T, 2T]: clusters of 2                      8   (32 KPT, T]: single CTAs
+//   9     at most 32 lanes x KPT keys: one warp each
+//   10,11 keys of 16 / 32 words: the narrow-tile kernels of k_sort.cu
+constexpr int kGroups = 12;
+__host__ __device__ inline int sort_group(uint32_t n, int W) {
+  if (W >= 16) return W == 16 ? 10 : 11;
+  const uint32_t T = tile2_keys(W);
+  if (n <= warp_keys(W)) return 9;
+  if (n <= T) return 8;
+  if (n <= 2 * T) return 7;
+  if (n <= 4 * T) return 6;
+  if (n <= (uint32_t)kSuperCluster * T) return 5;
+  return class_of_width(W);
+}
+// CTAs per cluster of the K4 launch that finishes group g (5..8)
+__host__ __device__ inline uint32_t group_cluster(int g) { return (uint32_t)kSuperCluster >> (g - 5); }
+// merge passes that take runs of `tile` keys to one run of n
+__host__ __device__ inline uint32_t merge_passes(uint64_t n, uint64_t tile) {
+  uint32_t p = 0;
+  while ((tile << p) < n) ++p;
+  return p;
+}
+__host__ __device__ inline uint32_t ceil_log2_u(uint64_t n) {
+#ifdef __CUDA_ARCH__
+  return n <= 1 ? 0u : (uint32_t)(64 - __clzll((long long)(n - 1)));
+#else
+  return n <= 1 ? 0u : (uint32_t)(64 - __builtin_clzll(n - 1));
+#endif
+}
+// The segment table's order of the groups, given the run length K4 leaves
+// for the merge passes: the groups K4 finishes (clusters of 8, 4, 2, 1), with
+// the groups that need merge passes (0..3, and the unused 4) placed just
+// before the one whose cluster size makes their runs, so that every K4
+// launch and every width's merge chain covers one contiguous range; then
+// the warp sort and the wide keys.  order[q] is the group at position q.
+__host__ __device__ inline void table_order(uint32_t runs, int* order, int* pos_of) {
+  int q = 0;
+  for (int gc = 5; gc <= 8; ++gc) {
+    if (group_cluster(gc) == runs || (runs > (uint32_t)kSuperCluster && gc == 5))
+      for (int g = 0; g < 5; ++g) order[q++] = g;
+    order[q++] = gc;
+  }
+  for (int g = 9; g < kGroups; ++g) order[q++] = g;
+  for (int i = 0; i < kGroups; ++i) pos_of[order[i]] = i;
+}
+// key words per unit of the duplicate-aware sort's hash aggregation
+constexpr uint32_t kDedupeUnitWords = 2048;
+__host__ __device__ inline uint32_t dedupe_unit_keys(uint32_t W) { return kDedupeUnitWords / W; }
 
 // Work items of the sort and emit kernels are numbered across buckets; a
 // CTA finds the bucket of an item by binary search over the buckets' first
@@ -501,7 +556,6 @@ cudaError_t launch_warp_sort(const Segment* segs, uint32_t sbeg, uint32_t send, 
 // `units` in all): every distinct key of a unit goes to its bucket's table
 // with its count; then the `ndd` buckets' distinct-key arrays are completed
 // and their tables' claimed slots zeroed.
-uint32_t dedupe_unit_keys(uint32_t W);
 cudaError_t launch_dedupe_hash(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t units, uint32_t sm_count,
                                const uint64_t* keys, DedupeOut o, uint32_t ndd, Meta* meta, uint64_t wait_limit,
                                cudaStream_t st);
@@ -565,5 +619,71 @@ size_t var_slices(uint32_t max_n);
 // Entries of the slice sums launch_expand needs per bucket (buffer ssum holds
 // nbuckets x expand_slices(max_U)); tfirst holds one entry per output tile.
 size_t expand_slices(uint32_t max_U);
+
+// ---- K2: the bucket layout ----
+// Per (group, column), the sums K2 builds the table from: segments, key
+// words, tiles (merge tiles of groups 0..3, tiles of the wide keys), merge
+// sample words, first-K4 supertiles (or hash-aggregation units), and the
+// duplicate-aware sort's table, array and count words.
+enum LayCol { kColCnt, kColKeyw, kColTile, kColSmp, kColStile, kColHtab, kColUniq, kColDcnt, kLayCols };
+constexpr int kMovedPasses = 32;  // merge passes the per-pass byte tags cover
+// What the host reads back after K2 (through page-locked memory): the
+// call-wide decisions, the table's group sizes, the column totals and the
+// per-group figures of the launches' tags.
+struct LayoutSummary {
+  uint32_t nseg;    // buckets in the table
+  uint32_t runs;    // K4 run length (tiles) of the buckets that need merge passes
+  uint32_t dd;      // 1: groups 0..3 go to the duplicate-aware sort
+  uint32_t dd_beg;  // table position of the first bucket of group 0
+  uint32_t group_n[kGroups];
+  uint32_t max_w[kGroups];       // widest key of the group's K4-sorted buckets
+  uint32_t max_passes[kGroups];  // most merge passes of one bucket (groups 0..3, 10, 11)
+  uint32_t max_doc_words;        // whole-text order: most words of one document
+  uint32_t seg_over;             // buckets that did not fit the table's capacity
+  uint32_t pad[2];
+  uint64_t big_tiles;  // merge tiles of the buckets of groups 0..3
+  uint64_t dd_bytes;   // key bytes the hash aggregation reads
+  uint64_t tot[kGroups][kLayCols];
+  uint64_t kb[kGroups], ob[kGroups];  // key bytes; output bytes (words and offsets, or keys kept)
+  uint64_t k4_bytes[kGroups];         // what K4 moves for the group's buckets
+  uint64_t levels[kGroups];           // key-levels of the group's first sort
+  uint64_t moved[6][kMovedPasses];    // bytes per merge pass: groups 0..3, then 10, 11
+};
+static_assert(sizeof(LayoutSummary) % 16 == 0, "the summary travels as 16-byte words");
+struct LayoutWork {
+  LayoutSummary s;
+  uint32_t ticket;      // K2b's CTAs done
+  uint32_t pad[3];
+  uint32_t barrier[4];  // grid-barrier counters of the four key widths' merge chains
+};
+struct LayoutParams {
+  uint32_t ndocs, order, codec, off_bytes;
+  uint32_t k4_runs, k4_runs_small, dedupe, pad;
+  uint64_t piped_tiles;  // merge tiles from which the merges are pipelined
+  uint32_t seg_cap;      // entries of the segment table and of the slot cursors
+  uint32_t dd_cap;       // entries of the hash-insert descriptors and distinct-key counters
+};
+// Where K2 writes the table: segments (table order), the (document, length)
+// -> segment lookup (every entry written), the slot cursors of K3 and the
+// distinct-key counters (written zero), the hash-insert descriptors (by
+// table position minus dd_beg), the whole-text order's descriptors (by table
+// position); blk holds K2's per-CTA sums (layout_scratch_words).
+struct LayoutOut {
+  Segment* segs;
+  uint32_t* lookup;
+  uint32_t* cursor;
+  uint32_t* ucnt;
+  DedupeIns* ins;
+  VarDesc* vdesc;
+  uint64_t* blk;
+};
+size_t layout_scratch_words(uint32_t ndocs);
+// K2 over the call's documents, after K1: reads the histograms and bases K1
+// left (hist, wbase, lbase, maxlen), accumulates into *work (zeroed before the
+// launch), and leaves the summary at hm.dst (n16 16-byte words, then seq in
+// *hm.flag) as soon as the table's sizes are known, before the table itself
+// is written.
+cudaError_t launch_layout(const LayoutParams& p, const uint32_t* hist, const uint32_t* wbase, const uint32_t* lbase,
+                          const uint32_t* maxlen, LayoutWork* work, LayoutOut out, HostMeta hm, cudaStream_t st);
 
 }  // namespace bsort

@@ -28,7 +28,7 @@ namespace bsort {
 namespace {
 
 constexpr int kHaThreads = 256;
-constexpr uint32_t kHaUnitWords = 2048;          // key words per unit (16 KiB)
+constexpr uint32_t kHaUnitWords = kDedupeUnitWords;  // key words per unit (16 KiB)
 constexpr uint32_t kHaSlots = 2 * kHaUnitWords;  // table slots for W = 1 (16 KiB)
 constexpr uint32_t kHaEmpty = 0xFFFFFFFFu;
 constexpr size_t kHaSmem = 8 * kHaUnitWords + 4 * kHaSlots;
@@ -215,8 +215,6 @@ __global__ void __launch_bounds__(kHaThreads) k_dedupe_finish(uint32_t ndd, Dedu
 int attr_done[64];
 
 }  // namespace
-
-uint32_t dedupe_unit_keys(uint32_t W) { return kHaUnitWords / W; }
 
 cudaError_t launch_dedupe_hash(const Segment* segs, uint32_t sbeg, uint32_t send, uint32_t units, uint32_t sm_count,
                                const uint64_t* keys, DedupeOut o, uint32_t ndd, Meta* meta, uint64_t wait_limit,

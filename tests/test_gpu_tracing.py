@@ -5,7 +5,8 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-FAMILIES = {"tokenize", "scatter", "tile_sort", "merge_pass", "merge_cut", "emit", "host_gap", "expand", "dedupe"}
+FAMILIES = {"tokenize", "layout", "scatter", "tile_sort", "merge_pass", "merge_cut", "emit", "host_gap", "expand",
+            "dedupe"}
 
 
 def test_profile_and_timeline(bsort_gpu, synth_mod):
@@ -19,11 +20,15 @@ def test_profile_and_timeline(bsort_gpu, synth_mod):
         stats = c.profile_read()
         assert c.trace_read() == []  # the profile read clears the records
     assert {r[0] for r in tl} <= FAMILIES
-    # every kernel launch is traced, plus the host round trip
-    assert sum(1 for r in tl if r[0] != "host_gap") == launches
+    # every kernel launch is traced (a record counts the kernels it covers),
+    # plus the host round trip
+    assert sum(r[6] for r in tl if r[0] != "host_gap") == launches
+    assert all(r[6] >= 1 for r in tl if r[0] != "host_gap")
     assert sum(1 for r in tl if r[0] == "host_gap") == 1
     assert tl[0][0] == "tokenize" and tl[0][1] == 0.0
-    for name, s, e, b, st, var in tl:
+    # the bucket layout runs on the device, between the tokenizer and the round trip
+    assert tl[1][0] == "layout" and tl[1][6] == 3
+    for name, s, e, b, st, var, nk in tl:
         assert 0.0 <= s <= e, name
         assert 0 <= st <= 4
         if name == "tile_sort":
@@ -33,7 +38,11 @@ def test_profile_and_timeline(bsort_gpu, synth_mod):
     for name in {r[0] for r in tl}:
         ms = sum(e - s for n, s, e, *_ in tl if n == name)
         assert stats[name][1] == pytest.approx(ms, rel=1e-3, abs=1e-3), name
-        assert stats[name][0] == sum(1 for r in tl if r[0] == name)
+        # (a host gap is no kernel: its count is the number of gaps)
+        want = sum(1 if name == "host_gap" else r[6] for r in tl if r[0] == name)
+        assert stats[name][0] == want, name
     # the tokenizer runs first, every sort launch starts after the round trip
     gap = next(r for r in tl if r[0] == "host_gap")
     assert all(r[1] >= gap[1] for r in tl if r[0] in ("scatter", "tile_sort", "merge_pass"))
+    lay = next(r for r in tl if r[0] == "layout")
+    assert lay[2] <= gap[1] + 1e-3
