@@ -283,7 +283,7 @@ typedef struct {
   uint32_t stream;    /* 0: the call's stream; 1..5: the side streams of the tile sorts, 6..9: those of the merge chains */
   uint32_t variant;   /* tile_sort: CTAs per cluster (0: the one-warp sort of tiny buckets);
                          merge_pass / merge_cut: key width in u64 words; else 0 */
-  uint32_t kernels;   /* kernels the launch comprises (layout: 3, dedupe: 2, expand: up to 4, the
+  uint32_t kernels;   /* kernels the launch comprises (layout: 1 or 3, dedupe: 2, expand: up to 4, the
                          length order and the whole-text emit: 3; host_gap: 0; else 1) */
   uint32_t reserved;
 } bsort_trace_rec;

@@ -1084,7 +1084,7 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     lp.dd_cap = dd_cap;
     const LayoutOut lo{segs_dev, lookup_dev, cursor_dev, ucnt_dev, ins_dev, var_dev, dptr<uint64_t>(c->plan, at_blk)};
     Trace tr_(c, st, kLayout, 4.0 * kHist * ndocs * 4);
-    tr_.kernels = 3;
+    tr_.kernels = (uint32_t)layout_kernels(ndocs);
     CK(tr_.done(launch_layout(lp, d_hist, d_wbase, d_lbase, dptr<uint32_t>(c->meta, ml.maxlen), d_work, lo, hlay, st)),
        "K2 layout");
   }

@@ -678,6 +678,8 @@ struct LayoutOut {
   uint64_t* blk;
 };
 size_t layout_scratch_words(uint32_t ndocs);
+// Kernels launch_layout starts for ndocs documents (one when one CTA holds them all).
+int layout_kernels(uint32_t ndocs);
 // K2 over the call's documents, after K1: reads the histograms and bases K1
 // left (hist, wbase, lbase, maxlen), accumulates into *work (zeroed before the
 // launch), and leaves the summary at hm.dst (n16 16-byte words, then seq in

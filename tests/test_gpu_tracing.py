@@ -27,7 +27,7 @@ def test_profile_and_timeline(bsort_gpu, synth_mod):
     assert sum(1 for r in tl if r[0] == "host_gap") == 1
     assert tl[0][0] == "tokenize" and tl[0][1] == 0.0
     # the bucket layout runs on the device, between the tokenizer and the round trip
-    assert tl[1][0] == "layout" and tl[1][6] == 3
+    assert tl[1][0] == "layout" and tl[1][6] == 1  # one document: the one-CTA form
     for name, s, e, b, st, var, nk in tl:
         assert 0.0 <= s <= e, name
         assert 0 <= st <= 4
