@@ -538,6 +538,8 @@ __global__ void __launch_bounds__(kLayThreads) k_layout_write(LayoutParams p, co
 }
 
 // All three phases in one CTA (every document in it): no scratch, no ticket.
+// The summary is built in shared memory and stored from there to the host
+// and to the work area.
 __global__ void __launch_bounds__(kLayThreads) k_layout_one(LayoutParams p, const uint32_t* __restrict__ hist,
                                                              const uint32_t* __restrict__ wbase,
                                                              const uint32_t* __restrict__ lbase,
@@ -550,16 +552,19 @@ __global__ void __launch_bounds__(kLayThreads) k_layout_one(LayoutParams p, cons
   __shared__ unsigned long long s_kb[kGroups];
   __shared__ unsigned long long s_bt[kLayDocs];
   __shared__ LayMax s_mx;
+  __shared__ __align__(16) LayoutSummary s_S;  // (copied as 16-byte words)
   const uint32_t t = threadIdx.x, lane = t & 31u, warp = t >> 5, d = warp;
   clear_shared(&s_slot[0][0], kLayDocs * kSlotEntries);
   for (uint32_t i = t; i < sizeof(LayMax) / 4; i += kLayThreads) reinterpret_cast<uint32_t*>(&s_mx)[i] = 0;
+  for (uint32_t i = t; i < sizeof(LayoutSummary) / 16; i += kLayThreads)
+    reinterpret_cast<uint4*>(&s_S)[i] = make_uint4(0, 0, 0, 0);
   const uint64_t bt = doc_tiles(p, d, hist, wbase, maxlen, lane);
   if (lane == 0) s_bt[warp] = bt;
   __syncthreads();
   unsigned long long big = 0;
   for (int w = 0; w < kLayDocs; ++w) big += s_bt[w];
   const Choice ch = choose(p, big);
-  LayoutSummary& S = work->s;
+  LayoutSummary& S = s_S;
   doc_sums<true>(p, ch, d, hist, wbase, maxlen, lane, s_slot[warp], &s_mx, &S);
   __syncthreads();
   for (uint32_t i = t; i < (uint32_t)kSlotEntries; i += kLayThreads) {
@@ -590,7 +595,23 @@ __global__ void __launch_bounds__(kLayThreads) k_layout_one(LayoutParams p, cons
   }
   __syncthreads();
   plan_groups(p, ch, s_tot, s_kb, s_base, S);
-  send_summary(S, hm);
+  __syncthreads();
+  {
+    // the summary to the work area and to the host, then the flag
+    const uint4* src = reinterpret_cast<const uint4*>(&S);
+    uint4* dev = reinterpret_cast<uint4*>(&work->s);
+    constexpr uint32_t n16 = sizeof(LayoutSummary) / 16;
+    for (uint32_t i = t; i < n16; i += kLayThreads) {
+      const uint4 v = src[i];
+      dev[i] = v;
+      if (hm.dst && i < hm.n16) hm.dst[i] = v;
+    }
+    if (hm.dst) {
+      __threadfence_system();
+      __syncthreads();
+      if (t == 0) asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(hm.flag), "r"(hm.seq) : "memory");
+    }
+  }
   // the documents' bases: the group bases, then the documents before each
   for (uint32_t i = lane; i < (uint32_t)kLayEntries; i += 32) {
     const uint32_t g = i / kLayCols, c = i % kLayCols;
