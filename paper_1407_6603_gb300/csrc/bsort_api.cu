@@ -143,9 +143,9 @@ struct MetaLayout {
 };
 
 enum Kind { kTokenize, kScatter, kTileSort, kMerge, kMergeCut, kEmit, kHostGap, kExpand, kDedupe, kLayout, kKinds };
-// host_gap is no kernel: the device time between counts reaching the host and
-// the first launch after the layout built from them (the call's round trips:
-// the length counts, and the distinct-key counts of the duplicate-aware sort)
+// host_gap is no kernel: the device time between a summary the host waits
+// for and the first launch planned from it (the call's round trips: the
+// layout's summary, and the distinct-key counts of the duplicate-aware sort)
 const char* const kKindName[kKinds] = {"tokenize", "scatter",  "tile_sort", "merge_pass",
                                        "merge_cut", "emit",     "host_gap",  "expand", "dedupe", "layout"};
 
