@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kTokThreads, BSORT_K1_MIN_CTAS) k_tokenize1p(
           st_acc(&rec[c].agg, total);
           st_release(&rec[c].status, 1u);
         }
-        int j0 = (int)c - 1;  // newest predecessor of this round
+        int j0 = (int)c - 1;  // newest predecessor the next 32-record read covers
         uint64_t polls = 0;
         for (;;) {
           const int idx = j0 - lane;
