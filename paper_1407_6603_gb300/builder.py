@@ -21,7 +21,8 @@ INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["k_tokenize1p.cu", "k_scatter.cu", "k_sort.cu", "k_sort2.cu", "k_tile_g2.cu", "k_tile_g4.cu",
            "k_tile_g8.cu", "k_strip_noalloc.cu", "k_dedupe.cu", "k_dedupe_hash.cu", "k_order.cu", "k_layout.cu",
            "bsort_api.cu", "bsort_serve.cu"]
-HEADERS = ["bsort_dev.cuh", "tok_common.cuh", "swar.h", "sort_common.cuh", "tile_sort2.cuh", "dedupe.cuh"]
+HEADERS = ["bsort_dev.cuh", "tok_common.cuh", "swar.h", "sort_common.cuh", "tile_sort2.cuh", "dedupe.cuh",
+           "layout_bounds.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", *ARCH]
 

@@ -23,6 +23,7 @@
 
 #include "bsort.h"
 #include "bsort_dev.cuh"
+#include "layout_bounds.h"
 
 using namespace bsort;
 
@@ -968,7 +969,8 @@ bsort_status run_path(bsort_ctx* c, const uint8_t* d_in, const uint64_t* offs, c
     total_len += lens[i];
     const uint64_t wb = lens[i] / 2 + 1;
     words_bound += wb;
-    seg_bound += std::min<uint64_t>(wb, kMaxLen);  // a bucket per length with words
+    // a bucket per length with words
+    seg_bound += std::min<uint64_t>(std::min<uint64_t>(wb, kMaxLen), max_distinct_lengths(lens[i]));
   }
   if (total_len >= (1ull << 32))
     return fail(c, BSORT_E_TOO_LARGE, "2^32 bytes or more in one pass (positions are 32-bit)");

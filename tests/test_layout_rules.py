@@ -14,7 +14,10 @@ functions as plain C++ and checks them against their definitions:
   `runs` tiles; before group 5 when runs exceed one cluster of 8), so that
   each K4 launch and each merge chain covers one contiguous range;
 * merge passes: the doublings that take runs of `tile` keys to one run of n;
-* ceil(log2 n).
+* ceil(log2 n);
+* the bucket table's capacity per document (layout_bounds.h): the most
+  distinct word lengths len bytes can hold, against a search over every set
+  of lengths for small documents.
 """
 import math
 import os
@@ -28,6 +31,7 @@ CSRC = os.path.join(ROOT, "paper_1407_6603_gb300", "csrc")
 
 PROGRAM = r"""
 #include "bsort_dev.cuh"
+#include "layout_bounds.h"
 #include <cstdio>
 int main() {
   using namespace bsort;
@@ -50,6 +54,10 @@ int main() {
       printf("passes %llu %llu %u\n", (unsigned long long)n, (unsigned long long)tile, merge_passes(n, tile));
   for (uint64_t n : {0ull, 1ull, 2ull, 3ull, 4ull, 5ull, 1023ull, 1024ull, 1025ull, (1ull << 40) + 1})
     printf("clog %llu %u\n", (unsigned long long)n, ceil_log2_u(n));
+  for (uint64_t len = 0; len <= 300; ++len)
+    printf("mdl %llu %llu\n", (unsigned long long)len, (unsigned long long)max_distinct_lengths(len));
+  for (uint64_t len : {1000ull, 1447000ull, 268435456ull, 4294967295ull})
+    printf("mdl %llu %llu\n", (unsigned long long)len, (unsigned long long)max_distinct_lengths(len));
   return 0;
 }
 """
@@ -132,3 +140,24 @@ def test_merge_passes_and_ceil_log2(rules):
     for r in (r for r in rules if r[0] == "clog"):
         n, v = int(r[1]), int(r[2])
         assert v == (0 if n <= 1 else (n - 1).bit_length()), n
+
+
+def test_distinct_length_bound(rules):
+    mdl = {int(r[1]): int(r[2]) for r in rules if r[0] == "mdl"}
+    # small documents: the largest set of distinct lengths whose words fit,
+    # each word its letters and one whitespace byte before every word but the first
+    for length in range(0, 17):
+        best = 0
+        for mask in range(1 << length):
+            ls = [i + 1 for i in range(length) if mask >> i & 1]
+            if ls and sum(ls) + len(ls) - 1 <= length:
+                best = max(best, len(ls))
+        assert mdl[length] == best, length
+    # every size: the largest k with k(k + 1)/2 + k - 1 <= len, never decreasing
+    prev = 0
+    for length, k in sorted(mdl.items()):
+        assert k * (k + 1) // 2 + k - 1 <= length or k == 0
+        assert (k + 1) * (k + 2) // 2 + k > length
+        assert k >= prev
+        prev = k
+    assert mdl[1000] == 43 and mdl[1447000] == 1699
